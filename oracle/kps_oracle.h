@@ -1,0 +1,141 @@
+/*
+ * kps_oracle.h -- plain CPU oracle for the Kronecker-structured payoff
+ * matrix of a poker river endgame (Farina & Sandholm, "Fast Payoff Matrix
+ * Sparsification Techniques for Structured Extensive-Form Games", AAAI-22).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no
+ * code, header, table or helper with the CUDA product path.
+ *
+ * Everything is FP64 and written for clarity, not speed: the payoff matrix is
+ * built from its definition (Sec. 2: A[s1,s2] = sum over terminals z of
+ * u(z) * c(z)), the chance distribution pi(h1,h2) of Sec. 3 and the
+ * skeleton betting tree of Fig. 1.
+ *
+ * Layout conventions used by this oracle (its own, independent of the
+ * library's):
+ *   - hands are in CANONICAL order: the deck minus the board in increasing
+ *     card id (card id = rank*suits + suit); 1-card hands are single cards,
+ *     2-card hands are the pairs (a<b) in lexicographic order;
+ *   - strategy and gradient vectors are [sequence][hand] (hand fastest);
+ *   - the dense payoff matrix follows the paper's block layout: row index
+ *     h1*n1 + s1, column index h2*n2 + s2 (Sec. 3, block A_{h1,h2}).
+ */
+#ifndef KPS_ORACLE_H
+#define KPS_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAX_BETS 8
+#define ORC_MAX_BOARD 8
+
+typedef struct {
+    int ranks, suits;          /* deck = ranks*suits cards                    */
+    int cards_per_hand;        /* 1 or 2                                      */
+    int nboard;                /* number of public cards                      */
+    int board[ORC_MAX_BOARD];  /* card ids                                    */
+    double stack[2];           /* chips behind at the start of the endgame    */
+    double contrib0[2];        /* pot contribution at the start               */
+    int nbet;                  /* number of bet/raise pot fractions           */
+    double bet_frac[ORC_MAX_BETS];
+    int raise_cap;             /* max aggressive actions in the round; <0 = none */
+    int allow_allin;           /* explicit all-in action                      */
+    const double *mu1, *mu2;   /* beliefs per canonical hand; NULL = uniform  */
+    const int *strength;       /* per canonical hand, higher = stronger       */
+} orc_spec;
+
+typedef struct orc_game orc_game;
+
+/* Build the skeleton, the hand list and pi.  Returns NULL on invalid input. */
+orc_game *orc_build(const orc_spec *spec);
+void orc_free(orc_game *g);
+
+/* info[0..9] = H, n1, n2, T, T_fold, T_showdown, nnodes, ncards_left,
+ *              nplayer_nodes1, nplayer_nodes2 */
+void orc_info(const orc_game *g, int *info);
+double orc_beta(const orc_game *g);
+double orc_pot0(const orc_game *g);
+
+/* Canonical hand list: cards[h*k + j]. */
+void orc_hands(const orc_game *g, int *cards);
+
+/* Terminal list in depth-first order.  kind: 0 fold, 1 showdown.
+ * folder: 0/1 for fold terminals, -1 otherwise.  s1, s2: the last sequence
+ * of each player on the path (-1 = empty sequence).  c1, c2: contributions. */
+void orc_terminals(const orc_game *g, int *s1, int *s2, int *kind, int *folder,
+                   double *c1, double *c2);
+
+/* Per player p: for each of its sequences, the player node it belongs to,
+ * the parent sequence of that node (-1 = empty) and the action code
+ * (0 fold, 1 check/call, 2 aggressive).  nodes_nact[i] = actions of node i. */
+void orc_sequences(const orc_game *g, int p, int *seq_node, int *seq_parent,
+                   int *seq_action, double *seq_amount, int *nodes_nact);
+
+/* Terminal reached by an action path; path tokens: 'f' fold, 'c' check/call,
+ * 'b' the k-th smallest aggressive amount is given as a digit after 'b'
+ * ("b0", "b1", ...), 'a' the largest aggressive amount (all-in).  Tokens are
+ * separated by spaces.  Returns the terminal index or -1. */
+int orc_find_terminal(const orc_game *g, const char *path);
+
+/* Dense payoff matrix for player 1 (Sec. 2 definition), paper block layout,
+ * (H*n1) x (H*n2) doubles, row-major. */
+int orc_dense_A(const orc_game *g, double *A);
+
+/* Direct products by summation over terminals and hand pairs.
+ * y: [batch][n2][H], out: [batch][n1][H]  (A y)
+ * x: [batch][n1][H], out: [batch][n2][H]  (A^T x) */
+void orc_matvec_A(const orc_game *g, const double *y, double *out, int batch,
+                  int nthreads);
+void orc_matvec_AT(const orc_game *g, const double *x, double *out, int batch,
+                   int nthreads);
+/* Selected entries of A y_b: for each k, out[k] = (A y_{b[k]})[s[k]][h[k]]. */
+void orc_matvec_A_entries(const orc_game *g, const double *y, int nent,
+                          const int *b, const int *s, const int *h, double *out);
+void orc_matvec_AT_entries(const orc_game *g, const double *x, int nent,
+                           const int *b, const int *s, const int *h, double *out);
+
+/* Brute-force expected payoff of player 1 by walking the full game tree
+ * (chance deal, then the skeleton) with behavioural strategies beh1 [n1][H]
+ * and beh2 [n2][H] (probability of each sequence's action at its node). */
+double orc_bruteforce_value(const orc_game *g, const double *beh1,
+                            const double *beh2);
+
+/* Behavioural -> sequence form for player p: [n_p][H] -> [n_p][H]. */
+void orc_seqform(const orc_game *g, int p, const double *beh, double *x);
+
+/* Technique B (Sec. 4): dense explicit factors in the strength-sorted hand
+ * order for small games.  Writes nnz counts:
+ * cnt[0..4]  = nnz(A), nnz(Ahat), nnz(U), nnz(M), nnz(V)   before postprocessing
+ * cnt[5..8]  = nnz(Ahat), nnz(U), nnz(M), nnz(V)           after postprocessing
+ * and returns max |A - (Ahat + U M^-1 V^T)| (entrywise), both sides in the
+ * sorted order, or -1 if the game is too large (H*max(n1,n2) > 4096). */
+double orc_technique_b(const orc_game *g, long long *cnt);
+
+/* Counts only (no dense matrices); valid for any size. Same cnt layout. */
+void orc_technique_b_counts(const orc_game *g, long long *cnt);
+
+/* RM+ (CFR+-style) alternating self-play with linearly weighted averages.
+ * x0, y0: initial behavioural strategies [n][H] (NULL = uniform).
+ * Runs iters iterations; writes average behavioural strategies (optional,
+ * may be NULL) and returns the exploitability of the average in units of
+ * the initial pot.  trace (optional, length iters) gets the exploitability
+ * of the average after every iteration when trace_every > 0 and
+ * (t % trace_every == 0), else 0. */
+double orc_rmplus(const orc_game *g, int iters, const double *beh1_0,
+                  const double *beh2_0, double *avg_beh1, double *avg_beh2,
+                  double *trace, int trace_every);
+
+/* Best-response values: br1 = max_x x^T A y, br2 = max_y -x^T A y for
+ * sequence-form x [n1][H], y [n2][H].  Returns (br1 + br2)/2/pot0. */
+double orc_exploitability(const orc_game *g, const double *x, const double *y,
+                          double *br1, double *br2);
+
+/* x^T A y for sequence-form vectors. */
+double orc_value(const orc_game *g, const double *x, const double *y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
