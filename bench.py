@@ -1,0 +1,320 @@
+"""Benchmark of the Kronecker payoff products on GB300.
+
+A step is one pass of the hot path over one batch: out = A*y and
+out' = A^T*x for 1024 strategy vectors of the 1081-hand river endgame
+(52-card deck, 5-card board, bets of 0.5 and 1.0 pot, at most 3 aggressive
+actions: 57 terminals, 43+43 sequences), FP32.  The metric counts
+vector-products (each A*y_b or A^T*x_b is one matvec).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "payoff matvecs/sec and HBM GB/s (fraction of peak); solver wall-time to 1e-3 pot"
+UNIT = "matvecs/s"
+BATCH = 1024
+WORKLOAD = "river endgame, 1081 hands, 43+43 sequences, 57 terminals, batch 1024, fp32"
+KERNEL_SRC = os.path.join(ROOT, "paper_2112_03804_gb300", "csrc", "kernels.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def _traffic(kernel_hash):
+    """DRAM bytes per launch from the committed ncu capture, if it was taken
+    on the current kernel source."""
+    try:
+        d = json.load(open(TRAFFIC_FILE))
+        if d.get("kernel_sha") == kernel_hash:
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _workload():
+    from paper_2112_03804_gb300 import synth
+    return synth.river_spec(seed=2)
+
+
+def cpu_baseline(spec, seconds: float):
+    """The FP64 oracle's direct products (its own OpenMP loop over vectors)
+    on this machine's host cores, on a bounded sample of the same workload."""
+    from oracle.oracle import OracleGame
+    from paper_2112_03804_gb300 import synth
+    og = OracleGame(spec)
+    cores = os.cpu_count() or 1
+    y1 = synth.simplex_vectors(og.sequences(1)["nact"], og.H, 1, seed=3)
+    t0 = time.perf_counter()
+    og.matvec_A(y1, nthreads=1)
+    per_vec = time.perf_counter() - t0
+    nvec = max(cores, int(seconds * cores / max(per_vec, 1e-6)) // cores * cores)
+    y = synth.simplex_vectors(og.sequences(1)["nact"], og.H, nvec, seed=3)
+    t0 = time.perf_counter()
+    og.matvec_A(y, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": nvec / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nvec} vectors of A*y on the benchmark game (FP64 oracle, direct sum over "
+                      f"terminals and hand pairs), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    spec = _workload()
+    from oracle.oracle import OracleGame
+    from paper_2112_03804_gb300 import synth
+    og = OracleGame(spec)
+    cores = os.cpu_count() or 1
+    # one step = a bounded sample (one vector per core, both directions)
+    ny = cores
+    y = synth.simplex_vectors(og.sequences(1)["nact"], og.H, ny, seed=3)
+    x = synth.simplex_vectors(og.sequences(0)["nact"], og.H, ny, seed=4)
+    for _ in range(args.warmup):
+        og.matvec_A(y[:1], nthreads=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        og.matvec_A(y, nthreads=cores)
+        og.matvec_AT(x, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = 2 * ny * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle sample: "
+                                                             f"{ny}+{ny} vectors per step)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{ny} vectors of A*y and {ny} of A^T*x per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2112_03804_gb300 import kps, synth
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    spec = _workload()
+    g = kps.Game(spec)
+    inf = g.info()
+    H, hs, n1, n2 = inf["H"], inf["hs"], inf["n1"], inf["n2"]
+    s = np.asarray(spec["strength"])
+    order = np.lexsort((np.arange(len(s)), s))
+    stream = torch.cuda.current_stream()
+    # inputs: per-infoset simplex vectors (library hand order), resident in HBM
+    def make(p, n, seed):
+        v = synth.simplex_vectors(g.sequences(p)["nact"], H, BATCH, seed=seed + 1000 * rank,
+                                  dtype=np.float32)
+        out = np.zeros((BATCH, n, hs), dtype=np.float32)
+        out[..., :H] = v
+        return torch.from_numpy(out).cuda()
+    y = make(1, n2, 3)
+    x = make(0, n1, 4)
+    oy = torch.empty((BATCH, n1, hs), device="cuda", dtype=torch.float32)
+    ox = torch.empty((BATCH, n2, hs), device="cuda", dtype=torch.float32)
+    g.upload(stream)
+
+    def step():
+        kps.matvec_A(g, y, oy, BATCH, stream=stream)
+        kps.matvec_AT(g, x, ox, BATCH, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    # per-launch durations (CUDA events on the launching stream)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            a, b, c = evs[i]
+            a.record(stream)
+            kps.matvec_A(g, y, oy, BATCH, stream=stream)
+            b.record(stream)
+            kps.matvec_AT(g, x, ox, BATCH, stream=stream)
+            c.record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    la = [e[0].elapsed_time(e[1]) for e in evs]
+    lt = [e[1].elapsed_time(e[2]) for e in evs]
+    mv_per_step = 2 * BATCH
+    value = mv_per_step * args.steps * world / (ms / 1e3)
+
+    # end to end through the host-buffer entry points (pinned host memory)
+    yh = y.cpu().pin_memory()
+    xh = x.cpu().pin_memory()
+    oyh = torch.empty(oy.shape, dtype=torch.float32).pin_memory()
+    oxh = torch.empty(ox.shape, dtype=torch.float32).pin_memory()
+    ne = max(2, min(args.steps, 5))
+    kps.matvec_A_host(g, yh.data_ptr(), oyh.data_ptr(), BATCH, kps.F32, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        kps.matvec_A_host(g, yh.data_ptr(), oyh.data_ptr(), BATCH, kps.F32, stream)
+        kps.matvec_AT_host(g, xh.data_ptr(), oxh.data_ptr(), BATCH, kps.F32, stream)
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": mv_per_step * ne * world / e2e_dt, "unit": UNIT,
+           "h2d_bytes_per_step": int(yh.numel() * 4 + xh.numel() * 4),
+           "d2h_bytes_per_step": int(oyh.numel() * 4 + oxh.numel() * 4)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = _peaks()
+    alg_bytes = 4.0 * H * (n1 + n2) * BATCH           # read one input, write one output, per vector
+    avg_launch_s = statistics.mean(la + lt) / 1e3
+    achieved = alg_bytes / avg_launch_s / 1e9
+    kh = _kernel_hash()
+    traffic = _traffic(kh)
+    clk_sum = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": BATCH * world, "hands": H,
+                   "sequences": [n1, n2], "terminals": inf["T"],
+                   "l2": "inputs larger than L2 (191 MB per operand, no flush)",
+                   "parallelism": f"dp{world}" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                     "kernel": "pair_scan_kernel", "alg_bytes_per_launch": alg_bytes,
+                     "launch_ms": {"A": statistics.mean(la), "AT": statistics.mean(lt)}},
+        "clocks": clk_sum,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(spec, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * kps.h -- C ABI of the Kronecker payoff-product library for GB300 (sm_103a).
+ *
+ * The library evaluates the payoff-matrix products A*y and A^T*x of a
+ * two-player poker river endgame directly in the Kronecker form of
+ * Farina & Sandholm, "Fast Payoff Matrix Sparsification Techniques for
+ * Structured Extensive-Form Games" (AAAI-22), Prop. 1:
+ *
+ *     A = C (x) F + (Lambda1 W Lambda2) (x) S,
+ *     C[h1,h2] = lambda1[h1] lambda2[h2] (1 - Hx[h1,h2]),
+ *     lambda_i = mu_i / sqrt(beta),
+ *
+ * with F and S the fold and showdown payoffs of the betting skeleton
+ * (Sec. 3), Hx the card-overlap indicator and W the win/lose sign.  The
+ * card blocks are applied in O(hands + cards): the fold block by
+ * inclusion-exclusion over the cards of a hand (the sparsified fold term of
+ * Sec. 4, eq. "cf"), the showdown block by strength-ordered prefix sums with
+ * per-card corrections (the prefix sum is the inverse of the bidiagonal D of
+ * Technique B, Sec. 4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Ownership: the caller owns every vector buffer (device pointers, e.g. a
+ *   torch tensor's data_ptr()).  The library owns the opaque kps_game object
+ *   and the device tables it uploads; kps_game_destroy frees both.
+ * Errors: no C++ exception crosses the ABI.  Every call returns a
+ *   kps_status; kps_last_error() returns a thread-local message describing
+ *   the most recent failure of the calling thread.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *   default stream).  GPU calls are asynchronous on that stream.
+ * Hand order ("library order"): hands sorted by ascending strength, ties
+ *   broken by canonical index.  The canonical order is the deck minus the
+ *   board in increasing card id (card id = rank*suits + suit); one-card hands
+ *   are single cards, two-card hands the pairs (a < b) in lexicographic
+ *   order.  kps_game_hands() returns the cards and canonical index of every
+ *   library-order hand.
+ * Sequence order: depth-first pre-order of the skeleton; when a decision
+ *   node is first reached, its actions receive consecutive sequence ids of
+ *   the acting player in action order: fold, check/call, then aggressive
+ *   actions by increasing amount.  The empty sequence is not stored.
+ * Vector layout: [batch][sequence][hs], hs = H rounded up to a multiple of 8
+ *   (kps_info.hs).  Entries h >= H are ignored on input and written as zero
+ *   on output.  Player-1 vectors have n1 sequences, player-2 vectors n2.
+ */
+#ifndef KPS_H
+#define KPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KPS_OK = 0,
+    KPS_EINVAL = 1,     /* invalid argument or game spec                      */
+    KPS_ENOMEM = 2,     /* host or device allocation failed                   */
+    KPS_ECUDA = 3,      /* a CUDA runtime call failed                         */
+    KPS_ETIMEOUT = 4,   /* a bounded device wait gave up                      */
+    KPS_ENOTSUP = 5,    /* valid input outside what this build supports       */
+    KPS_ENUMERIC = 6    /* NaN/Inf detected                                   */
+} kps_status;
+
+typedef enum {
+    KPS_F32 = 0,        /* storage f32, arithmetic f32                        */
+    KPS_F64 = 1,        /* storage f64, arithmetic f64                        */
+    KPS_BF16 = 2,       /* storage bf16, arithmetic f32                       */
+    KPS_F16 = 3         /* storage f16, arithmetic f32                        */
+} kps_dtype;
+
+#define KPS_MAX_BETS 8
+#define KPS_MAX_BOARD 8
+
+/* River endgame (Sec. 3): board B, stacks, initial pot contributions,
+ * beliefs mu1, mu2 and a fixed betting abstraction (appendix "Betting
+ * abstraction").  Betting rules (appendix "Betting rounds", Fig. 1 caption):
+ *   - player 1 acts first; with equal contributions a player may check or
+ *     bet, facing a larger contribution it may fold, call or raise;
+ *   - a bet/raise of fraction f first matches the opponent and then adds
+ *     f times the pot after matching;
+ *   - an amount at or above the effective stack min(contrib0+stack) is the
+ *     all-in amount and merges with the all-in action;
+ *   - raise_cap limits the aggressive actions of the round (bets, raises
+ *     and all-ins counted together; < 0 = no cap);
+ *   - a call, or a check after a check, ends the round in a showdown.
+ * The payoff of player 1 is +c2 when player 2 folds, -c1 when player 1
+ * folds, and gamma(h1,h2) * min(c1,c2) at a showdown. */
+typedef struct {
+    int32_t ranks, suits;               /* deck = ranks*suits <= 63 cards      */
+    int32_t cards_per_hand;             /* 1 or 2                              */
+    int32_t nboard;
+    int32_t board[KPS_MAX_BOARD];       /* card ids                            */
+    double stack[2];                    /* chips behind at the start           */
+    double contrib0[2];                 /* pot contributions at the start (>0) */
+    int32_t nbet;
+    double bet_frac[KPS_MAX_BETS];      /* > 0                                 */
+    int32_t raise_cap;
+    int32_t allow_allin;
+    const double *mu1, *mu2;            /* beliefs per CANONICAL hand; NULL = 1 */
+    const int32_t *strength;            /* per CANONICAL hand, higher wins     */
+} kps_game_spec;
+
+typedef struct {
+    int32_t H;            /* hands per player (same set for both players)     */
+    int32_t hs;           /* hand stride of the vector layout                 */
+    int32_t n1, n2;       /* sequences of player 1 / player 2                 */
+    int32_t T, T_fold, T_showdown;
+    int32_t ncards;       /* cards left after the board                       */
+    int32_t cards_per_hand;
+    int32_t nodes1, nodes2;       /* decision nodes of each player            */
+    int32_t max_tie;      /* longest run of equal strengths                    */
+    double beta;          /* normalisation of the chance deal pi (Sec. 3)     */
+    double pot0;          /* contrib0[0] + contrib0[1]                        */
+    /* Technique B (Sec. 4) sizes: nnz of A, then Ahat, U, M, V before and
+     * after the postprocessing of Sec. 4. */
+    int64_t nnz_A;
+    int64_t nnz_Ahat, nnz_U, nnz_M, nnz_V;
+    int64_t pp_nnz_Ahat, pp_nnz_U, pp_nnz_M, pp_nnz_V;
+} kps_info;
+
+typedef struct kps_game kps_game;
+
+/* Build a game from its spec on the host (Sec. 3 skeleton, Prop. 1 factor
+ * tables, Technique B counts).  Device tables are uploaded on the first GPU
+ * call (or by kps_game_upload).  *out receives a new object on KPS_OK.
+ * Errors: KPS_EINVAL (bad spec), KPS_ENOMEM, KPS_ENOTSUP (deck > 63 cards). */
+kps_status kps_sparsify(const kps_game_spec *spec, kps_game **out);
+
+/* Free the game and its device tables.  NULL is accepted. */
+kps_status kps_game_destroy(kps_game *game);
+
+/* Sizes and Technique B counts.  Host only. */
+kps_status kps_game_info(const kps_game *game, kps_info *info);
+
+/* Library-order hands: cards[i*k + j] (card ids), canon[i] = canonical
+ * index.  Either pointer may be NULL.  Host only. */
+kps_status kps_game_hands(const kps_game *game, int32_t *cards, int32_t *canon);
+
+/* Sequences of player p (0 or 1): decision-node index, parent sequence of
+ * that node (-1 = empty), action code (0 fold, 1 check/call, 2 aggressive),
+ * contribution after the action; nodes_nact[i] = actions of node i.  Any
+ * pointer may be NULL.  Host only. */
+kps_status kps_game_sequences(const kps_game *game, int32_t player, int32_t *seq_node,
+                              int32_t *seq_parent, int32_t *seq_action,
+                              double *seq_amount, int32_t *nodes_nact);
+
+/* Terminals in depth-first order: last sequence of each player, kind
+ * (0 fold, 1 showdown), folder (-1 for showdowns), contributions.  Any
+ * pointer may be NULL.  Host only. */
+kps_status kps_game_terminals(const kps_game *game, int32_t *s1, int32_t *s2,
+                              int32_t *kind, int32_t *folder, double *c1, double *c2);
+
+/* Upload the device tables now (otherwise done by the first GPU call).
+ * Call it before capturing GPU calls into a CUDA graph. */
+kps_status kps_game_upload(kps_game *game, void *stream);
+
+/* out_b = A * y_b for b < batch (Prop. 1; the gradient of Sec. 2, "First-
+ * order methods").  y: device [batch][n2][hs], out: device [batch][n1][hs],
+ * both of type dt, non-overlapping.  batch >= 0 (0 is a no-op).
+ * Errors: KPS_EINVAL (NULL/size/dtype), KPS_ECUDA (launch failure). */
+kps_status kps_matvec_A(kps_game *game, const void *y, void *out, int32_t batch,
+                        kps_dtype dt, void *stream);
+
+/* out_b = A^T * x_b.  x: device [batch][n1][hs], out: device [batch][n2][hs]. */
+kps_status kps_matvec_AT(kps_game *game, const void *x, void *out, int32_t batch,
+                         kps_dtype dt, void *stream);
+
+/* The same products through host buffers: copies in, computes on the
+ * device, copies out, synchronises `stream`.  Uses library-owned device
+ * staging buffers that grow as needed. */
+kps_status kps_matvec_A_host(kps_game *game, const void *y, void *out, int32_t batch,
+                             kps_dtype dt, void *stream);
+kps_status kps_matvec_AT_host(kps_game *game, const void *x, void *out, int32_t batch,
+                              kps_dtype dt, void *stream);
+
+/* Thread-local description of the last failure ("" if none). */
+const char *kps_last_error(void);
+
+/* Library version string. */
+const char *kps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KPS_H */

@@ -1,0 +1,417 @@
+// C ABI of the Kronecker payoff library (declared in include/kps.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/kps.h"
+#include "game.h"
+#include "kernels.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+kps_status fail(kps_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+kps_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(KPS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Device copies of the per-game tables, one allocation.
+struct DeviceTables {
+    void *blob = nullptr;
+    uint32_t *hinfo = nullptr;
+    float *lam1_f = nullptr, *lam2_f = nullptr;
+    double *lam1_d = nullptr, *lam2_d = nullptr;
+    // per output row: fold / showdown terminal (input sequence, payoff)
+    int *fcol[2] = {nullptr, nullptr}, *scol[2] = {nullptr, nullptr};
+    float *fcoef_f[2] = {nullptr, nullptr}, *scoef_f[2] = {nullptr, nullptr};
+    double *fcoef_d[2] = {nullptr, nullptr}, *scoef_d[2] = {nullptr, nullptr};
+};
+
+}  // namespace
+
+struct kps_game {
+    kps::HostGame host;
+    // per output row of each direction (0 = A, 1 = A^T): terminal pairs
+    std::vector<int> fcol[2], scol[2];
+    std::vector<double> fcoef[2], scoef[2];
+    bool uploaded = false;
+    int device = -1;
+    DeviceTables dev;
+    void *stage_in = nullptr, *stage_out = nullptr;
+    size_t stage_in_bytes = 0, stage_out_bytes = 0;
+};
+
+namespace {
+
+size_t dtype_size(kps_dtype dt) {
+    switch (dt) {
+        case KPS_F32: return 4;
+        case KPS_F64: return 8;
+        case KPS_BF16: return 2;
+        case KPS_F16: return 2;
+        default: return 0;
+    }
+}
+
+// Each output sequence has at most one fold terminal and one showdown
+// terminal as its last action (its own terminating action, or the opponent's
+// fold/call responses to it); split the terminal pair lists accordingly.
+std::string split_rows(kps_game *g) {
+    for (int dir = 0; dir < 2; ++dir) {
+        const kps::PairCsr &csr = dir == 0 ? g->host.csr_A : g->host.csr_AT;
+        const int rows = (int)csr.rowptr.size() - 1;
+        g->fcol[dir].assign(rows, -1);
+        g->scol[dir].assign(rows, -1);
+        g->fcoef[dir].assign(rows, 0.0);
+        g->scoef[dir].assign(rows, 0.0);
+        for (int r = 0; r < rows; ++r)
+            for (int e = csr.rowptr[r]; e < csr.rowptr[r + 1]; ++e) {
+                auto &col = csr.kind[e] == 0 ? g->fcol[dir] : g->scol[dir];
+                auto &coef = csr.kind[e] == 0 ? g->fcoef[dir] : g->scoef[dir];
+                if (col[r] >= 0) return "a sequence ends two terminals of the same kind";
+                col[r] = csr.col[e];
+                coef[r] = csr.coef[e];
+            }
+    }
+    return "";
+}
+
+kps_status upload(kps_game *g, cudaStream_t stream) {
+    if (g->uploaded) {
+        int dev = -1;
+        cudaGetDevice(&dev);
+        if (dev != g->device) return fail(KPS_EINVAL, "game tables live on another device");
+        return KPS_OK;
+    }
+    const kps::HostGame &h = g->host;
+    const int H = h.H;
+    // layout of the blob (8-byte aligned pieces)
+    auto al = [](size_t x) { return (x + 15) / 16 * 16; };
+    size_t off = 0;
+    const size_t o_hinfo = off; off = al(off + 4 * (size_t)H);
+    const size_t o_l1f = off; off = al(off + 4 * (size_t)H);
+    const size_t o_l2f = off; off = al(off + 4 * (size_t)H);
+    const size_t o_l1d = off; off = al(off + 8 * (size_t)H);
+    const size_t o_l2d = off; off = al(off + 8 * (size_t)H);
+    size_t o_fcol[2], o_scol[2], o_ff[2], o_sf[2], o_fd[2], o_sd[2];
+    for (int d = 0; d < 2; ++d) {
+        const size_t r = g->fcol[d].size();
+        o_fcol[d] = off; off = al(off + 4 * r);
+        o_scol[d] = off; off = al(off + 4 * r);
+        o_ff[d] = off; off = al(off + 4 * r);
+        o_sf[d] = off; off = al(off + 4 * r);
+        o_fd[d] = off; off = al(off + 8 * r);
+        o_sd[d] = off; off = al(off + 8 * r);
+    }
+    std::vector<unsigned char> hostblob(off, 0);
+    auto put = [&](size_t o, const void *src, size_t bytes) { if (bytes) std::memcpy(hostblob.data() + o, src, bytes); };
+    put(o_hinfo, h.hinfo.data(), 4 * (size_t)H);
+    std::vector<float> tmp(H);
+    for (int i = 0; i < H; ++i) tmp[i] = (float)h.lam1[i];
+    put(o_l1f, tmp.data(), 4 * (size_t)H);
+    for (int i = 0; i < H; ++i) tmp[i] = (float)h.lam2[i];
+    put(o_l2f, tmp.data(), 4 * (size_t)H);
+    put(o_l1d, h.lam1.data(), 8 * (size_t)H);
+    put(o_l2d, h.lam2.data(), 8 * (size_t)H);
+    for (int d = 0; d < 2; ++d) {
+        const size_t r = g->fcol[d].size();
+        put(o_fcol[d], g->fcol[d].data(), 4 * r);
+        put(o_scol[d], g->scol[d].data(), 4 * r);
+        std::vector<float> f(r), s(r);
+        for (size_t i = 0; i < r; ++i) { f[i] = (float)g->fcoef[d][i]; s[i] = (float)g->scoef[d][i]; }
+        put(o_ff[d], f.data(), 4 * r);
+        put(o_sf[d], s.data(), 4 * r);
+        put(o_fd[d], g->fcoef[d].data(), 8 * r);
+        put(o_sd[d], g->scoef[d].data(), 8 * r);
+    }
+    void *blob = nullptr;
+    cudaError_t e = cudaMalloc(&blob, off);
+    if (e != cudaSuccess) return fail(KPS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    e = cudaMemcpyAsync(blob, hostblob.data(), off, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        cudaFree(blob);
+        return cuda_fail(e, "uploading game tables");
+    }
+    unsigned char *b = static_cast<unsigned char *>(blob);
+    DeviceTables &t = g->dev;
+    t.blob = blob;
+    t.hinfo = reinterpret_cast<uint32_t *>(b + o_hinfo);
+    t.lam1_f = reinterpret_cast<float *>(b + o_l1f);
+    t.lam2_f = reinterpret_cast<float *>(b + o_l2f);
+    t.lam1_d = reinterpret_cast<double *>(b + o_l1d);
+    t.lam2_d = reinterpret_cast<double *>(b + o_l2d);
+    for (int d = 0; d < 2; ++d) {
+        t.fcol[d] = reinterpret_cast<int *>(b + o_fcol[d]);
+        t.scol[d] = reinterpret_cast<int *>(b + o_scol[d]);
+        t.fcoef_f[d] = reinterpret_cast<float *>(b + o_ff[d]);
+        t.scoef_f[d] = reinterpret_cast<float *>(b + o_sf[d]);
+        t.fcoef_d[d] = reinterpret_cast<double *>(b + o_fd[d]);
+        t.scoef_d[d] = reinterpret_cast<double *>(b + o_sd[d]);
+    }
+    cudaGetDevice(&g->device);
+    g->uploaded = true;
+    return KPS_OK;
+}
+
+kps_status matvec(kps_game *g, int dir, const void *vin, void *vout, int32_t batch, kps_dtype dt,
+                  void *stream_ptr) {
+    if (!g) return fail(KPS_EINVAL, "game is NULL");
+    if (batch < 0) return fail(KPS_EINVAL, "batch must be >= 0");
+    if (dtype_size(dt) == 0) return fail(KPS_EINVAL, "unknown dtype");
+    if (batch == 0) return KPS_OK;
+    if (!vin || !vout) return fail(KPS_EINVAL, "vector pointer is NULL");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    kps_status st = upload(g, stream);
+    if (st != KPS_OK) return st;
+    const kps::HostGame &h = g->host;
+    const int n_out = dir == 0 ? h.n[0] : h.n[1];
+    const int n_in = dir == 0 ? h.n[1] : h.n[0];
+    const size_t es = dtype_size(dt);
+    const size_t in_bytes = (size_t)batch * n_in * h.hs * es;
+    const size_t out_bytes = (size_t)batch * n_out * h.hs * es;
+    const char *ci = static_cast<const char *>(vin), *co = static_cast<const char *>(vout);
+    if (ci < co + out_bytes && co < ci + in_bytes) return fail(KPS_EINVAL, "input and output overlap");
+    if ((long long)n_out * batch > 0x7fffffffLL * 32LL) return fail(KPS_ENOTSUP, "too many columns");
+
+    kps::ScanParams p{};
+    p.vin = vin;
+    p.vout = vout;
+    p.H = h.H;
+    p.hs = h.hs;
+    p.nc = h.ncards + 1;
+    p.n_out = n_out;
+    p.n_in = n_in;
+    p.batch = batch;
+    const bool f64 = dt == KPS_F64;
+    const DeviceTables &t = g->dev;
+    p.fcol = t.fcol[dir];
+    p.scol = t.scol[dir];
+    p.fcoef = f64 ? (const void *)t.fcoef_d[dir] : (const void *)t.fcoef_f[dir];
+    p.scoef = f64 ? (const void *)t.scoef_d[dir] : (const void *)t.scoef_f[dir];
+    p.hinfo = t.hinfo;
+    const void *l1 = f64 ? (const void *)t.lam1_d : (const void *)t.lam1_f;
+    const void *l2 = f64 ? (const void *)t.lam2_d : (const void *)t.lam2_f;
+    p.lam_in = dir == 0 ? l2 : l1;
+    p.lam_out = dir == 0 ? l1 : l2;
+    const int storage = dt == KPS_F32 ? kps::kStoreF32 : dt == KPS_F64 ? kps::kStoreF64
+                        : dt == KPS_BF16 ? kps::kStoreBF16 : kps::kStoreF16;
+    // as many hand chunks (warps) as shared memory allows
+    const int smem_max = kps::max_dyn_smem();
+    bool pin = true;
+    int nw = 0;
+    for (int w = kps::kMaxWarps; w >= 1; --w)
+        if (kps::scan_smem_bytes(storage, h.H, p.nc, w, true) <= (size_t)smem_max) { nw = w; break; }
+    if (nw == 0) {
+        if (storage != kps::kStoreF32 && storage != kps::kStoreF64)
+            return fail(KPS_ENOTSUP, "hand count too large for half-precision storage");
+        pin = false;
+        for (int w = kps::kMaxWarps; w >= 1; --w)
+            if (kps::scan_smem_bytes(storage, h.H, p.nc, w, false) <= (size_t)smem_max) { nw = w; break; }
+        if (nw == 0) return fail(KPS_ENOTSUP, "card count too large for shared memory");
+    }
+    nw = std::min(nw, std::max(1, h.H));
+    p.nw = nw;
+    std::vector<int> cb = kps::chunk_bounds(h, nw);
+    for (int i = 0; i <= nw; ++i) p.chunk[i] = cb[i];
+    cudaError_t e = kps::launch_pair_scan(p, storage, h.k, pin, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the payoff scan");
+    return KPS_OK;
+}
+
+kps_status matvec_host(kps_game *g, int dir, const void *vin, void *vout, int32_t batch, kps_dtype dt,
+                       void *stream_ptr) {
+    if (!g) return fail(KPS_EINVAL, "game is NULL");
+    if (batch < 0) return fail(KPS_EINVAL, "batch must be >= 0");
+    if (dtype_size(dt) == 0) return fail(KPS_EINVAL, "unknown dtype");
+    if (batch == 0) return KPS_OK;
+    if (!vin || !vout) return fail(KPS_EINVAL, "vector pointer is NULL");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    const kps::HostGame &h = g->host;
+    const int n_out = dir == 0 ? h.n[0] : h.n[1];
+    const int n_in = dir == 0 ? h.n[1] : h.n[0];
+    const size_t es = dtype_size(dt);
+    const size_t in_bytes = (size_t)batch * n_in * h.hs * es;
+    const size_t out_bytes = (size_t)batch * n_out * h.hs * es;
+    cudaError_t e;
+    if (g->stage_in_bytes < in_bytes) {
+        if (g->stage_in) cudaFree(g->stage_in);
+        g->stage_in = nullptr;
+        g->stage_in_bytes = 0;
+        e = cudaMalloc(&g->stage_in, in_bytes);
+        if (e != cudaSuccess) return fail(KPS_ENOMEM, "staging buffer");
+        g->stage_in_bytes = in_bytes;
+    }
+    if (g->stage_out_bytes < out_bytes) {
+        if (g->stage_out) cudaFree(g->stage_out);
+        g->stage_out = nullptr;
+        g->stage_out_bytes = 0;
+        e = cudaMalloc(&g->stage_out, out_bytes);
+        if (e != cudaSuccess) return fail(KPS_ENOMEM, "staging buffer");
+        g->stage_out_bytes = out_bytes;
+    }
+    e = cudaMemcpyAsync(g->stage_in, vin, in_bytes, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copying input to the device");
+    kps_status st = matvec(g, dir, g->stage_in, g->stage_out, batch, dt, stream_ptr);
+    if (st != KPS_OK) return st;
+    e = cudaMemcpyAsync(vout, g->stage_out, out_bytes, cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copying output to the host");
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronising");
+    return KPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kps_status kps_sparsify(const kps_game_spec *spec, kps_game **out) {
+    if (!out) return fail(KPS_EINVAL, "out is NULL");
+    *out = nullptr;
+    kps_game *g = new (std::nothrow) kps_game();
+    if (!g) return fail(KPS_ENOMEM, "host allocation");
+    try {
+        kps_status code = KPS_OK;
+        std::string err = kps::build_game(spec, g->host, &code);
+        if (err.empty()) err = split_rows(g), code = err.empty() ? KPS_OK : KPS_ENOTSUP;
+        if (!err.empty()) {
+            delete g;
+            return fail(code, err);
+        }
+    } catch (const std::bad_alloc &) {
+        delete g;
+        return fail(KPS_ENOMEM, "host allocation");
+    } catch (...) {
+        delete g;
+        return fail(KPS_EINVAL, "unexpected failure while building the game");
+    }
+    *out = g;
+    g_last_error.clear();
+    return KPS_OK;
+}
+
+kps_status kps_game_destroy(kps_game *g) {
+    if (!g) return KPS_OK;
+    if (g->dev.blob) cudaFree(g->dev.blob);
+    if (g->stage_in) cudaFree(g->stage_in);
+    if (g->stage_out) cudaFree(g->stage_out);
+    delete g;
+    return KPS_OK;
+}
+
+kps_status kps_game_info(const kps_game *cg, kps_info *info) {
+    if (!cg || !info) return fail(KPS_EINVAL, "NULL argument");
+    kps_game *g = const_cast<kps_game *>(cg);
+    try {
+        kps::technique_b_counts(g->host);
+    } catch (...) {
+        return fail(KPS_ENOMEM, "counting Technique B sizes");
+    }
+    const kps::HostGame &h = g->host;
+    std::memset(info, 0, sizeof(*info));
+    info->H = h.H;
+    info->hs = h.hs;
+    info->n1 = h.n[0];
+    info->n2 = h.n[1];
+    info->T = h.T;
+    info->T_fold = h.TF;
+    info->T_showdown = h.TS;
+    info->ncards = h.ncards;
+    info->cards_per_hand = h.k;
+    info->nodes1 = h.nodes[0];
+    info->nodes2 = h.nodes[1];
+    info->max_tie = h.max_tie;
+    info->beta = h.beta;
+    info->pot0 = h.pot0;
+    info->nnz_A = h.counts[0];
+    info->nnz_Ahat = h.counts[1];
+    info->nnz_U = h.counts[2];
+    info->nnz_M = h.counts[3];
+    info->nnz_V = h.counts[4];
+    info->pp_nnz_Ahat = h.counts[5];
+    info->pp_nnz_U = h.counts[6];
+    info->pp_nnz_M = h.counts[7];
+    info->pp_nnz_V = h.counts[8];
+    return KPS_OK;
+}
+
+kps_status kps_game_hands(const kps_game *g, int32_t *cards, int32_t *canon) {
+    if (!g) return fail(KPS_EINVAL, "game is NULL");
+    const kps::HostGame &h = g->host;
+    for (int p = 0; p < h.H; ++p) {
+        if (cards)
+            for (int j = 0; j < h.k; ++j) cards[p * h.k + j] = h.slot_card[h.hand_slots[2 * p + j]];
+        if (canon) canon[p] = h.canon[p];
+    }
+    return KPS_OK;
+}
+
+kps_status kps_game_sequences(const kps_game *g, int32_t player, int32_t *seq_node, int32_t *seq_parent,
+                              int32_t *seq_action, double *seq_amount, int32_t *nodes_nact) {
+    if (!g) return fail(KPS_EINVAL, "game is NULL");
+    if (player != 0 && player != 1) return fail(KPS_EINVAL, "player must be 0 or 1");
+    const kps::HostGame &h = g->host;
+    const auto &sq = h.seqs[player];
+    for (size_t s = 0; s < sq.size(); ++s) {
+        if (seq_node) seq_node[s] = sq[s].node;
+        if (seq_parent) seq_parent[s] = sq[s].parent;
+        if (seq_action) seq_action[s] = sq[s].action;
+        if (seq_amount) seq_amount[s] = sq[s].amount;
+    }
+    if (nodes_nact)
+        for (size_t i = 0; i < h.nodes_nact[player].size(); ++i) nodes_nact[i] = h.nodes_nact[player][i];
+    return KPS_OK;
+}
+
+kps_status kps_game_terminals(const kps_game *g, int32_t *s1, int32_t *s2, int32_t *kind, int32_t *folder,
+                              double *c1, double *c2) {
+    if (!g) return fail(KPS_EINVAL, "game is NULL");
+    const auto &ts = g->host.terms;
+    for (size_t t = 0; t < ts.size(); ++t) {
+        if (s1) s1[t] = ts[t].s1;
+        if (s2) s2[t] = ts[t].s2;
+        if (kind) kind[t] = ts[t].kind;
+        if (folder) folder[t] = ts[t].folder;
+        if (c1) c1[t] = ts[t].c1;
+        if (c2) c2[t] = ts[t].c2;
+    }
+    return KPS_OK;
+}
+
+kps_status kps_game_upload(kps_game *g, void *stream) {
+    if (!g) return fail(KPS_EINVAL, "game is NULL");
+    return upload(g, static_cast<cudaStream_t>(stream));
+}
+
+kps_status kps_matvec_A(kps_game *g, const void *y, void *out, int32_t batch, kps_dtype dt, void *stream) {
+    return matvec(g, 0, y, out, batch, dt, stream);
+}
+
+kps_status kps_matvec_AT(kps_game *g, const void *x, void *out, int32_t batch, kps_dtype dt, void *stream) {
+    return matvec(g, 1, x, out, batch, dt, stream);
+}
+
+kps_status kps_matvec_A_host(kps_game *g, const void *y, void *out, int32_t batch, kps_dtype dt,
+                             void *stream) {
+    return matvec_host(g, 0, y, out, batch, dt, stream);
+}
+
+kps_status kps_matvec_AT_host(kps_game *g, const void *x, void *out, int32_t batch, kps_dtype dt,
+                              void *stream) {
+    return matvec_host(g, 1, x, out, batch, dt, stream);
+}
+
+const char *kps_last_error(void) { return g_last_error.c_str(); }
+
+const char *kps_version(void) { return "kps 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,42 @@
+// Device-side entry points of the Kronecker payoff library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace kps {
+
+constexpr int kMaxWarps = 8;     // warps (= hand chunks) per CTA
+constexpr int kColsPerCta = 32;  // one output column per lane
+
+// One direction (A or A^T) of the product for one game.
+//
+// Output column j of the CTA (lane j) is (sigma, b) with
+//   sigma = col / batch, b = col % batch, col = blockIdx.x * 32 + j.
+// Its terminal pairs are at most one fold terminal (input sequence fcol,
+// payoff fcoef) and one showdown terminal (scol, scoef); -1 = absent.
+struct ScanParams {
+    const void *vin;             // [batch][n_in][hs]
+    void *vout;                  // [batch][n_out][hs]
+    int H, hs, nc;               // nc = per-card table rows (cards left + 1)
+    int n_out, n_in, batch;
+    const int *fcol, *scol;      // [n_out]
+    const void *fcoef, *scoef;   // [n_out], compute type
+    const uint32_t *hinfo;       // [H]
+    const void *lam_in, *lam_out;  // [H], compute type
+    int nw;                      // warps per CTA = hand chunks
+    int chunk[kMaxWarps + 1];    // chunk boundaries (tie-group aligned)
+};
+
+enum StorageType { kStoreF32 = 0, kStoreF64 = 1, kStoreBF16 = 2, kStoreF16 = 3 };
+
+// Bytes of dynamic shared memory the scan kernel needs.
+size_t scan_smem_bytes(int storage, int H, int nc, int nw, bool partial_in_smem);
+
+// Largest dynamic shared memory per block on the current device.
+int max_dyn_smem();
+
+cudaError_t launch_pair_scan(const ScanParams &p, int storage, int cards_per_hand,
+                             bool partial_in_smem, cudaStream_t stream);
+
+}  // namespace kps

@@ -1,0 +1,244 @@
+"""Python binding of the C ABI in ``include/kps.h`` (argument marshalling only).
+
+Every computation runs in ``libkps.so``; this module converts Python values
+to the C structs and pointers the ABI takes.  Vector arguments may be torch
+tensors (their ``data_ptr()`` is passed) or raw integer addresses.  The
+library must have been built (``paper_2112_03804_gb300.build.build()``);
+importing the binding without it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkps.so")
+
+MAX_BETS = 8
+MAX_BOARD = 8
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP, ENUMERIC = range(7)
+F32, F64, BF16, F16 = 0, 1, 2, 3
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTSUP", 6: "ENUMERIC"}
+
+
+class KpsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GameSpec(C.Structure):
+    _fields_ = [("ranks", C.c_int32), ("suits", C.c_int32), ("cards_per_hand", C.c_int32),
+                ("nboard", C.c_int32), ("board", C.c_int32 * MAX_BOARD),
+                ("stack", C.c_double * 2), ("contrib0", C.c_double * 2),
+                ("nbet", C.c_int32), ("bet_frac", C.c_double * MAX_BETS),
+                ("raise_cap", C.c_int32), ("allow_allin", C.c_int32),
+                ("mu1", C.POINTER(C.c_double)), ("mu2", C.POINTER(C.c_double)),
+                ("strength", C.POINTER(C.c_int32))]
+
+
+class Info(C.Structure):
+    _fields_ = [("H", C.c_int32), ("hs", C.c_int32), ("n1", C.c_int32), ("n2", C.c_int32),
+                ("T", C.c_int32), ("T_fold", C.c_int32), ("T_showdown", C.c_int32),
+                ("ncards", C.c_int32), ("cards_per_hand", C.c_int32),
+                ("nodes1", C.c_int32), ("nodes2", C.c_int32), ("max_tie", C.c_int32),
+                ("beta", C.c_double), ("pot0", C.c_double),
+                ("nnz_A", C.c_int64), ("nnz_Ahat", C.c_int64), ("nnz_U", C.c_int64),
+                ("nnz_M", C.c_int64), ("nnz_V", C.c_int64), ("pp_nnz_Ahat", C.c_int64),
+                ("pp_nnz_U", C.c_int64), ("pp_nnz_M", C.c_int64), ("pp_nnz_V", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTED = ["kps_sparsify", "kps_game_destroy", "kps_game_info", "kps_game_hands",
+            "kps_game_sequences", "kps_game_terminals", "kps_game_upload",
+            "kps_matvec_A", "kps_matvec_AT", "kps_matvec_A_host", "kps_matvec_AT_host",
+            "kps_last_error", "kps_version"]
+
+_lib = None
+
+
+def lib():
+    """Load libkps.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2112_03804_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.kps_sparsify.argtypes = [C.POINTER(GameSpec), C.POINTER(C.c_void_p)]
+        L.kps_game_destroy.argtypes = [P]
+        L.kps_game_info.argtypes = [P, C.POINTER(Info)]
+        L.kps_game_hands.argtypes = [P, P, P]
+        L.kps_game_sequences.argtypes = [P, C.c_int32, P, P, P, P, P]
+        L.kps_game_terminals.argtypes = [P, P, P, P, P, P, P]
+        L.kps_game_upload.argtypes = [P, P]
+        for f in (L.kps_matvec_A, L.kps_matvec_AT, L.kps_matvec_A_host, L.kps_matvec_AT_host):
+            f.argtypes = [P, P, P, C.c_int32, C.c_int, P]
+        for name in EXPORTED:
+            if name not in ("kps_last_error", "kps_version"):
+                getattr(L, name).restype = C.c_int
+        L.kps_last_error.restype = C.c_char_p
+        L.kps_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise KpsError(status, lib().kps_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    raise TypeError(f"cannot pass {type(a)} as a pointer")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+_TORCH_DT = {}
+
+
+def _dtype_code(t, dtype):
+    if dtype is not None:
+        return dtype
+    import torch
+    m = {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16, torch.float16: F16}
+    return m[t.dtype]
+
+
+class Game:
+    """A river endgame built by ``kps_sparsify`` (see ``include/kps.h``)."""
+
+    def __init__(self, spec: dict):
+        s = GameSpec()
+        s.ranks, s.suits = int(spec["ranks"]), int(spec["suits"])
+        s.cards_per_hand = int(spec["cards_per_hand"])
+        board = list(spec.get("board", []))
+        if len(board) > MAX_BOARD:
+            raise ValueError("board too long")
+        s.nboard = len(board)
+        for i, c in enumerate(board):
+            s.board[i] = int(c)
+        s.stack[0], s.stack[1] = [float(v) for v in spec["stack"]]
+        s.contrib0[0], s.contrib0[1] = [float(v) for v in spec["contrib0"]]
+        fr = list(spec.get("bet_frac", []))
+        if len(fr) > MAX_BETS:
+            raise ValueError("too many bet sizes")
+        s.nbet = len(fr)
+        for i, f in enumerate(fr):
+            s.bet_frac[i] = float(f)
+        s.raise_cap = int(spec.get("raise_cap", -1))
+        s.allow_allin = 1 if spec.get("allow_allin", False) else 0
+        self._strength = np.ascontiguousarray(spec["strength"], dtype=np.int32)
+        mu1, mu2 = spec.get("mu1"), spec.get("mu2")
+        self._mu1 = None if mu1 is None else np.ascontiguousarray(mu1, dtype=np.float64)
+        self._mu2 = None if mu2 is None else np.ascontiguousarray(mu2, dtype=np.float64)
+        s.strength = self._strength.ctypes.data_as(C.POINTER(C.c_int32))
+        s.mu1 = self._mu1.ctypes.data_as(C.POINTER(C.c_double)) if self._mu1 is not None else None
+        s.mu2 = self._mu2.ctypes.data_as(C.POINTER(C.c_double)) if self._mu2 is not None else None
+        h = C.c_void_p()
+        _check(lib().kps_sparsify(C.byref(s), C.byref(h)))
+        self._h = h
+        self._info = None
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().kps_game_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        if self._info is None:
+            i = Info()
+            _check(lib().kps_game_info(self._h, C.byref(i)))
+            self._info = i.as_dict()
+        return self._info
+
+    def hands(self):
+        inf = self.info()
+        cards = np.zeros(inf["H"] * inf["cards_per_hand"], dtype=np.int32)
+        canon = np.zeros(inf["H"], dtype=np.int32)
+        _check(lib().kps_game_hands(self._h, cards.ctypes.data, canon.ctypes.data))
+        return cards.reshape(inf["H"], inf["cards_per_hand"]), canon
+
+    def sequences(self, player: int) -> dict:
+        inf = self.info()
+        n = inf["n1"] if player == 0 else inf["n2"]
+        nn = inf["nodes1"] if player == 0 else inf["nodes2"]
+        node, parent, action = (np.zeros(n, np.int32) for _ in range(3))
+        amount = np.zeros(n)
+        nact = np.zeros(nn, np.int32)
+        _check(lib().kps_game_sequences(self._h, player, node.ctypes.data, parent.ctypes.data,
+                                        action.ctypes.data, amount.ctypes.data, nact.ctypes.data))
+        return dict(node=node, parent=parent, action=action, amount=amount, nact=nact)
+
+    def terminals(self) -> dict:
+        T = self.info()["T"]
+        s1, s2, kind, folder = (np.zeros(T, np.int32) for _ in range(4))
+        c1, c2 = np.zeros(T), np.zeros(T)
+        _check(lib().kps_game_terminals(self._h, s1.ctypes.data, s2.ctypes.data, kind.ctypes.data,
+                                        folder.ctypes.data, c1.ctypes.data, c2.ctypes.data))
+        return dict(s1=s1, s2=s2, kind=kind, folder=folder, c1=c1, c2=c2)
+
+    def upload(self, stream=None):
+        _check(lib().kps_game_upload(self._h, _stream(stream)))
+
+
+def sparsify(spec: dict) -> Game:
+    return Game(spec)
+
+
+def matvec_A(game: Game, y, out, batch: int, dtype=None, stream=None):
+    """out[b] = A y[b]; y [batch][n2][hs], out [batch][n1][hs] on the device."""
+    _check(lib().kps_matvec_A(game._h, _ptr(y), _ptr(out), int(batch), _dtype_code(y, dtype), _stream(stream)))
+
+
+def matvec_AT(game: Game, x, out, batch: int, dtype=None, stream=None):
+    """out[b] = A^T x[b]; x [batch][n1][hs], out [batch][n2][hs] on the device."""
+    _check(lib().kps_matvec_AT(game._h, _ptr(x), _ptr(out), int(batch), _dtype_code(x, dtype), _stream(stream)))
+
+
+def matvec_A_host(game: Game, y, out, batch: int, dtype: int, stream=None):
+    """Same as matvec_A with host buffers (copies inside, synchronous)."""
+    _check(lib().kps_matvec_A_host(game._h, _ptr(y), _ptr(out), int(batch), dtype, _stream(stream)))
+
+
+def matvec_AT_host(game: Game, x, out, batch: int, dtype: int, stream=None):
+    _check(lib().kps_matvec_AT_host(game._h, _ptr(x), _ptr(out), int(batch), dtype, _stream(stream)))
+
+
+def version() -> str:
+    return lib().kps_version().decode()
