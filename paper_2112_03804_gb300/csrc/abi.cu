@@ -2,7 +2,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -48,6 +50,15 @@ struct kps_game {
     DeviceTables dev;
     void *stage_in = nullptr, *stage_out = nullptr;
     size_t stage_in_bytes = 0, stage_out_bytes = 0;
+    // tie-aligned tile lists on the device, per warp count
+    struct Tiles {
+        int2 *dev = nullptr;
+        std::vector<int> tchunk;
+    };
+    std::map<int, Tiles> tiles;
+    // FP32 partial results for half-precision outputs
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
 };
 
 namespace {
@@ -163,6 +174,87 @@ kps_status upload(kps_game *g, cudaStream_t stream) {
     return KPS_OK;
 }
 
+// Warps per CTA of the fast path: two CTAs of 4 warps per SM when they fit
+// (smaller CTAs shorten the tail of the last wave), else the largest count
+// that fits.  KPS_WARPS overrides the choice (1..8).
+int fast_warps(int storage, int nc, int H) {
+    const int smem_max = kps::max_dyn_smem();
+    int nw = 0;
+    if (const char *env = std::getenv("KPS_WARPS")) nw = std::atoi(env);
+    if (nw < 1 || nw > kps::kMaxWarps || kps::fast_smem_bytes(storage, nc, nw) > (size_t)smem_max) {
+        nw = 0;
+        if (2 * (kps::fast_smem_bytes(storage, nc, 4) + 1024) <= (size_t)smem_max + 1024) nw = 4;
+        else
+            for (int w = kps::kMaxWarps; w >= 1; --w)
+                if (kps::fast_smem_bytes(storage, nc, w) <= (size_t)smem_max) { nw = w; break; }
+    }
+    return std::max(1, std::min(nw, (H + kps::kTile - 1) / kps::kTile));
+}
+
+kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int storage, kps_dtype dt,
+                       cudaStream_t stream) {
+    const kps::HostGame &h = g->host;
+    const int nw = fast_warps(storage, sp.nc, h.H);
+    if (kps::fast_smem_bytes(storage, sp.nc, nw) > (size_t)kps::max_dyn_smem())
+        return fail(KPS_ENOTSUP, "card count too large for shared memory");
+    auto it = g->tiles.find(nw);
+    if (it == g->tiles.end()) {
+        kps_game::Tiles t;
+        std::vector<std::pair<int, int>> tl = kps::tie_tiles(h, nw, kps::kTile, t.tchunk);
+        std::vector<int2> host(tl.size());
+        for (size_t i = 0; i < tl.size(); ++i) host[i] = make_int2(tl[i].first, tl[i].second);
+        cudaError_t e = cudaMalloc(&t.dev, std::max<size_t>(1, host.size()) * sizeof(int2));
+        if (e != cudaSuccess) return fail(KPS_ENOMEM, "tile table");
+        if (!host.empty()) {
+            e = cudaMemcpyAsync(t.dev, host.data(), host.size() * sizeof(int2), cudaMemcpyHostToDevice, stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) {
+                cudaFree(t.dev);
+                return cuda_fail(e, "uploading the tile table");
+            }
+        }
+        it = g->tiles.emplace(nw, std::move(t)).first;
+    }
+    void *scratch = sp.vout;
+    if (storage == kps::kStoreBF16 || storage == kps::kStoreF16) {
+        const size_t need = (size_t)sp.batch * sp.n_out * h.hs * sizeof(float);
+        if (g->scratch_bytes < need) {
+            if (g->scratch) cudaFree(g->scratch);
+            g->scratch = nullptr;
+            g->scratch_bytes = 0;
+            cudaError_t e = cudaMalloc(&g->scratch, need);
+            if (e != cudaSuccess) return fail(KPS_ENOMEM, "partial-result buffer");
+            g->scratch_bytes = need;
+        }
+        scratch = g->scratch;
+    }
+    kps::FastParams p{};
+    p.vin = sp.vin;
+    p.vout = sp.vout;
+    p.scratch = scratch;
+    p.H = sp.H;
+    p.hs = sp.hs;
+    p.nc = sp.nc;
+    p.n_out = sp.n_out;
+    p.n_in = sp.n_in;
+    p.batch = sp.batch;
+    p.fcol = sp.fcol;
+    p.scol = sp.scol;
+    p.fcoef = sp.fcoef;
+    p.scoef = sp.scoef;
+    p.hinfo = sp.hinfo;
+    p.lam_in = sp.lam_in;
+    p.lam_out = sp.lam_out;
+    p.tiles = it->second.dev;
+    p.nw = nw;
+    for (int i = 0; i <= nw; ++i) p.tchunk[i] = it->second.tchunk[i];
+    (void)dir;
+    (void)dt;
+    cudaError_t e = kps::launch_fast_scan(p, storage, h.k, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the payoff scan");
+    return KPS_OK;
+}
+
 kps_status matvec(kps_game *g, int dir, const void *vin, void *vout, int32_t batch, kps_dtype dt,
                   void *stream_ptr) {
     if (!g) return fail(KPS_EINVAL, "game is NULL");
@@ -205,7 +297,8 @@ kps_status matvec(kps_game *g, int dir, const void *vin, void *vout, int32_t bat
     p.lam_out = dir == 0 ? l1 : l2;
     const int storage = dt == KPS_F32 ? kps::kStoreF32 : dt == KPS_F64 ? kps::kStoreF64
                         : dt == KPS_BF16 ? kps::kStoreBF16 : kps::kStoreF16;
-    // as many hand chunks (warps) as shared memory allows
+    if (h.max_tie <= kps::kTile) return matvec_fast(g, dir, p, storage, dt, stream);
+    // general path: as many hand chunks (warps) as shared memory allows
     const int smem_max = kps::max_dyn_smem();
     bool pin = true;
     int nw = 0;
@@ -304,6 +397,8 @@ kps_status kps_game_destroy(kps_game *g) {
     if (g->dev.blob) cudaFree(g->dev.blob);
     if (g->stage_in) cudaFree(g->stage_in);
     if (g->stage_out) cudaFree(g->stage_out);
+    if (g->scratch) cudaFree(g->scratch);
+    for (auto &kv : g->tiles) cudaFree(kv.second.dev);
     delete g;
     return KPS_OK;
 }

@@ -278,6 +278,15 @@ std::string build_hands(HostGame &g, const double *mu1_canon, const double *mu2_
         }
         lo = hi + 1;
     }
+    for (int p = 0; p + 1 < g.H; ++p) {
+        const bool untied = g.group_lo[p] == g.group_hi[p] && g.group_lo[p + 1] == g.group_hi[p + 1];
+        bool disjoint = true;
+        for (int i = 0; i < g.k; ++i)
+            for (int j = 0; j < g.k; ++j)
+                if (g.hand_slots[2 * p + i] == g.hand_slots[2 * (p + 1) + j]) disjoint = false;
+        if (untied && disjoint) g.hinfo[p] |= 1u << 14;
+        if (disjoint) g.hinfo[p] |= 1u << 15;
+    }
     if (g.max_tie > 65535) return "tie group too long";
     return "";
 }
@@ -316,6 +325,26 @@ std::vector<int> chunk_bounds(const HostGame &g, int parts) {
     }
     b[parts] = g.H;
     return b;
+}
+
+std::vector<std::pair<int, int>> tie_tiles(const HostGame &g, int parts, int tile,
+                                           std::vector<int> &tchunk) {
+    std::vector<int> cb = chunk_bounds(g, parts);
+    std::vector<std::pair<int, int>> tiles;
+    tchunk.assign(parts + 1, 0);
+    for (int k = 0; k < parts; ++k) {
+        tchunk[k] = (int)tiles.size();
+        int s = cb[k];
+        while (s < cb[k + 1]) {
+            int e = std::min(s + tile, cb[k + 1]);
+            // back off to a tie-group boundary unless the tile ends the chunk
+            if (e < cb[k + 1] && g.group_lo[e] > s) e = g.group_lo[e];
+            tiles.emplace_back(s, e - s);
+            s = e;
+        }
+    }
+    tchunk[parts] = (int)tiles.size();
+    return tiles;
 }
 
 // Sizes of Technique B, counted from the structure of its factors:

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/kps.h"
@@ -39,6 +40,9 @@ struct PairCsr {
 //   bits 6-11  slot of the second card (== ncards for one-card hands)
 //   bit  12    member of a tie group of length >= 2
 //   bit  13    last member of such a group
+//   bit  14    this hand and the next are both untied and share no card, so
+//              a scan may update their per-card sums together
+//   bit  15    this hand and the next share no card (ties allowed)
 //   bits 16-31 offset of the hand inside its tie group
 inline uint32_t pack_hinfo(int a, int b, bool tied, bool last, int off) {
     return (uint32_t)a | ((uint32_t)b << 6) | ((uint32_t)tied << 12) | ((uint32_t)last << 13) |
@@ -82,5 +86,11 @@ void technique_b_counts(HostGame &g);
 // Split [0, H) into `parts` contiguous chunks whose boundaries fall on tie
 // group boundaries.  Returns parts+1 offsets (some chunks may be empty).
 std::vector<int> chunk_bounds(const HostGame &g, int parts);
+
+// Tiles of at most `tile` hands inside each chunk, never splitting a tie
+// group (requires max_tie <= tile).  Returns (start, length) pairs; tchunk
+// receives parts+1 offsets into the tile list.
+std::vector<std::pair<int, int>> tie_tiles(const HostGame &g, int parts, int tile,
+                                           std::vector<int> &tchunk);
 
 }  // namespace kps

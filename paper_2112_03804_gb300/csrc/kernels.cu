@@ -138,6 +138,21 @@ pair_scan_kernel(const ScanParams p) {
     }
     const bool has_f = __syncthreads_or(kinds & 1) != 0;   // also publishes L.ci
     const bool has_s = __syncthreads_or(kinds & 2) != 0;
+    // Common case: the CTA's valid columns share one output sequence and
+    // take consecutive batch vectors, so input addresses are arithmetic.
+    const ColInfo c0i = L.ci[0];
+    int same = 1, nvalid_l = 0;
+    if (threadIdx.x < 32) {
+        const ColInfo c = L.ci[threadIdx.x];
+        if (c.out_off >= 0) {
+            nvalid_l = 1;
+            same = c.foff == c0i.foff && c.soff == c0i.soff &&
+                   c.in_off == c0i.in_off + (long long)threadIdx.x * p.n_in * p.hs;
+        }
+    }
+    const bool uni = __syncthreads_and(same) != 0;
+    const int nvalid = __syncthreads_count(nvalid_l);
+    const long long ustride = (long long)p.n_in * p.hs;
 
     C *Rv = L.tables + warp * L.per_warp;     // running per-card mass of v
     C *Rw = Rv + (size_t)nc * 32;             // per-card totals of w = u - v
@@ -168,78 +183,152 @@ pair_scan_kernel(const ScanParams p) {
     // ---- phase 1: chunk-local scan
     const int c0 = p.chunk[warp], c1 = p.chunk[warp + 1];
     C Gv = C(0), Gw = C(0), Pg = C(0);
+    // Inputs of the next 32-hand tile, lane = hand, one register per column:
+    // issued before the current tile is scanned so that DRAM latency overlaps
+    // the scan.
+    C xf[32], xs[32];
+    C lin_next = C(0);
+    uint32_t h_next = 0u;
+    auto fetch = [&](int t0) {
+        const int pos = t0 + lane;
+        const bool pin = pos < c1;
+        lin_next = pin ? lam_in[pos] : C(0);
+        h_next = pin ? __ldg(&p.hinfo[pos]) : 0u;
+        if (uni) {
+            const S *fb = vin + c0i.in_off + pos + c0i.foff;
+            const S *sb = vin + c0i.in_off + pos + c0i.soff;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                const bool ok = pin && jj < nvalid;
+                xf[jj] = (ok && c0i.foff >= 0) ? Store<S>::load(fb + jj * ustride) : C(0);
+                xs[jj] = (ok && c0i.soff >= 0) ? Store<S>::load(sb + jj * ustride) : C(0);
+            }
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                const ColInfo cj = L.ci[jj];
+                const S *base = vin + cj.in_off + pos;
+                xf[jj] = (pin && cj.foff >= 0) ? Store<S>::load(base + cj.foff) : C(0);
+                xs[jj] = (pin && cj.soff >= 0) ? Store<S>::load(base + cj.soff) : C(0);
+            }
+        }
+    };
+    // One hand of the scan (single step, ties deferred to the group end).
+    auto step1 = [&](int i, uint32_t hi, int q) {
+        const int ca = hi & 63, cb = (hi >> 6) & 63;
+        const C u = fco * stf[i * kPad + lane];
+        const C v = sco * sts[i * kPad + lane];
+        const C w = u - v;
+        if (has_s) {
+            const C ra = Rv[ca * 32 + lane];
+            const C rb = K2 == 2 ? Rv[cb * 32 + lane] : C(0);
+            const C lo = Gv - ra - rb;                  // compatible, strictly weaker
+            if (!(hi & (1u << 12))) {
+                Pref(q) = (K2 == 2 ? w : C(0)) + C(2) * lo;
+                Rv[ca * 32 + lane] = ra + v;
+                if (K2 == 2) Rv[cb * 32 + lane] = rb + v;
+                Gv += v;
+            } else {
+                // tie group: updates wait until its last member
+                Pref(q) = (K2 == 2 ? w + v : C(0)) + C(2) * lo;
+                Pc[ca * 32 + lane] += v;
+                if (K2 == 2) Pc[cb * 32 + lane] += v;
+                Pg += v;
+                if (hi & (1u << 13)) {
+                    const int q0 = q - (int)(hi >> 16);
+                    // compatible equal-strength mass, by inclusion-exclusion
+                    for (int r = q0; r <= q; ++r) {
+                        const uint32_t hr = __ldg(&p.hinfo[r]);
+                        C t = Pg - Pc[(hr & 63) * 32 + lane];
+                        if (K2 == 2) t -= Pc[((hr >> 6) & 63) * 32 + lane];
+                        Pref(r) += t;
+                    }
+                    for (int r = q0; r <= q; ++r) {
+                        const uint32_t hr = __ldg(&p.hinfo[r]);
+                        const int a = hr & 63;
+                        Rv[a * 32 + lane] += Pc[a * 32 + lane];
+                        Pc[a * 32 + lane] = C(0);
+                        if (K2 == 2) {
+                            const int b = (hr >> 6) & 63;
+                            Rv[b * 32 + lane] += Pc[b * 32 + lane];
+                            Pc[b * 32 + lane] = C(0);
+                        }
+                    }
+                    Gv += Pg;
+                    Pg = C(0);
+                }
+            }
+        } else {
+            Pref(q) = K2 == 2 ? w : C(0);
+        }
+        if (has_f) {
+            Rw[ca * 32 + lane] += w;
+            if (K2 == 2) Rw[cb * 32 + lane] += w;
+            Gw += w;
+        }
+    };
+    // Two consecutive untied hands with disjoint cards: all per-card loads
+    // are independent, so they are issued together (same result as two
+    // single steps).
+    auto step2 = [&](int i, uint32_t h1, uint32_t h2, int q) {
+        const int a1 = h1 & 63, b1 = (h1 >> 6) & 63, a2 = h2 & 63, b2 = (h2 >> 6) & 63;
+        const C u1 = fco * stf[i * kPad + lane], v1 = sco * sts[i * kPad + lane];
+        const C u2 = fco * stf[(i + 1) * kPad + lane], v2 = sco * sts[(i + 1) * kPad + lane];
+        const C w1 = u1 - v1, w2 = u2 - v2;
+        if (has_s) {
+            const C ra1 = Rv[a1 * 32 + lane], ra2 = Rv[a2 * 32 + lane];
+            const C rb1 = K2 == 2 ? Rv[b1 * 32 + lane] : C(0);
+            const C rb2 = K2 == 2 ? Rv[b2 * 32 + lane] : C(0);
+            const C lo1 = Gv - ra1 - rb1;
+            const C g1 = Gv + v1;
+            const C lo2 = g1 - ra2 - rb2;
+            Pref(q) = (K2 == 2 ? w1 : C(0)) + C(2) * lo1;
+            Pref(q + 1) = (K2 == 2 ? w2 : C(0)) + C(2) * lo2;
+            Rv[a1 * 32 + lane] = ra1 + v1;
+            Rv[a2 * 32 + lane] = ra2 + v2;
+            if (K2 == 2) {
+                Rv[b1 * 32 + lane] = rb1 + v1;
+                Rv[b2 * 32 + lane] = rb2 + v2;
+            }
+            Gv = g1 + v2;
+        } else {
+            Pref(q) = K2 == 2 ? w1 : C(0);
+            Pref(q + 1) = K2 == 2 ? w2 : C(0);
+        }
+        if (has_f) {
+            const C fa1 = Rw[a1 * 32 + lane], fa2 = Rw[a2 * 32 + lane];
+            const C fb1 = K2 == 2 ? Rw[b1 * 32 + lane] : C(0);
+            const C fb2 = K2 == 2 ? Rw[b2 * 32 + lane] : C(0);
+            Rw[a1 * 32 + lane] = fa1 + w1;
+            Rw[a2 * 32 + lane] = fa2 + w2;
+            if (K2 == 2) {
+                Rw[b1 * 32 + lane] = fb1 + w1;
+                Rw[b2 * 32 + lane] = fb2 + w2;
+            }
+            Gw = (Gw + w1) + w2;
+        }
+    };
+    if (c0 < c1) fetch(c0);
     for (int t0 = c0; t0 < c1; t0 += 32) {
         const int len = min(32, c1 - t0);
-        const int pos = t0 + lane;
-        const bool pin = lane < len;
-        const C lin = pin ? lam_in[pos] : C(0);
-        const uint32_t hreg = pin ? __ldg(&p.hinfo[pos]) : 0u;
-#pragma unroll 4
+        const C lin = lin_next;
+        const uint32_t hreg = h_next;
+#pragma unroll
         for (int jj = 0; jj < 32; ++jj) {
-            const ColInfo cj = L.ci[jj];
-            C xf = C(0), xs = C(0);
-            if (pin) {
-                const S *base = vin + cj.in_off + pos;
-                if (cj.foff >= 0) xf = Store<S>::load(base + cj.foff);
-                if (cj.soff >= 0) xs = Store<S>::load(base + cj.soff);
-            }
-            stf[lane * kPad + jj] = lin * xf;
-            sts[lane * kPad + jj] = lin * xs;
+            stf[lane * kPad + jj] = lin * xf[jj];
+            sts[lane * kPad + jj] = lin * xs[jj];
         }
         __syncwarp();
-        for (int i = 0; i < len; ++i) {
-            const uint32_t hi = __shfl_sync(kFull, hreg, i);
-            const int ca = hi & 63, cb = (hi >> 6) & 63;
-            const C u = fco * stf[i * kPad + lane];
-            const C v = sco * sts[i * kPad + lane];
-            const C w = u - v;
-            const int q = t0 + i;
-            if (has_s) {
-                const C ra = Rv[ca * 32 + lane];
-                const C rb = K2 == 2 ? Rv[cb * 32 + lane] : C(0);
-                const C lo = Gv - ra - rb;              // compatible, strictly weaker
-                if (!(hi & (1u << 12))) {
-                    Pref(q) = (K2 == 2 ? w : C(0)) + C(2) * lo;
-                    Rv[ca * 32 + lane] = ra + v;
-                    if (K2 == 2) Rv[cb * 32 + lane] = rb + v;
-                    Gv += v;
-                } else {
-                    // tie group: updates wait until its last member
-                    Pref(q) = (K2 == 2 ? w + v : C(0)) + C(2) * lo;
-                    Pc[ca * 32 + lane] += v;
-                    if (K2 == 2) Pc[cb * 32 + lane] += v;
-                    Pg += v;
-                    if (hi & (1u << 13)) {
-                        const int q0 = q - (int)(hi >> 16);
-                        // compatible equal-strength mass, by inclusion-exclusion
-                        for (int r = q0; r <= q; ++r) {
-                            const uint32_t hr = __ldg(&p.hinfo[r]);
-                            C t = Pg - Pc[(hr & 63) * 32 + lane];
-                            if (K2 == 2) t -= Pc[((hr >> 6) & 63) * 32 + lane];
-                            Pref(r) += t;
-                        }
-                        for (int r = q0; r <= q; ++r) {
-                            const uint32_t hr = __ldg(&p.hinfo[r]);
-                            const int a = hr & 63;
-                            Rv[a * 32 + lane] += Pc[a * 32 + lane];
-                            Pc[a * 32 + lane] = C(0);
-                            if (K2 == 2) {
-                                const int b = (hr >> 6) & 63;
-                                Rv[b * 32 + lane] += Pc[b * 32 + lane];
-                                Pc[b * 32 + lane] = C(0);
-                            }
-                        }
-                        Gv += Pg;
-                        Pg = C(0);
-                    }
-                }
+        if (t0 + 32 < c1) fetch(t0 + 32);
+        for (int i = 0; i < len;) {
+            const uint32_t h1 = __shfl_sync(kFull, hreg, i);
+            const uint32_t h2 = __shfl_sync(kFull, hreg, min(i + 1, 31));
+            if ((h1 & (1u << 14)) && i + 1 < len) {
+                step2(i, h1, h2, t0 + i);
+                i += 2;
             } else {
-                Pref(q) = K2 == 2 ? w : C(0);
-            }
-            if (has_f) {
-                Rw[ca * 32 + lane] += w;
-                if (K2 == 2) Rw[cb * 32 + lane] += w;
-                Gw += w;
+                step1(i, h1, t0 + i);
+                i += 1;
             }
         }
         __syncwarp();
@@ -248,7 +337,8 @@ pair_scan_kernel(const ScanParams p) {
     L.sums[(warp * 3 + 1) * 32 + lane] = Gw;
     __syncthreads();
 
-    // ---- phase 2: chunk offsets.  Z[k][c] = Pw[c] - 2 Xv[k][c] replaces Rv_k.
+    // ---- phase 2: chunk offsets.  Z[k][c] = Pw[c] + 2 Xv[k][c] replaces Rv_k, where
+    // Xv[k][c] is the mass of card c in earlier chunks (removed from Lo).
     for (int c = warp; c < nc; c += nw) {
         C pw = C(0);
         for (int k = 0; k < nw; ++k) {
@@ -259,7 +349,7 @@ pair_scan_kernel(const ScanParams p) {
         for (int k = 0; k < nw; ++k) {
             C *Tk = L.tables + k * L.per_warp;
             const C r = Tk[c * 32 + lane];
-            Tk[c * 32 + lane] = pw - C(2) * xv;
+            Tk[c * 32 + lane] = pw + C(2) * xv;
             xv += r;
         }
     }
@@ -275,11 +365,27 @@ pair_scan_kernel(const ScanParams p) {
     }
     __syncthreads();
 
-    // ---- phase 3: fold totals and cross-chunk scan terms
+    // ---- phase 3: fold totals and cross-chunk scan terms (4 hands per round:
+    // every load of the round is issued before its stores)
     {
         const C base = L.sums[(warp * 3 + 2) * 32 + lane];
         const C *Z = Rv;
-        for (int q = c0; q < c1; ++q) {
+        int q = c0;
+        for (; q + 4 <= c1; q += 4) {
+            uint32_t hq[4];
+            C pv[4], za[4], zb[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) hq[j] = __ldg(&p.hinfo[q + j]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                pv[j] = Pref(q + j);
+                za[j] = Z[(hq[j] & 63) * 32 + lane];
+                zb[j] = K2 == 2 ? Z[((hq[j] >> 6) & 63) * 32 + lane] : C(0);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Pref(q + j) = pv[j] + base - za[j] - zb[j];
+        }
+        for (; q < c1; ++q) {
             const uint32_t hq = __ldg(&p.hinfo[q]);
             C val = Pref(q) + base - Z[(hq & 63) * 32 + lane];
             if (K2 == 2) val -= Z[((hq >> 6) & 63) * 32 + lane];
@@ -301,10 +407,10 @@ pair_scan_kernel(const ScanParams p) {
             }
         }
     } else if (prow) {
-        for (int q = 0; q < p.hs; ++q) {
-            const C val = q < H ? lam_out[q] * Pref(q) : C(0);
-            prow[q] = Store<S>::conv(val);
-        }
+        // each warp scales its own chunk of the lane's row; the last one pads
+        for (int q = c0; q < c1; ++q) prow[q] = Store<S>::conv(lam_out[q] * Pref(q));
+        if (warp == nw - 1)
+            for (int q = H; q < p.hs; ++q) prow[q] = Store<S>::conv(C(0));
     }
 }
 

@@ -40,3 +40,31 @@ cudaError_t launch_pair_scan(const ScanParams &p, int storage, int cards_per_han
                              bool partial_in_smem, cudaStream_t stream);
 
 }  // namespace kps
+
+namespace kps {
+
+constexpr int kTile = 32;        // hands per staging tile (tie-aligned tiles are shorter)
+
+// Fast path: partial results pass through `scratch` (the output buffer for
+// FP32/FP64, an FP32 buffer for half-precision outputs) instead of shared
+// memory, tie groups are corrected inside tie-aligned tiles (needs every tie
+// group to fit in one tile).
+struct FastParams {
+    const void *vin;             // [batch][n_in][hs] storage type
+    void *vout;                  // [batch][n_out][hs] storage type
+    void *scratch;               // [batch][n_out][hs] compute type (may alias vout)
+    int H, hs, nc;
+    int n_out, n_in, batch;
+    const int *fcol, *scol;
+    const void *fcoef, *scoef;   // compute type
+    const uint32_t *hinfo;
+    const void *lam_in, *lam_out;  // compute type
+    const int2 *tiles;           // (start, length) of every tile, chunk after chunk
+    int nw;
+    int tchunk[kMaxWarps + 1];   // chunk k owns tiles [tchunk[k], tchunk[k+1])
+};
+
+size_t fast_smem_bytes(int storage, int nc, int nw);
+cudaError_t launch_fast_scan(const FastParams &p, int storage, int cards_per_hand, cudaStream_t stream);
+
+}  // namespace kps

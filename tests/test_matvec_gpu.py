@@ -160,3 +160,39 @@ def test_overlap_rejected(river):
     with pytest.raises(kps.KpsError) as ei:
         kps.matvec_A(g, buf, buf, 1)
     assert ei.value.status == kps.EINVAL
+
+
+@pytest.fixture(scope="module")
+def river_ties():
+    spec = synth.river_spec(seed=6)
+    spec["strength"] = [s // 40 for s in spec["strength"]]      # tie groups of up to ~15 hands
+    return spec, OracleGame(spec), kps.Game(spec), library_order(spec["strength"])
+
+
+@pytest.mark.parametrize("warps", ["1", "3", "8"])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_river_many_ties_warp_counts(river_ties, warps, transpose, monkeypatch):
+    """Tie groups inside tiles, several hand chunks per CTA."""
+    spec, og, g, order = river_ties
+    monkeypatch.setenv("KPS_WARPS", warps)
+    v = _inputs(og, 5, seed=53, transpose=transpose)
+    want = og.matvec_AT(v) if transpose else og.matvec_A(v)
+    got, _ = _run(g, order, v, transpose, kps.F64)
+    assert normwise_error(got, want) <= 1e-12
+    got, _ = _run(g, order, v, transpose, kps.F32)
+    assert normwise_error(got, want) <= 1e-5
+
+
+@pytest.mark.parametrize("dt", [kps.F64, kps.F32])
+def test_tie_group_longer_than_a_tile(dt):
+    """45 hands that all tie (longer than one 32-hand tile): general kernel."""
+    spec = synth.micro_spec(seed=19, ranks=5, suits=2, nboard=0)
+    spec["strength"] = [1] * 45
+    og, g = OracleGame(spec), kps.Game(spec)
+    assert g.info()["max_tie"] == 45
+    order = library_order(spec["strength"])
+    for transpose in (False, True):
+        v = _inputs(og, 3, seed=59, transpose=transpose)
+        got, _ = _run(g, order, v, transpose, dt)
+        want = og.matvec_AT(v) if transpose else og.matvec_A(v)
+        assert normwise_error(got, want) <= TOL[dt]
