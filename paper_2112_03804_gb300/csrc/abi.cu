@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <new>
@@ -108,11 +109,14 @@ kps_status upload(kps_game *g, cudaStream_t stream) {
     // layout of the blob (8-byte aligned pieces)
     auto al = [](size_t x) { return (x + 15) / 16 * 16; };
     size_t off = 0;
-    const size_t o_hinfo = off; off = al(off + 4 * (size_t)H);
-    const size_t o_l1f = off; off = al(off + 4 * (size_t)H);
-    const size_t o_l2f = off; off = al(off + 4 * (size_t)H);
-    const size_t o_l1d = off; off = al(off + 8 * (size_t)H);
-    const size_t o_l2d = off; off = al(off + 8 * (size_t)H);
+    // per-hand tables are padded by 16 entries: vector loads may round the
+    // end of a hand range up to a multiple of 4
+    const size_t Hp = (size_t)H + 16;
+    const size_t o_hinfo = off; off = al(off + 4 * Hp);
+    const size_t o_l1f = off; off = al(off + 4 * Hp);
+    const size_t o_l2f = off; off = al(off + 4 * Hp);
+    const size_t o_l1d = off; off = al(off + 8 * Hp);
+    const size_t o_l2d = off; off = al(off + 8 * Hp);
     size_t o_fcol[2], o_scol[2], o_ff[2], o_sf[2], o_fd[2], o_sd[2];
     for (int d = 0; d < 2; ++d) {
         const size_t r = g->fcol[d].size();
@@ -177,16 +181,19 @@ kps_status upload(kps_game *g, cudaStream_t stream) {
 // Warps per CTA of the fast path: two CTAs of 4 warps per SM when they fit
 // (smaller CTAs shorten the tail of the last wave), else the largest count
 // that fits.  KPS_WARPS overrides the choice (1..8).
-int fast_warps(int storage, int nc, int H) {
+int fast_warps(int storage, int nc, int H, bool vec) {
     const int smem_max = kps::max_dyn_smem();
+    auto bytes = [&](int w) { return vec ? kps::vec_smem_bytes(storage, nc, w) : kps::fast_smem_bytes(storage, nc, w); };
     int nw = 0;
     if (const char *env = std::getenv("KPS_WARPS")) nw = std::atoi(env);
-    if (nw < 1 || nw > kps::kMaxWarps || kps::fast_smem_bytes(storage, nc, nw) > (size_t)smem_max) {
+    if (nw < 1 || nw > kps::kMaxWarps || bytes(nw) > (size_t)smem_max) {
         nw = 0;
-        if (2 * (kps::fast_smem_bytes(storage, nc, 4) + 1024) <= (size_t)smem_max + 1024) nw = 4;
-        else
+        // prefer two CTAs per SM (227 KB per SM, 1 KB reserved per CTA)
+        for (int w = 4; w >= 2 && nw == 0; --w)
+            if (2 * (bytes(w) + 1024) <= (size_t)smem_max + 1024) nw = w;
+        if (nw == 0)
             for (int w = kps::kMaxWarps; w >= 1; --w)
-                if (kps::fast_smem_bytes(storage, nc, w) <= (size_t)smem_max) { nw = w; break; }
+                if (bytes(w) <= (size_t)smem_max) { nw = w; break; }
     }
     return std::max(1, std::min(nw, (H + kps::kTile - 1) / kps::kTile));
 }
@@ -194,8 +201,13 @@ int fast_warps(int storage, int nc, int H) {
 kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int storage, kps_dtype dt,
                        cudaStream_t stream) {
     const kps::HostGame &h = g->host;
-    const int nw = fast_warps(storage, sp.nc, h.H);
-    if (kps::fast_smem_bytes(storage, sp.nc, nw) > (size_t)kps::max_dyn_smem())
+    // 16-byte async copies need 16-byte aligned vectors (FP32/FP64 storage)
+    const bool aligned = ((reinterpret_cast<uintptr_t>(sp.vin) | reinterpret_cast<uintptr_t>(sp.vout)) & 15) == 0;
+    const bool vec = aligned && (storage == kps::kStoreF32 || storage == kps::kStoreF64) && sp.nc <= 64 &&
+                     std::getenv("KPS_NO_VEC") == nullptr;
+    const int nw = fast_warps(storage, sp.nc, h.H, vec);
+    const size_t need = vec ? kps::vec_smem_bytes(storage, sp.nc, nw) : kps::fast_smem_bytes(storage, sp.nc, nw);
+    if (need > (size_t)kps::max_dyn_smem())
         return fail(KPS_ENOTSUP, "card count too large for shared memory");
     auto it = g->tiles.find(nw);
     if (it == g->tiles.end()) {
@@ -250,7 +262,9 @@ kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int stor
     for (int i = 0; i <= nw; ++i) p.tchunk[i] = it->second.tchunk[i];
     (void)dir;
     (void)dt;
-    cudaError_t e = kps::launch_fast_scan(p, storage, h.k, stream);
+    cudaError_t e;
+    if (vec) e = kps::launch_vec_scan(p, storage, h.k, stream);
+    else e = kps::launch_fast_scan(p, storage, h.k, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launching the payoff scan");
     return KPS_OK;
 }

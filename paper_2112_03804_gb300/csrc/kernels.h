@@ -68,3 +68,13 @@ size_t fast_smem_bytes(int storage, int nc, int nw);
 cudaError_t launch_fast_scan(const FastParams &p, int storage, int cards_per_hand, cudaStream_t stream);
 
 }  // namespace kps
+
+namespace kps {
+
+// Vectorised fast path for FP32/FP64 storage (16-byte async copies); same
+// parameters as the fast path.  Column kinds (fold only, showdown only,
+// both) get their own specialised scan.
+size_t vec_smem_bytes(int storage, int nc, int nw);
+cudaError_t launch_vec_scan(const FastParams &p, int storage, int cards_per_hand, cudaStream_t stream);
+
+}  // namespace kps

@@ -1,0 +1,463 @@
+// Vectorised fast path of the Kronecker-form payoff products (sm_103a),
+// FP32 and FP64 storage.
+//
+// Mathematics as in kernels.cu / kernels_fast.cu:
+//   out / lambda_out = K_F(u - v) + 2 Lo(v) + TieC(v)
+// (u, v: lambda-weighted fold and showdown inputs of an output column; K_F
+// the card-removal fold operator; Lo the compatible strictly-weaker mass).
+//
+// What this version changes, all to cut instructions per (hand, column):
+//   * staging: each warp double-buffers its 32-hand tiles with 16-byte
+//     cp.async copies straight into shared memory, [column][hand] with a
+//     pitch of 36 floats (34 doubles); the scan then reads 4 (2) hands of
+//     its column per 128-bit load, conflict free per quarter warp;
+//   * the scan over a tile is fully unrolled, and specialised by column
+//     kind: fold only (K_F alone: one per-card total), showdown only (one
+//     per-card running sum, w = -v), or both (float2 per card);
+//   * partial results leave through 128-bit stores into a [column][hand]
+//     tile and 16-byte global stores (edges of a tile stored element-wise);
+//   * the final pass (lane = hand) reads the [column][card] table at
+//     compile-time offsets.
+// Tie groups are corrected inside tie-aligned tiles exactly as in
+// kernels_fast.cu.  No atomics: results are bit-reproducible.
+#include "kernels.h"
+
+#include <cstdint>
+
+namespace kps {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kZPitch = 65;      // [column][card] table pitch (>= cards + 1, odd)
+
+enum Kind { kKindF = 1, kKindS = 2, kKindFS = 3 };
+
+template <typename S> struct Cfg;
+template <> struct Cfg<float> {
+    static constexpr int V = 4;    // elements per 16-byte vector
+    static constexpr int W = 9;    // vectors covering any 32-hand tile
+    static constexpr int P = 36;   // pitch of a staged column
+    using C2 = float2;
+    using Vec = float4;
+    __device__ static float get(const Vec &x, int k) { return k == 0 ? x.x : k == 1 ? x.y : k == 2 ? x.z : x.w; }
+    __device__ static Vec make(const float *v) { return make_float4(v[0], v[1], v[2], v[3]); }
+};
+template <> struct Cfg<double> {
+    static constexpr int V = 2;
+    static constexpr int W = 17;
+    static constexpr int P = 34;
+    using C2 = double2;
+    using Vec = double2;
+    __device__ static double get(const Vec &x, int k) { return k == 0 ? x.x : x.y; }
+    __device__ static Vec make(const double *v) { return make_double2(v[0], v[1]); }
+};
+
+struct Col {
+    long long in_off;
+    long long out_off;   // -1 = no column
+    int foff, soff;      // -1 = no such terminal
+};
+
+__device__ __forceinline__ void cp16(void *smem, const void *gmem, int bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ constexpr int hw_pitch(int P) { return (P + 4 + 3) / 4 * 4; }
+
+// Byte layout of one warp's shared memory.
+struct WarpLayout {
+    size_t r, stage, lam, hw, ptile, total;
+};
+__host__ __device__ inline WarpLayout warp_layout(int nc, size_t cs, int P) {
+    WarpLayout L;
+    size_t o = 0;
+    L.r = o;     o = al16(o + (size_t)nc * 32 * 2 * cs);         // per-card state
+    L.stage = o; o = al16(o + 2 * 2 * 32 * (size_t)P * cs);      // [buf][term][col][P]
+    L.lam = o;   o = al16(o + 2 * (size_t)(P + 4) * cs);         // [buf][P+4]
+    L.hw = o;    o = al16(o + 2 * (size_t)hw_pitch(P) * 4);      // [buf][hw_pitch] hand records
+    L.ptile = o; o = al16(o + 32 * (size_t)P * cs);              // [col][P]
+    L.total = o;
+    return L;
+}
+__host__ __device__ inline size_t header_bytes(int nw, size_t cs) {
+    return al16(32 * sizeof(Col) + 2 * 32 * cs + (size_t)nw * 3 * 32 * cs);
+}
+
+template <typename S, int K2, int KIND>
+__device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *smem, const Col *ci,
+                                          const S *fco_s, const S *sco_s, S *sums, bool uni, int nvalid) {
+    using C = S;
+    using CF = Cfg<S>;
+    using C2 = typename CF::C2;
+    using Vec = typename CF::Vec;
+    constexpr int V = CF::V, W = CF::W, P = CF::P;
+    constexpr bool HF = (KIND & kKindF) != 0, HS = (KIND & kKindS) != 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = p.nw, nc = p.nc;
+    const int H = p.H, hs = p.hs;
+    const size_t cs = sizeof(C);
+    const WarpLayout WL = warp_layout(nc, cs, P);
+    const size_t hdr = header_bytes(nw, cs);
+    unsigned char *mine = smem + hdr + (size_t)warp * WL.total;
+    C2 *R2 = reinterpret_cast<C2 *>(mine + WL.r);     // both kinds: {v running, w total}
+    C *R1 = reinterpret_cast<C *>(mine + WL.r);       // one kind: [nc][32]
+    C *stage = reinterpret_cast<C *>(mine + WL.stage);
+    C *lamw = reinterpret_cast<C *>(mine + WL.lam);
+    uint32_t *hw = reinterpret_cast<uint32_t *>(mine + WL.hw);
+    C *ptile = reinterpret_cast<C *>(mine + WL.ptile);
+    const S *vin = static_cast<const S *>(p.vin);
+    S *vout = static_cast<S *>(p.vout);
+    C *scr = static_cast<C *>(p.scratch);
+    const C *lam_in = static_cast<const C *>(p.lam_in);
+    const C *lam_out = static_cast<const C *>(p.lam_out);
+    const Col c0i = ci[0];
+    const long long istride = (long long)p.n_in * hs, ostride = (long long)p.n_out * hs;
+    const C fco = fco_s[lane], sco = sco_s[lane];
+
+    if (HF && HS) {
+        for (int c = 0; c < nc; ++c) R2[c * 32 + lane] = C2{C(0), C(0)};
+    } else {
+        for (int c = 0; c < nc; ++c) R1[c * 32 + lane] = C(0);
+    }
+
+    // ---- phase 1
+    const int tb = p.tchunk[warp], te = p.tchunk[warp + 1];
+    auto issue = [&](int t, int buf) {
+        const int2 tl = p.tiles[t];
+        const int wb = tl.x & ~(V - 1);
+        const int nv = (tl.x + tl.y - wb + V - 1) / V;
+        C *sf = stage + (size_t)(buf * 2 + 0) * 32 * P;
+        C *ss = stage + (size_t)(buf * 2 + 1) * 32 * P;
+        for (int idx = lane; idx < 32 * W; idx += 32) {
+            const int jj = idx / W, v = idx - jj * W;
+            if (v >= nv) continue;
+            const S *base;
+            int fo, so;
+            bool ok;
+            if (uni) {
+                base = vin + c0i.in_off + jj * istride;
+                fo = c0i.foff;
+                so = c0i.soff;
+                ok = jj < nvalid;
+            } else {
+                const Col cj = ci[jj];
+                base = vin + cj.in_off;
+                fo = cj.foff;
+                so = cj.soff;
+                ok = cj.out_off >= 0;
+            }
+            const long long e = wb + v * V;
+            if (HF) {
+                const bool q = ok && fo >= 0;
+                cp16(sf + jj * P + v * V, q ? (const void *)(base + fo + e) : (const void *)vin, q ? 16 : 0);
+            }
+            if (HS) {
+                const bool q = ok && so >= 0;
+                cp16(ss + jj * P + v * V, q ? (const void *)(base + so + e) : (const void *)vin, q ? 16 : 0);
+            }
+        }
+        if (lane < nv) cp16(lamw + buf * (P + 4) + lane * V, lam_in + wb + lane * V, 16);
+        const int hb = wb & ~3;
+        const int nh = (wb + nv * V - hb + 3) / 4;
+        if (lane < nh) cp16(hw + buf * hw_pitch(P) + lane * 4, p.hinfo + hb + lane * 4, 16);
+        cp_commit();
+    };
+
+    C Gv = C(0), Gw = C(0);
+    if (tb < te) issue(tb, 0);
+    for (int t = tb; t < te; ++t) {
+        const int buf = (t - tb) & 1;
+        if (t + 1 < te) {
+            issue(t + 1, buf ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncwarp();
+        const int2 tl = p.tiles[t];
+        const int t0 = tl.x, len = tl.y;
+        const int wb = t0 & ~(V - 1), off = t0 - wb;
+        const int nv = (off + len + V - 1) / V;
+        const int hoff = wb - (wb & ~3);
+        const C *xf_s = stage + (size_t)(buf * 2 + 0) * 32 * P + lane * P;
+        const C *xs_s = stage + (size_t)(buf * 2 + 1) * 32 * P + lane * P;
+        const C *lw = lamw + buf * (P + 4);
+        const uint32_t *hv = hw + buf * hw_pitch(P) + hoff;
+        bool any_tie = false;
+#pragma unroll
+        for (int v = 0; v < W; ++v) {
+            if (v < nv) {
+                Vec xf4{}, xs4{};
+                if (HF) xf4 = *reinterpret_cast<const Vec *>(xf_s + v * V);
+                if (HS) xs4 = *reinterpret_cast<const Vec *>(xs_s + v * V);
+                C res[V];
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    res[k] = C(0);
+                    const int slot = v * V + k;
+                    if (slot >= off && slot < off + len) {
+                        const uint32_t h = hv[slot];
+                        const C lam = lw[slot];
+                        const int a = h & 63, b = (h >> 6) & 63;
+                        any_tie |= (h & (1u << 12)) != 0;
+                        if (HF && HS) {
+                            const C u = (fco * lam) * CF::get(xf4, k);
+                            const C vv = (sco * lam) * CF::get(xs4, k);
+                            const C w = u - vv;
+                            const C2 ra = R2[a * 32 + lane];
+                            const C2 rb = K2 == 2 ? R2[b * 32 + lane] : C2{C(0), C(0)};
+                            res[k] = (K2 == 2 ? w : C(0)) + C(2) * (Gv - ra.x - rb.x);
+                            R2[a * 32 + lane] = C2{ra.x + vv, ra.y + w};
+                            if (K2 == 2) R2[b * 32 + lane] = C2{rb.x + vv, rb.y + w};
+                            Gv += vv;
+                            Gw += w;
+                        } else if (HS) {
+                            const C vv = (sco * lam) * CF::get(xs4, k);
+                            const C ra = R1[a * 32 + lane];
+                            const C rb = K2 == 2 ? R1[b * 32 + lane] : C(0);
+                            res[k] = (K2 == 2 ? -vv : C(0)) + C(2) * (Gv - ra - rb);
+                            R1[a * 32 + lane] = ra + vv;
+                            if (K2 == 2) R1[b * 32 + lane] = rb + vv;
+                            Gv += vv;
+                        } else {
+                            const C u = (fco * lam) * CF::get(xf4, k);
+                            res[k] = K2 == 2 ? u : C(0);
+                            const C ra = R1[a * 32 + lane];
+                            const C rb = K2 == 2 ? R1[b * 32 + lane] : C(0);
+                            R1[a * 32 + lane] = ra + u;
+                            if (K2 == 2) R1[b * 32 + lane] = rb + u;
+                            Gw += u;
+                        }
+                    }
+                }
+                *reinterpret_cast<Vec *>(ptile + lane * P + v * V) = CF::make(res);
+            }
+        }
+        // tie groups of the tile: exact equal-strength term (see kernels_fast.cu)
+        if (HS && any_tie) {
+            for (int i = 0; i < len; ++i) {
+                const uint32_t hi = hv[off + i];
+                if (!(hi & (1u << 13))) continue;
+                const int g0 = i - (int)(hi >> 16);
+                for (int q = g0; q <= i; ++q) {
+                    const uint32_t hq = hv[off + q];
+                    C corr = C(0);
+                    for (int r = g0; r <= i; ++r) {
+                        if (r == q) continue;
+                        const uint32_t hr = hv[off + r];
+                        const int qa = hq & 63, qb = (hq >> 6) & 63, ra = hr & 63, rb = (hr >> 6) & 63;
+                        bool share = qa == ra;
+                        if (K2 == 2) share = share || qa == rb || qb == ra || qb == rb;
+                        if (share) continue;
+                        const C vr = (sco * lw[off + r]) * xs_s[off + r];
+                        corr += r > q ? vr : -vr;
+                    }
+                    ptile[lane * P + off + q] += corr;
+                }
+            }
+        }
+        __syncwarp();
+        // partial results out: 16-byte stores, element-wise at the tile edges
+        for (int idx = lane; idx < 32 * W; idx += 32) {
+            const int jj = idx / W, v = idx - jj * W;
+            if (v >= nv) continue;
+            long long o;
+            if (uni) o = jj < nvalid ? c0i.out_off + jj * ostride : -1;
+            else o = ci[jj].out_off;
+            if (o < 0) continue;
+            const Vec val = *reinterpret_cast<const Vec *>(ptile + jj * P + v * V);
+            C *dst = scr + o + wb + v * V;
+            if (v * V >= off && v * V + V <= off + len) {
+                *reinterpret_cast<Vec *>(dst) = val;
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const int slot = v * V + k;
+                    if (slot >= off && slot < off + len) dst[k] = CF::get(val, k);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    sums[(warp * 3 + 0) * 32 + lane] = Gv;
+    sums[(warp * 3 + 1) * 32 + lane] = Gw;
+    __syncthreads();
+
+    // ---- phase 2: Z_k[column][card] = Pw + 2 Xv_k, into warp k's stage area
+    for (int c = warp; c < nc; c += nw) {
+        C pw = C(0);
+        for (int k = 0; k < nw; ++k) {
+            const unsigned char *bk = smem + hdr + (size_t)k * WL.total + WL.r;
+            if (HF && HS) pw += reinterpret_cast<const C2 *>(bk)[c * 32 + lane].y;
+            else if (HS) pw -= reinterpret_cast<const C *>(bk)[c * 32 + lane];
+            else pw += reinterpret_cast<const C *>(bk)[c * 32 + lane];
+        }
+        C xv = C(0);
+        for (int k = 0; k < nw; ++k) {
+            const unsigned char *bk = smem + hdr + (size_t)k * WL.total;
+            C *Zk = reinterpret_cast<C *>(smem + hdr + (size_t)k * WL.total + WL.stage);
+            C r = C(0);
+            if (HF && HS) r = reinterpret_cast<const C2 *>(bk + WL.r)[c * 32 + lane].x;
+            else if (HS) r = reinterpret_cast<const C *>(bk + WL.r)[c * 32 + lane];
+            Zk[lane * kZPitch + c] = pw + C(2) * xv;
+            xv += r;
+        }
+    }
+    if (warp == 0) {
+        C tw = C(0);
+        for (int k = 0; k < nw; ++k)
+            tw += HF ? sums[(k * 3 + 1) * 32 + lane] : -sums[(k * 3 + 0) * 32 + lane];
+        C xg = C(0);
+        for (int k = 0; k < nw; ++k) {
+            sums[(k * 3 + 2) * 32 + lane] = tw + C(2) * xg;
+            xg += sums[(k * 3 + 0) * 32 + lane];
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3: finish, lane = hand
+    const C *Z = reinterpret_cast<const C *>(mine + WL.stage);
+    const C basev = sums[(warp * 3 + 2) * 32 + lane];
+    for (int t = tb; t < te; ++t) {
+        const int2 tl = p.tiles[t];
+        const int pos = tl.x + lane;
+        const bool pin = lane < tl.y;
+        const uint32_t hq = pin ? __ldg(&p.hinfo[pos]) : 0u;
+        const C lo = pin ? lam_out[pos] : C(0);
+        const C *za = Z + (hq & 63);
+        const C *zb = Z + ((hq >> 6) & 63);
+        C part[32];
+        if (uni) {
+            const C *src = scr + c0i.out_off + pos;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) part[jj] = (pin && jj < nvalid) ? src[jj * ostride] : C(0);
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                const long long o = ci[jj].out_off;
+                part[jj] = (pin && o >= 0) ? scr[o + pos] : C(0);
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+            const C bj = __shfl_sync(kFull, basev, jj);
+            C val = part[jj] + bj - za[jj * kZPitch];
+            if (K2 == 2) val -= zb[jj * kZPitch];
+            part[jj] = lo * val;
+        }
+        if (pin) {
+            if (uni) {
+                S *dst = vout + c0i.out_off + pos;
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj)
+                    if (jj < nvalid) dst[jj * ostride] = part[jj];
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    const long long o = ci[jj].out_off;
+                    if (o >= 0) vout[o + pos] = part[jj];
+                }
+            }
+        }
+    }
+    if (warp == nw - 1 && H + lane < hs) {
+        for (int jj = 0; jj < 32; ++jj) {
+            const long long o = ci[jj].out_off;
+            if (o >= 0) vout[o + H + lane] = S(0);
+        }
+    }
+}
+
+template <typename S, int K2>
+__global__ void __launch_bounds__(32 * kMaxWarps)
+vec_scan_kernel(const FastParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int hs = p.hs;
+    Col *ci = reinterpret_cast<Col *>(smem_raw);
+    S *fco_s = reinterpret_cast<S *>(smem_raw + 32 * sizeof(Col));
+    S *sco_s = fco_s + 32;
+    S *sums = sco_s + 32;
+    int kinds = 0;
+    if (threadIdx.x < 32) {
+        const long long col = (long long)blockIdx.x * 32 + threadIdx.x;
+        Col c;
+        S f = S(0), s = S(0);
+        if (col < (long long)p.n_out * p.batch) {
+            const int sg = (int)(col / p.batch), b = (int)(col % p.batch);
+            const int fc = p.fcol[sg], sc = p.scol[sg];
+            c.in_off = (long long)b * p.n_in * hs;
+            c.out_off = ((long long)b * p.n_out + sg) * hs;
+            c.foff = fc >= 0 ? fc * hs : -1;
+            c.soff = sc >= 0 ? sc * hs : -1;
+            if (fc >= 0) f = static_cast<const S *>(p.fcoef)[sg];
+            if (sc >= 0) s = static_cast<const S *>(p.scoef)[sg];
+        } else {
+            c.in_off = 0;
+            c.out_off = -1;
+            c.foff = c.soff = -1;
+        }
+        ci[threadIdx.x] = c;
+        fco_s[threadIdx.x] = f;
+        sco_s[threadIdx.x] = s;
+        kinds = (c.foff >= 0 ? 1 : 0) | (c.soff >= 0 ? 2 : 0);
+    }
+    const bool has_f = __syncthreads_or(kinds & 1) != 0;
+    const bool has_s = __syncthreads_or(kinds & 2) != 0;
+    const Col c0i = ci[0];
+    int same = 1, valid = 0;
+    if (threadIdx.x < 32) {
+        const Col c = ci[threadIdx.x];
+        if (c.out_off >= 0) {
+            valid = 1;
+            same = c.foff == c0i.foff && c.soff == c0i.soff &&
+                   c.in_off == c0i.in_off + (long long)threadIdx.x * p.n_in * hs &&
+                   c.out_off == c0i.out_off + (long long)threadIdx.x * p.n_out * hs;
+        }
+    }
+    const bool uni = __syncthreads_and(same) != 0;
+    const int nvalid = __syncthreads_count(valid);
+    if (has_f && has_s) scan_body<S, K2, kKindFS>(p, smem_raw, ci, fco_s, sco_s, sums, uni, nvalid);
+    else if (has_s) scan_body<S, K2, kKindS>(p, smem_raw, ci, fco_s, sco_s, sums, uni, nvalid);
+    else scan_body<S, K2, kKindF>(p, smem_raw, ci, fco_s, sco_s, sums, uni, nvalid);
+}
+
+template <typename S, int K2>
+cudaError_t launch_t(const FastParams &p, size_t smem, cudaStream_t stream) {
+    static size_t configured = 0;
+    auto fn = vec_scan_kernel<S, K2>;
+    if (configured < smem) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    const long long ncols = (long long)p.n_out * p.batch;
+    const long long blocks = (ncols + 31) / 32;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    fn<<<(unsigned)blocks, 32 * p.nw, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t vec_smem_bytes(int storage, int nc, int nw) {
+    const size_t cs = storage == kStoreF64 ? 8 : 4;
+    const int P = storage == kStoreF64 ? Cfg<double>::P : Cfg<float>::P;
+    return header_bytes(nw, cs) + (size_t)nw * warp_layout(nc, cs, P).total;
+}
+
+cudaError_t launch_vec_scan(const FastParams &p, int storage, int k, cudaStream_t stream) {
+    if (p.nc > kZPitch - 1) return cudaErrorInvalidValue;
+    const size_t smem = vec_smem_bytes(storage, p.nc, p.nw);
+    switch (storage) {
+        case kStoreF32: return k == 1 ? launch_t<float, 1>(p, smem, stream) : launch_t<float, 2>(p, smem, stream);
+        case kStoreF64: return k == 1 ? launch_t<double, 1>(p, smem, stream) : launch_t<double, 2>(p, smem, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace kps

@@ -196,3 +196,32 @@ def test_tie_group_longer_than_a_tile(dt):
         got, _ = _run(g, order, v, transpose, dt)
         want = og.matvec_AT(v) if transpose else og.matvec_A(v)
         assert normwise_error(got, want) <= TOL[dt]
+
+
+@pytest.mark.parametrize("dt", [kps.F64, kps.F32])
+def test_scalar_staging_path(river, dt, monkeypatch):
+    """The non-vectorised fast path (used for half precision and for vectors
+    that are not 16-byte aligned) on the river game."""
+    spec, og, g, order = river
+    monkeypatch.setenv("KPS_NO_VEC", "1")
+    for transpose in (False, True):
+        v = _inputs(og, 4, seed=61, transpose=transpose)
+        got, _ = _run(g, order, v, transpose, dt)
+        want = og.matvec_AT(v) if transpose else og.matvec_A(v)
+        assert normwise_error(got, want) <= TOL[dt]
+
+
+def test_unaligned_vectors(river):
+    """Vectors starting 4 bytes into an allocation take the scalar staging path."""
+    spec, og, g, order = river
+    inf = g.info()
+    B = 3
+    y = _inputs(og, B, seed=67, transpose=False)
+    yl = torch.from_numpy(to_library(y, order, inf["hs"])).to("cuda", torch.float32).reshape(-1)
+    ybuf = torch.zeros(yl.numel() + 1, device="cuda")
+    ybuf[1:] = yl
+    obuf = torch.zeros(B * inf["n1"] * inf["hs"] + 1, device="cuda")
+    kps.matvec_A(g, ybuf[1:], obuf[1:], B)
+    torch.cuda.synchronize()
+    o = obuf[1:].reshape(B, inf["n1"], inf["hs"]).double().cpu().numpy()
+    assert normwise_error(from_library(o, order, inf["H"]), og.matvec_A(y)) <= 1e-5
