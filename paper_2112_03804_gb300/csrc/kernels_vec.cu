@@ -27,7 +27,6 @@
 namespace kps {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kZPitch = 65;      // [column][card] table pitch (>= cards + 1, odd)
 
 enum Kind { kKindF = 1, kKindS = 2, kKindFS = 3 };
@@ -95,7 +94,7 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
     using CF = Cfg<S>;
     using C2 = typename CF::C2;
     using Vec = typename CF::Vec;
-    constexpr int V = CF::V, W = CF::W, P = CF::P;
+    constexpr int V = CF::V, W = CF::W, P = CF::P, HP = hw_pitch(CF::P);
     constexpr bool HF = (KIND & kKindF) != 0, HS = (KIND & kKindS) != 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = p.nw, nc = p.nc;
     const int H = p.H, hs = p.hs;
@@ -103,67 +102,57 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
     const WarpLayout WL = warp_layout(nc, cs, P);
     const size_t hdr = header_bytes(nw, cs);
     unsigned char *mine = smem + hdr + (size_t)warp * WL.total;
-    C2 *R2 = reinterpret_cast<C2 *>(mine + WL.r);     // both kinds: {v running, w total}
-    C *R1 = reinterpret_cast<C *>(mine + WL.r);       // one kind: [nc][32]
+    C2 *R2 = reinterpret_cast<C2 *>(mine + WL.r) + lane;   // [card][32]: {v running, w total}
+    C *R1 = reinterpret_cast<C *>(mine + WL.r) + lane;     // [card][32]: one kind
     C *stage = reinterpret_cast<C *>(mine + WL.stage);
     C *lamw = reinterpret_cast<C *>(mine + WL.lam);
     uint32_t *hw = reinterpret_cast<uint32_t *>(mine + WL.hw);
-    C *ptile = reinterpret_cast<C *>(mine + WL.ptile);
     const S *vin = static_cast<const S *>(p.vin);
     S *vout = static_cast<S *>(p.vout);
     C *scr = static_cast<C *>(p.scratch);
     const C *lam_in = static_cast<const C *>(p.lam_in);
     const C *lam_out = static_cast<const C *>(p.lam_out);
-    const Col c0i = ci[0];
     const long long istride = (long long)p.n_in * hs, ostride = (long long)p.n_out * hs;
     const C fco = fco_s[lane], sco = sco_s[lane];
+    // this lane's column
+    const Col cme = ci[lane];
+    const bool valid = uni ? lane < nvalid : cme.out_off >= 0;
+    const S *in_f = nullptr, *in_s = nullptr;
+    if (valid) {
+        const long long base = uni ? ci[0].in_off + lane * istride : cme.in_off;
+        const int fo = uni ? ci[0].foff : cme.foff, so = uni ? ci[0].soff : cme.soff;
+        if (fo >= 0) in_f = vin + base + fo;
+        if (so >= 0) in_s = vin + base + so;
+    }
+    const long long out_off = valid ? (uni ? ci[0].out_off + lane * ostride : cme.out_off) : 0;
+    // hands outside the current tile point at this card slot with weight 0
+    const uint32_t kTrash = (uint32_t)(nc - 1) | ((uint32_t)(nc - 1) << 6);
 
     if (HF && HS) {
-        for (int c = 0; c < nc; ++c) R2[c * 32 + lane] = C2{C(0), C(0)};
+        for (int c = 0; c < nc; ++c) R2[c * 32] = C2{C(0), C(0)};
     } else {
-        for (int c = 0; c < nc; ++c) R1[c * 32 + lane] = C(0);
+        for (int c = 0; c < nc; ++c) R1[c * 32] = C(0);
     }
 
-    // ---- phase 1
+    // ---- phase 1: scan (lane = column)
     const int tb = p.tchunk[warp], te = p.tchunk[warp + 1];
     auto issue = [&](int t, int buf) {
         const int2 tl = p.tiles[t];
         const int wb = tl.x & ~(V - 1);
-        const int nv = (tl.x + tl.y - wb + V - 1) / V;
-        C *sf = stage + (size_t)(buf * 2 + 0) * 32 * P;
-        C *ss = stage + (size_t)(buf * 2 + 1) * 32 * P;
-        for (int idx = lane; idx < 32 * W; idx += 32) {
-            const int jj = idx / W, v = idx - jj * W;
-            if (v >= nv) continue;
-            const S *base;
-            int fo, so;
-            bool ok;
-            if (uni) {
-                base = vin + c0i.in_off + jj * istride;
-                fo = c0i.foff;
-                so = c0i.soff;
-                ok = jj < nvalid;
-            } else {
-                const Col cj = ci[jj];
-                base = vin + cj.in_off;
-                fo = cj.foff;
-                so = cj.soff;
-                ok = cj.out_off >= 0;
-            }
-            const long long e = wb + v * V;
-            if (HF) {
-                const bool q = ok && fo >= 0;
-                cp16(sf + jj * P + v * V, q ? (const void *)(base + fo + e) : (const void *)vin, q ? 16 : 0);
-            }
-            if (HS) {
-                const bool q = ok && so >= 0;
-                cp16(ss + jj * P + v * V, q ? (const void *)(base + so + e) : (const void *)vin, q ? 16 : 0);
-            }
+        const int end = tl.x + tl.y;                          // first hand after the tile
+        const int nv = (end - wb + V - 1) / V;
+        C *sf = stage + (size_t)(buf * 2 + 0) * 32 * P + lane * P;
+        C *ss = stage + (size_t)(buf * 2 + 1) * 32 * P + lane * P;
+        for (int v = 0; v < nv; ++v) {
+            // bytes inside the tile; the rest of the vector is zero-filled
+            const int inside = min(V, end - (wb + v * V)) * (int)sizeof(C);
+            if (HF) cp16(sf + v * V, in_f ? (const void *)(in_f + wb + v * V) : (const void *)vin, in_f ? inside : 0);
+            if (HS) cp16(ss + v * V, in_s ? (const void *)(in_s + wb + v * V) : (const void *)vin, in_s ? inside : 0);
         }
         if (lane < nv) cp16(lamw + buf * (P + 4) + lane * V, lam_in + wb + lane * V, 16);
         const int hb = wb & ~3;
         const int nh = (wb + nv * V - hb + 3) / 4;
-        if (lane < nh) cp16(hw + buf * hw_pitch(P) + lane * 4, p.hinfo + hb + lane * 4, 16);
+        if (lane < nh) cp16(hw + buf * HP + lane * 4, p.hinfo + hb + lane * 4, 16);
         cp_commit();
     };
 
@@ -182,63 +171,79 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
         const int t0 = tl.x, len = tl.y;
         const int wb = t0 & ~(V - 1), off = t0 - wb;
         const int nv = (off + len + V - 1) / V;
-        const int hoff = wb - (wb & ~3);
+        C *lw = lamw + buf * (P + 4);
+        uint32_t *hv = hw + buf * HP + (wb - (wb & ~3));
+        // neutralise the window's hands that lie outside the tile
+        for (int sl = lane; sl < nv * V; sl += 32) {
+            if (sl < off || sl >= off + len) {
+                lw[sl] = C(0);
+                hv[sl] = kTrash;
+            }
+        }
+        __syncwarp();
         const C *xf_s = stage + (size_t)(buf * 2 + 0) * 32 * P + lane * P;
         const C *xs_s = stage + (size_t)(buf * 2 + 1) * 32 * P + lane * P;
-        const C *lw = lamw + buf * (P + 4);
-        const uint32_t *hv = hw + buf * hw_pitch(P) + hoff;
-        bool any_tie = false;
+        C *pout = scr + out_off + wb;
+        uint32_t tie_any = 0;
 #pragma unroll
         for (int v = 0; v < W; ++v) {
-            if (v < nv) {
-                Vec xf4{}, xs4{};
-                if (HF) xf4 = *reinterpret_cast<const Vec *>(xf_s + v * V);
-                if (HS) xs4 = *reinterpret_cast<const Vec *>(xs_s + v * V);
-                C res[V];
+            if (v >= nv) break;
+            Vec xf4{}, xs4{};
+            if (HF) xf4 = *reinterpret_cast<const Vec *>(xf_s + v * V);
+            if (HS) xs4 = *reinterpret_cast<const Vec *>(xs_s + v * V);
+            C res[V];
 #pragma unroll
-                for (int k = 0; k < V; ++k) {
-                    res[k] = C(0);
-                    const int slot = v * V + k;
-                    if (slot >= off && slot < off + len) {
-                        const uint32_t h = hv[slot];
-                        const C lam = lw[slot];
-                        const int a = h & 63, b = (h >> 6) & 63;
-                        any_tie |= (h & (1u << 12)) != 0;
-                        if (HF && HS) {
-                            const C u = (fco * lam) * CF::get(xf4, k);
-                            const C vv = (sco * lam) * CF::get(xs4, k);
-                            const C w = u - vv;
-                            const C2 ra = R2[a * 32 + lane];
-                            const C2 rb = K2 == 2 ? R2[b * 32 + lane] : C2{C(0), C(0)};
-                            res[k] = (K2 == 2 ? w : C(0)) + C(2) * (Gv - ra.x - rb.x);
-                            R2[a * 32 + lane] = C2{ra.x + vv, ra.y + w};
-                            if (K2 == 2) R2[b * 32 + lane] = C2{rb.x + vv, rb.y + w};
-                            Gv += vv;
-                            Gw += w;
-                        } else if (HS) {
-                            const C vv = (sco * lam) * CF::get(xs4, k);
-                            const C ra = R1[a * 32 + lane];
-                            const C rb = K2 == 2 ? R1[b * 32 + lane] : C(0);
-                            res[k] = (K2 == 2 ? -vv : C(0)) + C(2) * (Gv - ra - rb);
-                            R1[a * 32 + lane] = ra + vv;
-                            if (K2 == 2) R1[b * 32 + lane] = rb + vv;
-                            Gv += vv;
-                        } else {
-                            const C u = (fco * lam) * CF::get(xf4, k);
-                            res[k] = K2 == 2 ? u : C(0);
-                            const C ra = R1[a * 32 + lane];
-                            const C rb = K2 == 2 ? R1[b * 32 + lane] : C(0);
-                            R1[a * 32 + lane] = ra + u;
-                            if (K2 == 2) R1[b * 32 + lane] = rb + u;
-                            Gw += u;
-                        }
+            for (int k = 0; k < V; ++k) {
+                const int slot = v * V + k;
+                const uint32_t h = hv[slot];
+                const C lam = lw[slot];
+                const int a = h & 63, b = (h >> 6) & 63;
+                tie_any |= h;
+                if (HF && HS) {
+                    const C u = (fco * lam) * CF::get(xf4, k);
+                    const C vv = (sco * lam) * CF::get(xs4, k);
+                    const C w = u - vv;
+                    const C2 ra = R2[a * 32];
+                    const C2 rb = K2 == 2 ? R2[b * 32] : C2{C(0), C(0)};
+                    res[k] = (K2 == 2 ? w : C(0)) + C(2) * (Gv - ra.x - rb.x);
+                    R2[a * 32] = C2{ra.x + vv, ra.y + w};
+                    if (K2 == 2) R2[b * 32] = C2{rb.x + vv, rb.y + w};
+                    Gv += vv;
+                    Gw += w;
+                } else if (HS) {
+                    const C vv = (sco * lam) * CF::get(xs4, k);
+                    const C ra = R1[a * 32];
+                    const C rb = K2 == 2 ? R1[b * 32] : C(0);
+                    res[k] = (K2 == 2 ? -vv : C(0)) + C(2) * (Gv - ra - rb);
+                    R1[a * 32] = ra + vv;
+                    if (K2 == 2) R1[b * 32] = rb + vv;
+                    Gv += vv;
+                } else {
+                    const C u = (fco * lam) * CF::get(xf4, k);
+                    res[k] = K2 == 2 ? u : C(0);
+                    const C ra = R1[a * 32];
+                    R1[a * 32] = ra + u;
+                    if (K2 == 2) {
+                        const C rb = R1[b * 32];
+                        R1[b * 32] = rb + u;
+                    }
+                    Gw += u;
+                }
+            }
+            if (valid) {
+                if (v * V >= off && v * V + V <= off + len) {
+                    *reinterpret_cast<Vec *>(pout + v * V) = CF::make(res);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < V; ++k) {
+                        const int slot = v * V + k;
+                        if (slot >= off && slot < off + len) pout[slot] = res[k];
                     }
                 }
-                *reinterpret_cast<Vec *>(ptile + lane * P + v * V) = CF::make(res);
             }
         }
         // tie groups of the tile: exact equal-strength term (see kernels_fast.cu)
-        if (HS && any_tie) {
+        if (HS && (tie_any & (1u << 12))) {
             for (int i = 0; i < len; ++i) {
                 const uint32_t hi = hv[off + i];
                 if (!(hi & (1u << 13))) continue;
@@ -256,28 +261,7 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
                         const C vr = (sco * lw[off + r]) * xs_s[off + r];
                         corr += r > q ? vr : -vr;
                     }
-                    ptile[lane * P + off + q] += corr;
-                }
-            }
-        }
-        __syncwarp();
-        // partial results out: 16-byte stores, element-wise at the tile edges
-        for (int idx = lane; idx < 32 * W; idx += 32) {
-            const int jj = idx / W, v = idx - jj * W;
-            if (v >= nv) continue;
-            long long o;
-            if (uni) o = jj < nvalid ? c0i.out_off + jj * ostride : -1;
-            else o = ci[jj].out_off;
-            if (o < 0) continue;
-            const Vec val = *reinterpret_cast<const Vec *>(ptile + jj * P + v * V);
-            C *dst = scr + o + wb + v * V;
-            if (v * V >= off && v * V + V <= off + len) {
-                *reinterpret_cast<Vec *>(dst) = val;
-            } else {
-#pragma unroll
-                for (int k = 0; k < V; ++k) {
-                    const int slot = v * V + k;
-                    if (slot >= off && slot < off + len) dst[k] = CF::get(val, k);
+                    if (valid) pout[off + q] += corr;
                 }
             }
         }
@@ -287,7 +271,7 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
     sums[(warp * 3 + 1) * 32 + lane] = Gw;
     __syncthreads();
 
-    // ---- phase 2: Z_k[column][card] = Pw + 2 Xv_k, into warp k's stage area
+    // ---- phase 2: Z_k[card][column] = Pw + 2 Xv_k, into warp k's stage area
     for (int c = warp; c < nc; c += nw) {
         C pw = C(0);
         for (int k = 0; k < nw; ++k) {
@@ -303,7 +287,7 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
             C r = C(0);
             if (HF && HS) r = reinterpret_cast<const C2 *>(bk + WL.r)[c * 32 + lane].x;
             else if (HS) r = reinterpret_cast<const C *>(bk + WL.r)[c * 32 + lane];
-            Zk[lane * kZPitch + c] = pw + C(2) * xv;
+            Zk[c * 32 + lane] = pw + C(2) * xv;
             xv += r;
         }
     }
@@ -319,57 +303,56 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
     }
     __syncthreads();
 
-    // ---- phase 3: finish, lane = hand
-    const C *Z = reinterpret_cast<const C *>(mine + WL.stage);
-    const C basev = sums[(warp * 3 + 2) * 32 + lane];
+    // ---- phase 3: finish (lane = column): out = lambda_out (part + base - Z[a] - Z[b])
+    const C *Z = reinterpret_cast<const C *>(mine + WL.stage) + lane;
+    const C base = sums[(warp * 3 + 2) * 32 + lane];
     for (int t = tb; t < te; ++t) {
         const int2 tl = p.tiles[t];
-        const int pos = tl.x + lane;
-        const bool pin = lane < tl.y;
-        const uint32_t hq = pin ? __ldg(&p.hinfo[pos]) : 0u;
-        const C lo = pin ? lam_out[pos] : C(0);
-        const C *za = Z + (hq & 63);
-        const C *zb = Z + ((hq >> 6) & 63);
-        C part[32];
-        if (uni) {
-            const C *src = scr + c0i.out_off + pos;
+        const int t0 = tl.x, len = tl.y;
+        const int wb = t0 & ~(V - 1), off = t0 - wb;
+        const int nv = (off + len + V - 1) / V;
+        const C *pin_ = scr + out_off + wb;
+        S *po = vout + out_off + wb;
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) part[jj] = (pin && jj < nvalid) ? src[jj * ostride] : C(0);
-        } else {
+        for (int v = 0; v < W; ++v) {
+            if (v >= nv) break;
+            const bool full = v * V >= off && v * V + V <= off + len;
+            C part[V];
+            if (valid && full) {
+                const Vec x = *reinterpret_cast<const Vec *>(pin_ + v * V);
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-                const long long o = ci[jj].out_off;
-                part[jj] = (pin && o >= 0) ? scr[o + pos] : C(0);
-            }
-        }
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-            const C bj = __shfl_sync(kFull, basev, jj);
-            C val = part[jj] + bj - za[jj * kZPitch];
-            if (K2 == 2) val -= zb[jj * kZPitch];
-            part[jj] = lo * val;
-        }
-        if (pin) {
-            if (uni) {
-                S *dst = vout + c0i.out_off + pos;
-#pragma unroll
-                for (int jj = 0; jj < 32; ++jj)
-                    if (jj < nvalid) dst[jj * ostride] = part[jj];
+                for (int k = 0; k < V; ++k) part[k] = CF::get(x, k);
             } else {
 #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) {
-                    const long long o = ci[jj].out_off;
-                    if (o >= 0) vout[o + pos] = part[jj];
+                for (int k = 0; k < V; ++k) {
+                    const int slot = v * V + k;
+                    part[k] = (valid && slot >= off && slot < off + len) ? pin_[slot] : C(0);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const int pos = wb + v * V + k;          // inside the padded tables
+                const uint32_t h = __ldg(&p.hinfo[pos]);
+                const C lo = lam_out[pos];
+                C val = part[k] + base - Z[(h & 63) * 32];
+                if (K2 == 2) val -= Z[((h >> 6) & 63) * 32];
+                part[k] = lo * val;
+            }
+            if (valid) {
+                if (full) {
+                    *reinterpret_cast<Vec *>(po + v * V) = CF::make(part);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < V; ++k) {
+                        const int slot = v * V + k;
+                        if (slot >= off && slot < off + len) po[slot] = part[k];
+                    }
                 }
             }
         }
     }
-    if (warp == nw - 1 && H + lane < hs) {
-        for (int jj = 0; jj < 32; ++jj) {
-            const long long o = ci[jj].out_off;
-            if (o >= 0) vout[o + H + lane] = S(0);
-        }
-    }
+    if (warp == nw - 1 && valid)
+        for (int q = H; q < hs; ++q) vout[out_off + q] = S(0);
 }
 
 template <typename S, int K2>
