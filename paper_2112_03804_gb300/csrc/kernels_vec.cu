@@ -303,7 +303,10 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
     }
     __syncthreads();
 
-    // ---- phase 3: finish (lane = column): out = lambda_out (part + base - Z[a] - Z[b])
+    // ---- phase 3: finish (lane = column): out = lambda_out (part + base - Z[a] - Z[b]).
+    // Per tile: the hand records and lambda_out of the window go to shared
+    // memory by cp.async while every partial of the tile is loaded, then
+    // all results are computed and stored.
     const C *Z = reinterpret_cast<const C *>(mine + WL.stage) + lane;
     const C base = sums[(warp * 3 + 2) * 32 + lane];
     for (int t = tb; t < te; ++t) {
@@ -311,45 +314,60 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
         const int t0 = tl.x, len = tl.y;
         const int wb = t0 & ~(V - 1), off = t0 - wb;
         const int nv = (off + len + V - 1) / V;
-        const C *pin_ = scr + out_off + wb;
-        S *po = vout + out_off + wb;
+        if (lane < nv) cp16(lamw + lane * V, lam_out + wb + lane * V, 16);
+        const int hb = wb & ~3;
+        const int nh = (wb + nv * V - hb + 3) / 4;
+        if (lane < nh) cp16(hw + lane * 4, p.hinfo + hb + lane * 4, 16);
+        cp_commit();
+        const C *__restrict__ pin_ = scr + out_off + wb;
+        Vec part[W];
+#pragma unroll
+        for (int v = 0; v < W; ++v) {
+            part[v] = Vec{};
+            if (v < nv && valid) {
+                if (v * V >= off && v * V + V <= off + len) {
+                    part[v] = *reinterpret_cast<const Vec *>(pin_ + v * V);
+                } else {
+                    C e[V];
+#pragma unroll
+                    for (int k = 0; k < V; ++k) {
+                        const int slot = v * V + k;
+                        e[k] = (slot >= off && slot < off + len) ? pin_[slot] : C(0);
+                    }
+                    part[v] = CF::make(e);
+                }
+            }
+        }
+        cp_wait<0>();
+        __syncwarp();
+        const C *lw = lamw;
+        const uint32_t *hv = hw + (wb - hb);
+        S *__restrict__ po = vout + out_off + wb;
 #pragma unroll
         for (int v = 0; v < W; ++v) {
             if (v >= nv) break;
-            const bool full = v * V >= off && v * V + V <= off + len;
-            C part[V];
-            if (valid && full) {
-                const Vec x = *reinterpret_cast<const Vec *>(pin_ + v * V);
-#pragma unroll
-                for (int k = 0; k < V; ++k) part[k] = CF::get(x, k);
-            } else {
-#pragma unroll
-                for (int k = 0; k < V; ++k) {
-                    const int slot = v * V + k;
-                    part[k] = (valid && slot >= off && slot < off + len) ? pin_[slot] : C(0);
-                }
-            }
+            C res[V];
 #pragma unroll
             for (int k = 0; k < V; ++k) {
-                const int pos = wb + v * V + k;          // inside the padded tables
-                const uint32_t h = __ldg(&p.hinfo[pos]);
-                const C lo = lam_out[pos];
-                C val = part[k] + base - Z[(h & 63) * 32];
+                const int slot = v * V + k;
+                const uint32_t h = hv[slot];
+                C val = CF::get(part[v], k) + base - Z[(h & 63) * 32];
                 if (K2 == 2) val -= Z[((h >> 6) & 63) * 32];
-                part[k] = lo * val;
+                res[k] = lw[slot] * val;
             }
             if (valid) {
-                if (full) {
-                    *reinterpret_cast<Vec *>(po + v * V) = CF::make(part);
+                if (v * V >= off && v * V + V <= off + len) {
+                    *reinterpret_cast<Vec *>(po + v * V) = CF::make(res);
                 } else {
 #pragma unroll
                     for (int k = 0; k < V; ++k) {
                         const int slot = v * V + k;
-                        if (slot >= off && slot < off + len) po[slot] = part[k];
+                        if (slot >= off && slot < off + len) po[slot] = res[k];
                     }
                 }
             }
         }
+        __syncwarp();
     }
     if (warp == nw - 1 && valid)
         for (int q = H; q < hs; ++q) vout[out_off + q] = S(0);
