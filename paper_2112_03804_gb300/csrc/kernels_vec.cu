@@ -6,18 +6,23 @@
 // (u, v: lambda-weighted fold and showdown inputs of an output column; K_F
 // the card-removal fold operator; Lo the compatible strictly-weaker mass).
 //
-// What this version changes, all to cut instructions per (hand, column):
-//   * staging: each warp double-buffers its 32-hand tiles with 16-byte
-//     cp.async copies straight into shared memory, [column][hand] with a
-//     pitch of 36 floats (34 doubles); the scan then reads 4 (2) hands of
-//     its column per 128-bit load, conflict free per quarter warp;
-//   * the scan over a tile is fully unrolled, and specialised by column
-//     kind: fold only (K_F alone: one per-card total), showdown only (one
-//     per-card running sum, w = -v), or both (float2 per card);
-//   * partial results leave through 128-bit stores into a [column][hand]
-//     tile and 16-byte global stores (edges of a tile stored element-wise);
-//   * the final pass (lane = hand) reads the [column][card] table at
-//     compile-time offsets.
+// What this version changes, all to cut instructions and latency per
+// (hand, column):
+//   * every global transfer is a coalesced 16-byte access: consecutive
+//     lanes move consecutive 16-byte pieces of one column's row, by
+//     cp.async into shared memory ([column][hand] tiles, pitch 36 floats /
+//     34 doubles) or by vector stores out of shared memory;
+//   * all arithmetic runs lane = column on those tiles (128-bit loads of 4
+//     or 2 hands of the lane's own row, conflict free per quarter warp);
+//   * tiles are double-buffered (the next tile is in flight while the
+//     current one is scanned or finished);
+//   * the scan is specialised by column kind: fold only (K_F alone: one
+//     per-card total), showdown only (one per-card running sum, w = -v), or
+//     both (float2 per card); hands of the staging window outside the tile
+//     get weight 0 and a spare card slot, so the unrolled scan has no range
+//     checks, and the next 4 (2) hands' records and inputs are loaded before
+//     the current ones are stored;
+//   * the per-card tables are [card][lane] (lane-private, conflict free).
 // Tie groups are corrected inside tie-aligned tiles exactly as in
 // kernels_fast.cu.  No atomics: results are bit-reproducible.
 #include "kernels.h"
@@ -76,7 +81,9 @@ __host__ __device__ inline WarpLayout warp_layout(int nc, size_t cs, int P) {
     WarpLayout L;
     size_t o = 0;
     L.r = o;     o = al16(o + (size_t)nc * 32 * 2 * cs);         // per-card state
-    L.stage = o; o = al16(o + 2 * 2 * 32 * (size_t)P * cs);      // [buf][term][col][P]
+    // [buf][term][col][P] in the scan; Z [nc][32] + [buf][col][P] afterwards
+    const size_t st = 2 * 2 * 32 * (size_t)P * cs, fin = ((size_t)nc * 32 + 2 * 32 * (size_t)P) * cs;
+    L.stage = o; o = al16(o + (st > fin ? st : fin));
     L.lam = o;   o = al16(o + 2 * (size_t)(P + 4) * cs);         // [buf][P+4]
     L.hw = o;    o = al16(o + 2 * (size_t)hw_pitch(P) * 4);      // [buf][hw_pitch] hand records
     L.ptile = o; o = al16(o + 32 * (size_t)P * cs);              // [col][P]
@@ -104,9 +111,10 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
     unsigned char *mine = smem + hdr + (size_t)warp * WL.total;
     C2 *R2 = reinterpret_cast<C2 *>(mine + WL.r) + lane;   // [card][32]: {v running, w total}
     C *R1 = reinterpret_cast<C *>(mine + WL.r) + lane;     // [card][32]: one kind
-    C *stage = reinterpret_cast<C *>(mine + WL.stage);
-    C *lamw = reinterpret_cast<C *>(mine + WL.lam);
-    uint32_t *hw = reinterpret_cast<uint32_t *>(mine + WL.hw);
+    C *stage = reinterpret_cast<C *>(mine + WL.stage);     // [buf][term][32][P]
+    C *lamw = reinterpret_cast<C *>(mine + WL.lam);        // [buf][P + 4]
+    uint32_t *hw = reinterpret_cast<uint32_t *>(mine + WL.hw);  // [buf][HP]
+    C *ptile = reinterpret_cast<C *>(mine + WL.ptile);     // [32][P]
     const S *vin = static_cast<const S *>(p.vin);
     S *vout = static_cast<S *>(p.vout);
     C *scr = static_cast<C *>(p.scratch);
@@ -114,17 +122,21 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
     const C *lam_out = static_cast<const C *>(p.lam_out);
     const long long istride = (long long)p.n_in * hs, ostride = (long long)p.n_out * hs;
     const C fco = fco_s[lane], sco = sco_s[lane];
-    // this lane's column
-    const Col cme = ci[lane];
-    const bool valid = uni ? lane < nvalid : cme.out_off >= 0;
-    const S *in_f = nullptr, *in_s = nullptr;
-    if (valid) {
-        const long long base = uni ? ci[0].in_off + lane * istride : cme.in_off;
-        const int fo = uni ? ci[0].foff : cme.foff, so = uni ? ci[0].soff : cme.soff;
-        if (fo >= 0) in_f = vin + base + fo;
-        if (so >= 0) in_s = vin + base + so;
-    }
-    const long long out_off = valid ? (uni ? ci[0].out_off + lane * ostride : cme.out_off) : 0;
+    const Col c0 = ci[0];
+    // column jj's input rows and output row (coalesced transfers use any jj)
+    auto col_in = [&](int jj, int term) -> const S * {
+        if (uni) {
+            const int o = term == 0 ? c0.foff : c0.soff;
+            return (jj < nvalid && o >= 0) ? vin + c0.in_off + jj * istride + o : nullptr;
+        }
+        const Col cj = ci[jj];
+        const int o = term == 0 ? cj.foff : cj.soff;
+        return (cj.out_off >= 0 && o >= 0) ? vin + cj.in_off + o : nullptr;
+    };
+    auto col_out = [&](int jj) -> long long {
+        if (uni) return jj < nvalid ? c0.out_off + jj * ostride : -1;
+        return ci[jj].out_off;
+    };
     // hands outside the current tile point at this card slot with weight 0
     const uint32_t kTrash = (uint32_t)(nc - 1) | ((uint32_t)(nc - 1) << 6);
 
@@ -136,18 +148,28 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
 
     // ---- phase 1: scan (lane = column)
     const int tb = p.tchunk[warp], te = p.tchunk[warp + 1];
-    auto issue = [&](int t, int buf) {
+    // 16-byte pieces of the window [wb, wb + nv V) of every column, coalesced:
+    // lane l of step i moves piece (l + 32 i) % W of column (l + 32 i) / W.
+    // Pieces past the tile end are zero-filled.
+    auto stage_tile = [&](int t, int buf) {
         const int2 tl = p.tiles[t];
-        const int wb = tl.x & ~(V - 1);
-        const int end = tl.x + tl.y;                          // first hand after the tile
+        const int wb = tl.x & ~(V - 1), end = tl.x + tl.y;
         const int nv = (end - wb + V - 1) / V;
-        C *sf = stage + (size_t)(buf * 2 + 0) * 32 * P + lane * P;
-        C *ss = stage + (size_t)(buf * 2 + 1) * 32 * P + lane * P;
-        for (int v = 0; v < nv; ++v) {
-            // bytes inside the tile; the rest of the vector is zero-filled
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const int idx = lane + 32 * i, jj = idx / W, v = idx - jj * W;
+            if (v >= nv) continue;
             const int inside = min(V, end - (wb + v * V)) * (int)sizeof(C);
-            if (HF) cp16(sf + v * V, in_f ? (const void *)(in_f + wb + v * V) : (const void *)vin, in_f ? inside : 0);
-            if (HS) cp16(ss + v * V, in_s ? (const void *)(in_s + wb + v * V) : (const void *)vin, in_s ? inside : 0);
+            if (HF) {
+                const S *src = col_in(jj, 0);
+                cp16(stage + ((size_t)(buf * 2 + 0) * 32 + jj) * P + v * V,
+                     src ? (const void *)(src + wb + v * V) : (const void *)vin, src ? inside : 0);
+            }
+            if (HS) {
+                const S *src = col_in(jj, 1);
+                cp16(stage + ((size_t)(buf * 2 + 1) * 32 + jj) * P + v * V,
+                     src ? (const void *)(src + wb + v * V) : (const void *)vin, src ? inside : 0);
+            }
         }
         if (lane < nv) cp16(lamw + buf * (P + 4) + lane * V, lam_in + wb + lane * V, 16);
         const int hb = wb & ~3;
@@ -157,11 +179,11 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
     };
 
     C Gv = C(0), Gw = C(0);
-    if (tb < te) issue(tb, 0);
+    if (tb < te) stage_tile(tb, 0);
     for (int t = tb; t < te; ++t) {
         const int buf = (t - tb) & 1;
         if (t + 1 < te) {
-            issue(t + 1, buf ^ 1);
+            stage_tile(t + 1, buf ^ 1);
             cp_wait<1>();
         } else {
             cp_wait<0>();
@@ -173,7 +195,6 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
         const int nv = (off + len + V - 1) / V;
         C *lw = lamw + buf * (P + 4);
         uint32_t *hv = hw + buf * HP + (wb - (wb & ~3));
-        // neutralise the window's hands that lie outside the tile
         for (int sl = lane; sl < nv * V; sl += 32) {
             if (sl < off || sl >= off + len) {
                 lw[sl] = C(0);
@@ -181,22 +202,35 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
             }
         }
         __syncwarp();
-        const C *xf_s = stage + (size_t)(buf * 2 + 0) * 32 * P + lane * P;
-        const C *xs_s = stage + (size_t)(buf * 2 + 1) * 32 * P + lane * P;
-        C *pout = scr + out_off + wb;
+        const C *xf_s = stage + ((size_t)(buf * 2 + 0) * 32 + lane) * P;
+        const C *xs_s = stage + ((size_t)(buf * 2 + 1) * 32 + lane) * P;
+        C *prow = ptile + lane * P;
         uint32_t tie_any = 0;
+        // loads of vector 0, then each step loads vector v+1 before storing v
+        Vec xf4{}, xs4{};
+        uint32_t h4[V];
+        C l4[V];
+        if (HF) xf4 = *reinterpret_cast<const Vec *>(xf_s);
+        if (HS) xs4 = *reinterpret_cast<const Vec *>(xs_s);
+#pragma unroll
+        for (int k = 0; k < V; ++k) { h4[k] = hv[k]; l4[k] = lw[k]; }
 #pragma unroll
         for (int v = 0; v < W; ++v) {
             if (v >= nv) break;
-            Vec xf4{}, xs4{};
-            if (HF) xf4 = *reinterpret_cast<const Vec *>(xf_s + v * V);
-            if (HS) xs4 = *reinterpret_cast<const Vec *>(xs_s + v * V);
+            Vec nf4{}, ns4{};
+            uint32_t nh4[V];
+            C nl4[V];
+            if (v + 1 < W) {
+                if (HF) nf4 = *reinterpret_cast<const Vec *>(xf_s + (v + 1) * V);
+                if (HS) ns4 = *reinterpret_cast<const Vec *>(xs_s + (v + 1) * V);
+#pragma unroll
+                for (int k = 0; k < V; ++k) { nh4[k] = hv[(v + 1) * V + k]; nl4[k] = lw[(v + 1) * V + k]; }
+            }
             C res[V];
 #pragma unroll
             for (int k = 0; k < V; ++k) {
-                const int slot = v * V + k;
-                const uint32_t h = hv[slot];
-                const C lam = lw[slot];
+                const uint32_t h = h4[k];
+                const C lam = l4[k];
                 const int a = h & 63, b = (h >> 6) & 63;
                 tie_any |= h;
                 if (HF && HS) {
@@ -222,25 +256,17 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
                     const C u = (fco * lam) * CF::get(xf4, k);
                     res[k] = K2 == 2 ? u : C(0);
                     const C ra = R1[a * 32];
+                    const C rb = K2 == 2 ? R1[b * 32] : C(0);
                     R1[a * 32] = ra + u;
-                    if (K2 == 2) {
-                        const C rb = R1[b * 32];
-                        R1[b * 32] = rb + u;
-                    }
+                    if (K2 == 2) R1[b * 32] = rb + u;
                     Gw += u;
                 }
             }
-            if (valid) {
-                if (v * V >= off && v * V + V <= off + len) {
-                    *reinterpret_cast<Vec *>(pout + v * V) = CF::make(res);
-                } else {
+            *reinterpret_cast<Vec *>(prow + v * V) = CF::make(res);
+            xf4 = nf4;
+            xs4 = ns4;
 #pragma unroll
-                    for (int k = 0; k < V; ++k) {
-                        const int slot = v * V + k;
-                        if (slot >= off && slot < off + len) pout[slot] = res[k];
-                    }
-                }
-            }
+            for (int k = 0; k < V; ++k) { h4[k] = nh4[k]; l4[k] = nl4[k]; }
         }
         // tie groups of the tile: exact equal-strength term (see kernels_fast.cu)
         if (HS && (tie_any & (1u << 12))) {
@@ -261,7 +287,27 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
                         const C vr = (sco * lw[off + r]) * xs_s[off + r];
                         corr += r > q ? vr : -vr;
                     }
-                    if (valid) pout[off + q] += corr;
+                    prow[off + q] += corr;
+                }
+            }
+        }
+        __syncwarp();
+        // partial results out, coalesced; tile edges element-wise
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const int idx = lane + 32 * i, jj = idx / W, v = idx - jj * W;
+            if (v >= nv) continue;
+            const long long o = col_out(jj);
+            if (o < 0) continue;
+            const Vec val = *reinterpret_cast<const Vec *>(ptile + jj * P + v * V);
+            C *dst = scr + o + wb + v * V;
+            if (v * V >= off && v * V + V <= off + len) {
+                *reinterpret_cast<Vec *>(dst) = val;
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const int slot = v * V + k;
+                    if (slot >= off && slot < off + len) dst[k] = CF::get(val, k);
                 }
             }
         }
@@ -273,22 +319,35 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
 
     // ---- phase 2: Z_k[card][column] = Pw + 2 Xv_k, into warp k's stage area
     for (int c = warp; c < nc; c += nw) {
-        C pw = C(0);
-        for (int k = 0; k < nw; ++k) {
-            const unsigned char *bk = smem + hdr + (size_t)k * WL.total + WL.r;
-            if (HF && HS) pw += reinterpret_cast<const C2 *>(bk)[c * 32 + lane].y;
-            else if (HS) pw -= reinterpret_cast<const C *>(bk)[c * 32 + lane];
-            else pw += reinterpret_cast<const C *>(bk)[c * 32 + lane];
+        C tot[kMaxWarps], run[kMaxWarps];
+#pragma unroll
+        for (int k = 0; k < kMaxWarps; ++k) {
+            tot[k] = run[k] = C(0);
+            if (k < nw) {
+                const unsigned char *bk = smem + hdr + (size_t)k * WL.total + WL.r;
+                if (HF && HS) {
+                    const C2 r2 = reinterpret_cast<const C2 *>(bk)[c * 32 + lane];
+                    tot[k] = r2.y;
+                    run[k] = r2.x;
+                } else if (HS) {
+                    run[k] = reinterpret_cast<const C *>(bk)[c * 32 + lane];
+                    tot[k] = -run[k];
+                } else {
+                    tot[k] = reinterpret_cast<const C *>(bk)[c * 32 + lane];
+                }
+            }
         }
+        C pw = C(0);
+#pragma unroll
+        for (int k = 0; k < kMaxWarps; ++k) pw += tot[k];
         C xv = C(0);
-        for (int k = 0; k < nw; ++k) {
-            const unsigned char *bk = smem + hdr + (size_t)k * WL.total;
-            C *Zk = reinterpret_cast<C *>(smem + hdr + (size_t)k * WL.total + WL.stage);
-            C r = C(0);
-            if (HF && HS) r = reinterpret_cast<const C2 *>(bk + WL.r)[c * 32 + lane].x;
-            else if (HS) r = reinterpret_cast<const C *>(bk + WL.r)[c * 32 + lane];
-            Zk[c * 32 + lane] = pw + C(2) * xv;
-            xv += r;
+#pragma unroll
+        for (int k = 0; k < kMaxWarps; ++k) {
+            if (k < nw) {
+                C *Zk = reinterpret_cast<C *>(smem + hdr + (size_t)k * WL.total + WL.stage);
+                Zk[c * 32 + lane] = pw + C(2) * xv;
+                xv += run[k];
+            }
         }
     }
     if (warp == 0) {
@@ -304,73 +363,97 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
     __syncthreads();
 
     // ---- phase 3: finish (lane = column): out = lambda_out (part + base - Z[a] - Z[b]).
-    // Per tile: the hand records and lambda_out of the window go to shared
-    // memory by cp.async while every partial of the tile is loaded, then
-    // all results are computed and stored.
+    // Partial tiles come back by coalesced cp.async (double-buffered, after
+    // the Z table in the stage area); results go out through ptile.
     const C *Z = reinterpret_cast<const C *>(mine + WL.stage) + lane;
+    C *pbuf = reinterpret_cast<C *>(mine + WL.stage) + (size_t)nc * 32;   // [buf][32][P]
     const C base = sums[(warp * 3 + 2) * 32 + lane];
+    auto load_partials = [&](int t, int buf) {
+        const int2 tl = p.tiles[t];
+        const int wb = tl.x & ~(V - 1), end = tl.x + tl.y;
+        const int nv = (end - wb + V - 1) / V;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const int idx = lane + 32 * i, jj = idx / W, v = idx - jj * W;
+            if (v >= nv) continue;
+            const long long o = col_out(jj);
+            // only the tile's own hands: the rest of the vector belongs to
+            // neighbouring tiles that may not be written yet
+            const int lo = max(0, tl.x - (wb + v * V)), hi = min(V, end - (wb + v * V));
+            C *dst = pbuf + ((size_t)buf * 32 + jj) * P + v * V;
+            if (o >= 0 && lo == 0 && hi == V) {
+                cp16(dst, scr + o + wb + v * V, 16);
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; ++k) dst[k] = (o >= 0 && k >= lo && k < hi) ? scr[o + wb + v * V + k] : C(0);
+            }
+        }
+        if (lane < nv) cp16(lamw + buf * (P + 4) + lane * V, lam_out + wb + lane * V, 16);
+        const int hb = wb & ~3;
+        const int nh = (wb + nv * V - hb + 3) / 4;
+        if (lane < nh) cp16(hw + buf * HP + lane * 4, p.hinfo + hb + lane * 4, 16);
+        cp_commit();
+    };
+    if (tb < te) load_partials(tb, 0);
     for (int t = tb; t < te; ++t) {
+        const int buf = (t - tb) & 1;
+        if (t + 1 < te) {
+            load_partials(t + 1, buf ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncwarp();
         const int2 tl = p.tiles[t];
         const int t0 = tl.x, len = tl.y;
         const int wb = t0 & ~(V - 1), off = t0 - wb;
         const int nv = (off + len + V - 1) / V;
-        if (lane < nv) cp16(lamw + lane * V, lam_out + wb + lane * V, 16);
-        const int hb = wb & ~3;
-        const int nh = (wb + nv * V - hb + 3) / 4;
-        if (lane < nh) cp16(hw + lane * 4, p.hinfo + hb + lane * 4, 16);
-        cp_commit();
-        const C *__restrict__ pin_ = scr + out_off + wb;
-        Vec part[W];
-#pragma unroll
-        for (int v = 0; v < W; ++v) {
-            part[v] = Vec{};
-            if (v < nv && valid) {
-                if (v * V >= off && v * V + V <= off + len) {
-                    part[v] = *reinterpret_cast<const Vec *>(pin_ + v * V);
-                } else {
-                    C e[V];
-#pragma unroll
-                    for (int k = 0; k < V; ++k) {
-                        const int slot = v * V + k;
-                        e[k] = (slot >= off && slot < off + len) ? pin_[slot] : C(0);
-                    }
-                    part[v] = CF::make(e);
-                }
-            }
-        }
-        cp_wait<0>();
-        __syncwarp();
-        const C *lw = lamw;
-        const uint32_t *hv = hw + (wb - hb);
-        S *__restrict__ po = vout + out_off + wb;
+        const C *lw = lamw + buf * (P + 4);
+        const uint32_t *hv = hw + buf * HP + (wb - (wb & ~3));
+        const C *prow_in = pbuf + ((size_t)buf * 32 + lane) * P;
+        C *prow = ptile + lane * P;
 #pragma unroll
         for (int v = 0; v < W; ++v) {
             if (v >= nv) break;
+            const Vec x = *reinterpret_cast<const Vec *>(prow_in + v * V);
             C res[V];
 #pragma unroll
             for (int k = 0; k < V; ++k) {
                 const int slot = v * V + k;
                 const uint32_t h = hv[slot];
-                C val = CF::get(part[v], k) + base - Z[(h & 63) * 32];
+                C val = CF::get(x, k) + base - Z[(h & 63) * 32];
                 if (K2 == 2) val -= Z[((h >> 6) & 63) * 32];
                 res[k] = lw[slot] * val;
             }
-            if (valid) {
-                if (v * V >= off && v * V + V <= off + len) {
-                    *reinterpret_cast<Vec *>(po + v * V) = CF::make(res);
-                } else {
+            *reinterpret_cast<Vec *>(prow + v * V) = CF::make(res);
+        }
+        __syncwarp();
 #pragma unroll
-                    for (int k = 0; k < V; ++k) {
-                        const int slot = v * V + k;
-                        if (slot >= off && slot < off + len) po[slot] = res[k];
-                    }
+        for (int i = 0; i < W; ++i) {
+            const int idx = lane + 32 * i, jj = idx / W, v = idx - jj * W;
+            if (v >= nv) continue;
+            const long long o = col_out(jj);
+            if (o < 0) continue;
+            const Vec val = *reinterpret_cast<const Vec *>(ptile + jj * P + v * V);
+            S *dst = vout + o + wb + v * V;
+            if (v * V >= off && v * V + V <= off + len) {
+                *reinterpret_cast<Vec *>(dst) = val;
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const int slot = v * V + k;
+                    if (slot >= off && slot < off + len) dst[k] = CF::get(val, k);
                 }
             }
         }
         __syncwarp();
     }
-    if (warp == nw - 1 && valid)
-        for (int q = H; q < hs; ++q) vout[out_off + q] = S(0);
+    if (warp == nw - 1 && H + lane < hs) {
+        for (int jj = 0; jj < 32; ++jj) {
+            const long long o = col_out(jj);
+            if (o >= 0) vout[o + H + lane] = S(0);
+        }
+    }
 }
 
 template <typename S, int K2>
