@@ -54,6 +54,7 @@ struct kps_game {
     // tie-aligned tile lists on the device, per warp count
     struct Tiles {
         int2 *dev = nullptr;
+        std::vector<int2> host;
         std::vector<int> tchunk;
     };
     std::map<int, Tiles> tiles;
@@ -201,12 +202,34 @@ int fast_warps(int storage, int nc, int H, bool vec) {
 kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int storage, kps_dtype dt,
                        cudaStream_t stream) {
     const kps::HostGame &h = g->host;
-    // 16-byte async copies need 16-byte aligned vectors (FP32/FP64 storage)
+    // Kernel choice: tensor-memory partials (FP32 arithmetic storages), else
+    // the vectorised path (16-byte aligned FP32/FP64), else scalar staging.
+    // KPS_KERNEL=tmem|vec|fast forces one where it applies.
+    const char *force = std::getenv("KPS_KERNEL");
     const bool aligned = ((reinterpret_cast<uintptr_t>(sp.vin) | reinterpret_cast<uintptr_t>(sp.vout)) & 15) == 0;
-    const bool vec = aligned && (storage == kps::kStoreF32 || storage == kps::kStoreF64) && sp.nc <= 64 &&
-                     std::getenv("KPS_NO_VEC") == nullptr;
-    const int nw = fast_warps(storage, sp.nc, h.H, vec);
-    const size_t need = vec ? kps::vec_smem_bytes(storage, sp.nc, nw) : kps::fast_smem_bytes(storage, sp.nc, nw);
+    const bool vec_ok = aligned && (storage == kps::kStoreF32 || storage == kps::kStoreF64) && sp.nc <= 64 &&
+                        std::getenv("KPS_NO_VEC") == nullptr;
+    const bool tmem_ok = storage != kps::kStoreF64 && sp.nc <= 66;
+    enum { kTmem, kVec, kScalar } path = tmem_ok ? kTmem : vec_ok ? kVec : kScalar;
+    if (force) {
+        if (!std::strcmp(force, "vec") && vec_ok) path = kVec;
+        else if (!std::strcmp(force, "fast")) path = kScalar;
+        else if (!std::strcmp(force, "tmem") && tmem_ok) path = kTmem;
+    }
+    int nw;
+    if (path == kTmem) {
+        // enough warps that every chunk fits a warp's tensor-memory region
+        nw = std::max((h.H + 199) / 200, std::min(kps::kMaxWarps, (h.H + kps::kTile - 1) / kps::kTile));
+        if (const char *env = std::getenv("KPS_WARPS")) {
+            const int w = std::atoi(env);
+            if (w >= 1 && w <= kps::kMaxWarps && (long long)w * kps::kTmemChunk >= (long long)h.H + 64) nw = w;
+        }
+        if (nw > kps::kMaxWarps || kps::tmem_smem_bytes(sp.nc, nw) > (size_t)kps::max_dyn_smem()) path = kScalar;
+    }
+    const bool vec = path == kVec;
+    if (path != kTmem) nw = fast_warps(storage, sp.nc, h.H, vec);
+    const size_t need = path == kTmem ? kps::tmem_smem_bytes(sp.nc, nw)
+                        : vec ? kps::vec_smem_bytes(storage, sp.nc, nw) : kps::fast_smem_bytes(storage, sp.nc, nw);
     if (need > (size_t)kps::max_dyn_smem())
         return fail(KPS_ENOTSUP, "card count too large for shared memory");
     auto it = g->tiles.find(nw);
@@ -215,6 +238,7 @@ kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int stor
         std::vector<std::pair<int, int>> tl = kps::tie_tiles(h, nw, kps::kTile, t.tchunk);
         std::vector<int2> host(tl.size());
         for (size_t i = 0; i < tl.size(); ++i) host[i] = make_int2(tl[i].first, tl[i].second);
+        t.host = host;
         cudaError_t e = cudaMalloc(&t.dev, std::max<size_t>(1, host.size()) * sizeof(int2));
         if (e != cudaSuccess) return fail(KPS_ENOMEM, "tile table");
         if (!host.empty()) {
@@ -227,8 +251,19 @@ kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int stor
         }
         it = g->tiles.emplace(nw, std::move(t)).first;
     }
+    if (path == kTmem) {
+        // every chunk must fit a warp's tensor-memory region
+        const auto &tc = it->second.tchunk;
+        bool fits = true;
+        for (int k = 0; k < nw && fits; ++k) {
+            if (tc[k] == tc[k + 1]) continue;
+            const int2 a = it->second.host[tc[k]], b = it->second.host[tc[k + 1] - 1];
+            fits = b.x + b.y - a.x <= kps::kTmemChunk;
+        }
+        if (!fits) return fail(KPS_ENOTSUP, "hand chunk too long for tensor memory");
+    }
     void *scratch = sp.vout;
-    if (storage == kps::kStoreBF16 || storage == kps::kStoreF16) {
+    if (path != kTmem && (storage == kps::kStoreBF16 || storage == kps::kStoreF16)) {
         const size_t need = (size_t)sp.batch * sp.n_out * h.hs * sizeof(float);
         if (g->scratch_bytes < need) {
             if (g->scratch) cudaFree(g->scratch);
@@ -263,7 +298,8 @@ kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int stor
     (void)dir;
     (void)dt;
     cudaError_t e;
-    if (vec) e = kps::launch_vec_scan(p, storage, h.k, stream);
+    if (path == kTmem) e = kps::launch_tmem_scan(p, storage, h.k, stream);
+    else if (vec) e = kps::launch_vec_scan(p, storage, h.k, stream);
     else e = kps::launch_fast_scan(p, storage, h.k, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launching the payoff scan");
     return KPS_OK;

@@ -78,3 +78,14 @@ size_t vec_smem_bytes(int storage, int nc, int nw);
 cudaError_t launch_vec_scan(const FastParams &p, int storage, int cards_per_hand, cudaStream_t stream);
 
 }  // namespace kps
+
+namespace kps {
+
+// Tensor-memory path (FP32 arithmetic; FP32/BF16/FP16 storage): partial
+// results stay in tensor memory.  Every warp's chunk must span at most
+// kTmemChunk hands.  `scratch` is unused.
+constexpr int kTmemChunk = 224;
+size_t tmem_smem_bytes(int nc, int nw);
+cudaError_t launch_tmem_scan(const FastParams &p, int storage, int cards_per_hand, cudaStream_t stream);
+
+}  // namespace kps

@@ -1,0 +1,450 @@
+// Kronecker-form payoff products with partial results held in tensor memory
+// (sm_103a).  FP32 arithmetic; FP32, BF16 or FP16 storage.
+//
+// Mathematics as in kernels.cu:
+//   out / lambda_out = K_F(u - v) + 2 Lo(v) + TieC(v)
+// with u, v the lambda-weighted fold and showdown inputs of an output column
+// (its fold terminal and its showdown terminal, Sec. 3 / Prop. 1), K_F the
+// card-removal fold operator and Lo the compatible strictly-weaker mass of
+// the strength-ordered scan (the inverse of Technique B's bidiagonal D).
+//
+// Organisation (one CTA = 32 output columns, one per lane, up to 8 warps):
+//   * each warp scans one tie-aligned chunk of the hand order; its inputs are
+//     prefetched tile by tile (32 hands) into registers with coalesced loads
+//     (lane = hand) and transposed through shared memory, while the previous
+//     tile is scanned (lane = column; per-card state [card][lane] in shared
+//     memory, conflict free, two hands per step when they share no card);
+//   * the partial result of every (hand, column) goes to tensor memory: the
+//     warp's 32 lanes are the 32 columns, a tensor-memory column is a hand,
+//     so a tile leaves in one tcgen05.st and comes back in one tcgen05.ld.
+//     Shared memory keeps only per-warp state (about 25 KB), the partial
+//     results never travel to global memory;
+//   * after the chunks' per-card sums are combined (fold totals and the mass
+//     of earlier chunks), each warp finishes its hands and writes the output
+//     with coalesced stores (lane = hand).
+// Scans are specialised by column kind: fold only, showdown only, or both.
+// No atomics: results are bit-reproducible.
+#include "kernels.h"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+namespace kps {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPitch = 33;         // row pitch of [hand][column] tiles
+constexpr int kRegion = 256;       // tensor-memory columns owned by one warp
+
+template <typename S> struct Num;
+template <> struct Num<float> {
+    __device__ static float load(const float *p) { return __ldg(p); }
+    __device__ static float conv(float x) { return x; }
+};
+template <> struct Num<__nv_bfloat16> {
+    __device__ static float load(const __nv_bfloat16 *p) {
+        return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p))));
+    }
+    __device__ static __nv_bfloat16 conv(float x) { return __float2bfloat16_rn(x); }
+};
+template <> struct Num<__half> {
+    __device__ static float load(const __half *p) {
+        return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p))));
+    }
+    __device__ static __half conv(float x) { return __float2half_rn(x); }
+};
+
+struct Col {
+    long long in_off;
+    long long out_off;   // -1 = no column
+    int foff, soff;      // -1 = no such terminal
+};
+
+enum Kind { kKindF = 1, kKindS = 2, kKindFS = 3 };
+
+// ---- tensor memory (tcgen05) ---------------------------------------------
+__device__ __forceinline__ void tm_alloc(uint32_t *dst_smem, uint32_t ncols) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(dst_smem);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s), "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tm_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;"); }
+__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;"); }
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;"); }
+
+// 32 consecutive tensor-memory columns of this warp's lanes <-> r[0..31]
+__device__ __forceinline__ void tm_st32(uint32_t taddr, const float *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "f"(r[0]), "f"(r[1]), "f"(r[2]), "f"(r[3]), "f"(r[4]), "f"(r[5]), "f"(r[6]), "f"(r[7]), "f"(r[8]), "f"(r[9]),
+        "f"(r[10]), "f"(r[11]), "f"(r[12]), "f"(r[13]), "f"(r[14]), "f"(r[15]), "f"(r[16]), "f"(r[17]), "f"(r[18]),
+        "f"(r[19]), "f"(r[20]), "f"(r[21]), "f"(r[22]), "f"(r[23]), "f"(r[24]), "f"(r[25]), "f"(r[26]), "f"(r[27]),
+        "f"(r[28]), "f"(r[29]), "f"(r[30]), "f"(r[31]));
+}
+__device__ __forceinline__ void tm_ld32(uint32_t taddr, float *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+        "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]), "=f"(r[8]),
+          "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15]), "=f"(r[16]),
+          "=f"(r[17]), "=f"(r[18]), "=f"(r[19]), "=f"(r[20]), "=f"(r[21]), "=f"(r[22]), "=f"(r[23]), "=f"(r[24]),
+          "=f"(r[25]), "=f"(r[26]), "=f"(r[27]), "=f"(r[28]), "=f"(r[29]), "=f"(r[30]), "=f"(r[31])
+        : "r"(taddr));
+}
+
+// Shared memory: header then, per warp, state [nc][32] float2,
+// stage [32][kPitch] float2 and a [32][kPitch] float tile.
+__host__ __device__ inline size_t tm_header_bytes(int nw) {
+    return (32 * sizeof(Col) + (2 * 32 + (size_t)nw * 3 * 32) * sizeof(float) + 16 + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t tm_warp_floats(int nc) { return 2 * (size_t)nc * 32 + 3 * 32 * kPitch; }
+
+struct Cta {
+    const Col *ci;
+    float *sums;      // [nw][3][32]
+    bool uni;         // columns share a sequence and take consecutive vectors
+    int nvalid;
+    uint32_t tmem;    // tensor-memory base address of the CTA
+};
+
+template <typename S, int K2, int KIND>
+__device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem, const Cta &cta,
+                                        const float *fco_s, const float *sco_s) {
+    constexpr bool HF = (KIND & kKindF) != 0, HS = (KIND & kKindS) != 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = p.nw, nc = p.nc;
+    const int H = p.H, hs = p.hs;
+    const Col *ci = cta.ci;
+    float *sums = cta.sums;
+    const bool uni = cta.uni;
+    const int nvalid = cta.nvalid;
+    float *wbase = reinterpret_cast<float *>(smem + tm_header_bytes(nw));
+    float *mine = wbase + (size_t)warp * tm_warp_floats(nc);
+    float2 *R = reinterpret_cast<float2 *>(mine);            // [card][32]: {v running, w total}
+    float2 *stage = R + (size_t)nc * 32;                     // [hand][kPitch]: lambda_in * {x_f, x_s}
+    float *ptile = reinterpret_cast<float *>(stage + 32 * kPitch);   // [hand][kPitch]
+    const S *vin = static_cast<const S *>(p.vin);
+    S *vout = static_cast<S *>(p.vout);
+    const float *lam_in = static_cast<const float *>(p.lam_in);
+    const float *lam_out = static_cast<const float *>(p.lam_out);
+    const long long istride = (long long)p.n_in * hs, ostride = (long long)p.n_out * hs;
+    const float fco = fco_s[lane], sco = sco_s[lane];
+    const Col c0i = ci[0];
+    // this warp's tensor-memory lanes (= its 32 columns) and column region
+    const uint32_t treg = cta.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * kRegion);
+
+    for (int c = 0; c < nc; ++c) R[c * 32 + lane] = make_float2(0.f, 0.f);
+
+    // ---- phase 1: scan the chunk's tiles (lane = column)
+    const int tb = p.tchunk[warp], te = p.tchunk[warp + 1];
+    const int cstart = tb < te ? p.tiles[tb].x : 0;
+    float Gv = 0.f, Gw = 0.f;
+    float xf[32], xs[32];
+    float lin_n = 0.f;
+    uint32_t h_n = 0u;
+    // next tile's inputs, lane = hand, one register per column
+    auto fetch = [&](int t) {
+        const int2 tl = p.tiles[t];
+        const int pos = tl.x + lane;
+        const bool pin = lane < tl.y;
+        lin_n = pin ? lam_in[pos] : 0.f;
+        h_n = pin ? __ldg(&p.hinfo[pos]) : 0u;
+        if (uni) {
+            const S *fb = vin + c0i.in_off + pos + c0i.foff;
+            const S *sb = vin + c0i.in_off + pos + c0i.soff;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                const bool ok = pin && jj < nvalid;
+                xf[jj] = (HF && ok && c0i.foff >= 0) ? Num<S>::load(fb + jj * istride) : 0.f;
+                xs[jj] = (HS && ok && c0i.soff >= 0) ? Num<S>::load(sb + jj * istride) : 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                const Col cj = ci[jj];
+                const S *base = vin + cj.in_off + pos;
+                xf[jj] = (HF && pin && cj.foff >= 0) ? Num<S>::load(base + cj.foff) : 0.f;
+                xs[jj] = (HS && pin && cj.soff >= 0) ? Num<S>::load(base + cj.soff) : 0.f;
+            }
+        }
+    };
+    if (tb < te) fetch(tb);
+    for (int t = tb; t < te; ++t) {
+        const int2 tl = p.tiles[t];
+        const int t0 = tl.x, len = tl.y;
+        const float lin = lin_n;
+        const uint32_t hreg = h_n;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) stage[lane * kPitch + jj] = make_float2(lin * xf[jj], lin * xs[jj]);
+        __syncwarp();
+        if (t + 1 < te) fetch(t + 1);
+        for (int i = 0; i < len;) {
+            const uint32_t h1 = __shfl_sync(kFull, hreg, i);
+            const uint32_t h2 = __shfl_sync(kFull, hreg, min(i + 1, 31));
+            const int a1 = h1 & 63, b1 = (h1 >> 6) & 63;
+            const float2 x1 = stage[i * kPitch + lane];
+            const float u1 = HF ? fco * x1.x : 0.f, v1 = HS ? sco * x1.y : 0.f, w1 = u1 - v1;
+            if ((h1 & (1u << 15)) && i + 1 < len) {
+                // the next hand shares no card: both hands' loads are independent
+                const int a2 = h2 & 63, b2 = (h2 >> 6) & 63;
+                const float2 x2 = stage[(i + 1) * kPitch + lane];
+                const float u2 = HF ? fco * x2.x : 0.f, v2 = HS ? sco * x2.y : 0.f, w2 = u2 - v2;
+                const float2 ra1 = R[a1 * 32 + lane], ra2 = R[a2 * 32 + lane];
+                float2 rb1 = make_float2(0.f, 0.f), rb2 = make_float2(0.f, 0.f);
+                if (K2 == 2) {
+                    rb1 = R[b1 * 32 + lane];
+                    rb2 = R[b2 * 32 + lane];
+                }
+                const float g1 = Gv + v1;
+                ptile[i * kPitch + lane] = (K2 == 2 ? w1 : 0.f) + (HS ? 2.f * (Gv - ra1.x - rb1.x) : 0.f);
+                ptile[(i + 1) * kPitch + lane] = (K2 == 2 ? w2 : 0.f) + (HS ? 2.f * (g1 - ra2.x - rb2.x) : 0.f);
+                R[a1 * 32 + lane] = make_float2(ra1.x + v1, ra1.y + w1);
+                R[a2 * 32 + lane] = make_float2(ra2.x + v2, ra2.y + w2);
+                if (K2 == 2) {
+                    R[b1 * 32 + lane] = make_float2(rb1.x + v1, rb1.y + w1);
+                    R[b2 * 32 + lane] = make_float2(rb2.x + v2, rb2.y + w2);
+                }
+                Gv = g1 + v2;
+                Gw = (Gw + w1) + w2;
+                i += 2;
+            } else {
+                const float2 ra1 = R[a1 * 32 + lane];
+                const float2 rb1 = K2 == 2 ? R[b1 * 32 + lane] : make_float2(0.f, 0.f);
+                ptile[i * kPitch + lane] = (K2 == 2 ? w1 : 0.f) + (HS ? 2.f * (Gv - ra1.x - rb1.x) : 0.f);
+                R[a1 * 32 + lane] = make_float2(ra1.x + v1, ra1.y + w1);
+                if (K2 == 2) R[b1 * 32 + lane] = make_float2(rb1.x + v1, rb1.y + w1);
+                Gv += v1;
+                Gw += w1;
+                i += 1;
+            }
+        }
+        // Tie groups (never split across a tile): the scan counted earlier
+        // members as weaker; the exact equal-strength term adds the later
+        // compatible members and removes the earlier ones.
+        if (HS) {
+            uint32_t last = __ballot_sync(kFull, lane < len && (hreg & (1u << 13)) != 0u);
+            while (last) {
+                const int i = __ffs(last) - 1;
+                last &= last - 1;
+                const uint32_t hi = __shfl_sync(kFull, hreg, i);
+                const int g0 = i - (int)(hi >> 16);
+                for (int q = g0; q <= i; ++q) {
+                    const uint32_t hq = __shfl_sync(kFull, hreg, q);
+                    float corr = 0.f;
+                    for (int r = g0; r <= i; ++r) {
+                        const uint32_t hr = __shfl_sync(kFull, hreg, r);
+                        if (r == q) continue;
+                        const int qa = hq & 63, qb = (hq >> 6) & 63, ra = hr & 63, rb = (hr >> 6) & 63;
+                        bool share = qa == ra;
+                        if (K2 == 2) share = share || qa == rb || qb == ra || qb == rb;
+                        if (share) continue;
+                        const float vr = sco * stage[r * kPitch + lane].y;
+                        corr += r > q ? vr : -vr;
+                    }
+                    ptile[q * kPitch + lane] += corr;
+                }
+            }
+        }
+        __syncwarp();
+        // the tile's partial results to tensor memory (lane = column)
+        float r[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) r[k] = ptile[k * kPitch + lane];
+        tm_st32(treg + (uint32_t)(t0 - cstart), r);
+        __syncwarp();
+    }
+    tm_wait_st();
+    sums[(warp * 3 + 0) * 32 + lane] = Gv;
+    sums[(warp * 3 + 1) * 32 + lane] = Gw;
+    __syncthreads();
+
+    // ---- phase 2: per (card, column): fold total Pw and the card's mass Xv_k
+    // in earlier chunks; Z_k[card][column] = Pw + 2 Xv_k goes to warp k's
+    // (now free) staging area.  base_k = Tw + 2 Xg_k.
+    for (int c = warp; c < nc; c += nw) {
+        float tot[kMaxWarps], run[kMaxWarps];
+#pragma unroll
+        for (int k = 0; k < kMaxWarps; ++k) {
+            tot[k] = run[k] = 0.f;
+            if (k < nw) {
+                const float2 s2 = reinterpret_cast<const float2 *>(wbase + (size_t)k * tm_warp_floats(nc))[c * 32 + lane];
+                run[k] = HS ? s2.x : 0.f;
+                tot[k] = HF ? s2.y : -s2.x;
+            }
+        }
+        float pw = 0.f;
+#pragma unroll
+        for (int k = 0; k < kMaxWarps; ++k) pw += tot[k];
+        float xv = 0.f;
+#pragma unroll
+        for (int k = 0; k < kMaxWarps; ++k) {
+            if (k < nw) {
+                float *Zk = wbase + (size_t)k * tm_warp_floats(nc) + 2 * (size_t)nc * 32;
+                Zk[c * 32 + lane] = pw + 2.f * xv;
+                xv += run[k];
+            }
+        }
+    }
+    if (warp == 0) {
+        float tw = 0.f;
+        for (int k = 0; k < nw; ++k) tw += HF ? sums[(k * 3 + 1) * 32 + lane] : -sums[(k * 3 + 0) * 32 + lane];
+        float xg = 0.f;
+        for (int k = 0; k < nw; ++k) {
+            sums[(k * 3 + 2) * 32 + lane] = tw + 2.f * xg;
+            xg += sums[(k * 3 + 0) * 32 + lane];
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3: finish each tile from tensor memory (lane = column), then
+    // write it out with coalesced stores (lane = hand)
+    const float *Z = mine + 2 * (size_t)nc * 32 + lane;
+    const float base = sums[(warp * 3 + 2) * 32 + lane];
+    for (int t = tb; t < te; ++t) {
+        const int2 tl = p.tiles[t];
+        const int t0 = tl.x, len = tl.y;
+        const int pos = t0 + lane;
+        const bool pin = lane < len;
+        const uint32_t hq = pin ? __ldg(&p.hinfo[pos]) : 0u;
+        const float lo = pin ? lam_out[pos] : 0.f;
+        float r[32];
+        tm_ld32(treg + (uint32_t)(t0 - cstart), r);
+        tm_wait_ld();
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t h = __shfl_sync(kFull, hq, k);
+            const float l = __shfl_sync(kFull, lo, k);
+            float val = r[k] + base - Z[(h & 63) * 32];
+            if (K2 == 2) val -= Z[((h >> 6) & 63) * 32];
+            ptile[k * kPitch + lane] = l * val;
+        }
+        __syncwarp();
+        if (pin) {
+            if (uni) {
+                S *dst = vout + c0i.out_off + pos;
+                for (int jj = 0; jj < nvalid; ++jj) dst[jj * ostride] = Num<S>::conv(ptile[lane * kPitch + jj]);
+            } else {
+                for (int jj = 0; jj < 32; ++jj) {
+                    const long long o = ci[jj].out_off;
+                    if (o >= 0) vout[o + pos] = Num<S>::conv(ptile[lane * kPitch + jj]);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // padding of every row
+    if (warp == nw - 1 && H + lane < hs) {
+        for (int jj = 0; jj < 32; ++jj) {
+            const long long o = ci[jj].out_off;
+            if (o >= 0) vout[o + H + lane] = Num<S>::conv(0.f);
+        }
+    }
+}
+
+template <typename S, int K2>
+__global__ void __launch_bounds__(32 * kMaxWarps)
+tmem_scan_kernel(const FastParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int hs = p.hs, nw = p.nw;
+    Col *ci = reinterpret_cast<Col *>(smem_raw);
+    float *fco_s = reinterpret_cast<float *>(smem_raw + 32 * sizeof(Col));
+    float *sco_s = fco_s + 32;
+    float *sums = sco_s + 32;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sums + (size_t)nw * 3 * 32);
+    // two warps share a lane quadrant when more than four run: 512 columns
+    const uint32_t ncols = nw > 4 ? 2 * kRegion : kRegion;
+    if (threadIdx.x < 32) tm_alloc(tmem_slot, ncols);
+    int kinds = 0;
+    if (threadIdx.x < 32) {
+        const long long col = (long long)blockIdx.x * 32 + threadIdx.x;
+        Col c;
+        float f = 0.f, s = 0.f;
+        if (col < (long long)p.n_out * p.batch) {
+            const int sg = (int)(col / p.batch), b = (int)(col % p.batch);
+            const int fc = p.fcol[sg], sc = p.scol[sg];
+            c.in_off = (long long)b * p.n_in * hs;
+            c.out_off = ((long long)b * p.n_out + sg) * hs;
+            c.foff = fc >= 0 ? fc * hs : -1;
+            c.soff = sc >= 0 ? sc * hs : -1;
+            if (fc >= 0) f = static_cast<const float *>(p.fcoef)[sg];
+            if (sc >= 0) s = static_cast<const float *>(p.scoef)[sg];
+        } else {
+            c.in_off = 0;
+            c.out_off = -1;
+            c.foff = c.soff = -1;
+        }
+        ci[threadIdx.x] = c;
+        fco_s[threadIdx.x] = f;
+        sco_s[threadIdx.x] = s;
+        kinds = (c.foff >= 0 ? 1 : 0) | (c.soff >= 0 ? 2 : 0);
+    }
+    tm_fence_before();
+    const bool has_f = __syncthreads_or(kinds & 1) != 0;
+    tm_fence_after();
+    const bool has_s = __syncthreads_or(kinds & 2) != 0;
+    const Col c0i = ci[0];
+    int same = 1, valid = 0;
+    if (threadIdx.x < 32) {
+        const Col c = ci[threadIdx.x];
+        if (c.out_off >= 0) {
+            valid = 1;
+            same = c.foff == c0i.foff && c.soff == c0i.soff &&
+                   c.in_off == c0i.in_off + (long long)threadIdx.x * p.n_in * hs &&
+                   c.out_off == c0i.out_off + (long long)threadIdx.x * p.n_out * hs;
+        }
+    }
+    Cta cta;
+    cta.ci = ci;
+    cta.sums = sums;
+    cta.uni = __syncthreads_and(same) != 0;
+    cta.nvalid = __syncthreads_count(valid);
+    cta.tmem = *tmem_slot;
+    if (has_f && has_s) tm_body<S, K2, kKindFS>(p, smem_raw, cta, fco_s, sco_s);
+    else if (has_s) tm_body<S, K2, kKindS>(p, smem_raw, cta, fco_s, sco_s);
+    else tm_body<S, K2, kKindF>(p, smem_raw, cta, fco_s, sco_s);
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (threadIdx.x < 32) tm_dealloc(cta.tmem, ncols);
+}
+
+template <typename S, int K2>
+cudaError_t launch_t(const FastParams &p, size_t smem, cudaStream_t stream) {
+    static size_t configured = 0;
+    auto fn = tmem_scan_kernel<S, K2>;
+    if (configured < smem) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    const long long ncols = (long long)p.n_out * p.batch;
+    const long long blocks = (ncols + 31) / 32;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    fn<<<(unsigned)blocks, 32 * p.nw, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tmem_smem_bytes(int nc, int nw) { return tm_header_bytes(nw) + (size_t)nw * tm_warp_floats(nc) * 4; }
+
+cudaError_t launch_tmem_scan(const FastParams &p, int storage, int k, cudaStream_t stream) {
+    if (p.nc > 66 || p.nw < 1 || p.nw > kMaxWarps) return cudaErrorInvalidValue;
+    const size_t smem = tmem_smem_bytes(p.nc, p.nw);
+    switch (storage) {
+        case kStoreF32: return k == 1 ? launch_t<float, 1>(p, smem, stream) : launch_t<float, 2>(p, smem, stream);
+        case kStoreBF16:
+            return k == 1 ? launch_t<__nv_bfloat16, 1>(p, smem, stream) : launch_t<__nv_bfloat16, 2>(p, smem, stream);
+        case kStoreF16: return k == 1 ? launch_t<__half, 1>(p, smem, stream) : launch_t<__half, 2>(p, smem, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace kps

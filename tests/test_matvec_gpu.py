@@ -70,9 +70,15 @@ def river():
     return spec, OracleGame(spec), kps.Game(spec), library_order(spec["strength"])
 
 
+KERNELS = ["tmem", "vec", "fast"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("transpose", [False, True])
-def test_river_fp32_ragged_batch(river, transpose):
-    """1081 hands, 43+43 sequences, 37 vectors: many tiles, a ragged last CTA."""
+def test_river_fp32_ragged_batch(river, transpose, kernel, monkeypatch):
+    """1081 hands, 43+43 sequences, 37 vectors: many tiles, a ragged last CTA,
+    through each kernel path."""
+    monkeypatch.setenv("KPS_KERNEL", kernel)
     spec, og, g, order = river
     v = _inputs(og, 37, seed=23, transpose=transpose)
     got, _ = _run(g, order, v, transpose, kps.F32)
@@ -90,8 +96,10 @@ def test_river_fp64(river):
     assert normwise_error(got, og.matvec_AT(x)) <= 1e-12
 
 
+@pytest.mark.parametrize("kernel", ["tmem", "fast"])
 @pytest.mark.parametrize("dt", [kps.BF16, kps.F16])
-def test_river_half_storage(river, dt):
+def test_river_half_storage(river, dt, kernel, monkeypatch):
+    monkeypatch.setenv("KPS_KERNEL", kernel)
     spec, og, g, order = river
     v = _inputs(og, 5, seed=37, transpose=False)
     rounded = torch.from_numpy(v).to(TDT[dt]).to(torch.float64).numpy()
@@ -169,12 +177,15 @@ def river_ties():
     return spec, OracleGame(spec), kps.Game(spec), library_order(spec["strength"])
 
 
-@pytest.mark.parametrize("warps", ["1", "3", "8"])
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("warps", ["1", "3", "6", "8"])
 @pytest.mark.parametrize("transpose", [False, True])
-def test_river_many_ties_warp_counts(river_ties, warps, transpose, monkeypatch):
-    """Tie groups inside tiles, several hand chunks per CTA."""
+def test_river_many_ties_warp_counts(river_ties, warps, transpose, kernel, monkeypatch):
+    """Tie groups inside tiles, several hand chunks per CTA, each kernel path
+    (FP64 runs on the vectorised or scalar path)."""
     spec, og, g, order = river_ties
     monkeypatch.setenv("KPS_WARPS", warps)
+    monkeypatch.setenv("KPS_KERNEL", kernel)
     v = _inputs(og, 5, seed=53, transpose=transpose)
     want = og.matvec_AT(v) if transpose else og.matvec_A(v)
     got, _ = _run(g, order, v, transpose, kps.F64)
