@@ -29,7 +29,8 @@ METRIC = "payoff matvecs/sec and HBM GB/s (fraction of peak); solver wall-time t
 UNIT = "matvecs/s"
 BATCH = 1024
 WORKLOAD = "river endgame, 1081 hands, 43+43 sequences, 57 terminals, batch 1024, fp32"
-KERNEL_SRC = os.path.join(ROOT, "paper_2112_03804_gb300", "csrc", "kernels.cu")
+CSRC = os.path.join(ROOT, "paper_2112_03804_gb300", "csrc")
+KERNEL = "tmem_scan_kernel"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -63,7 +64,13 @@ def _peaks():
 
 
 def _kernel_hash():
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    """Hash of every device source of the library (changes whenever a kernel does)."""
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith((".cu", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def _traffic(kernel_hash):
@@ -310,7 +317,7 @@ def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec):
                    "parallelism": f"dp{world}" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": "pair_scan_kernel", "alg_bytes_per_launch": alg_bytes,
+                     "kernel": KERNEL, "alg_bytes_per_launch": alg_bytes,
                      "launch_ms": {"A": statistics.mean(la), "AT": statistics.mean(lt)}},
         "clocks": clk_sum,
         "e2e": e2e,
