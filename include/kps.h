@@ -173,6 +173,32 @@ kps_status kps_matvec_A_host(kps_game *game, const void *y, void *out, int32_t b
 kps_status kps_matvec_AT_host(kps_game *game, const void *x, void *out, int32_t batch,
                               kps_dtype dt, void *stream);
 
+/* A * y for BF16 or FP16 vectors without any device allocation.  The paper
+ * has no counterpart: this is a service for callers that must not allocate
+ * device memory while they run, such as serving loops that reserve all of
+ * the GPU's memory up front for their own pool, real-time loops that cannot
+ * afford cudaMalloc's implicit device synchronisation, or code that shares
+ * a memory budget with other tenants and must not grow it.  kps_matvec_A
+ * with BF16/FP16 storage allocates an FP32 partial-result buffer (and a tile
+ * list) on first use; this variant uses instead a statically reserved device
+ * array of KPS_STATIC_SCRATCH_FLOATS floats plus 64 KiB, which every device
+ * that loads the library holds until the process exits.
+ *   - Requires the game's tables on the current device (kps_game_upload or
+ *     any earlier product call); KPS_EINVAL otherwise.
+ *   - batch * n1 * hs must not exceed KPS_STATIC_SCRATCH_FLOATS; larger
+ *     requests fail with KPS_EINVAL and a message giving both numbers.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (other
+ *     streams, other threads) race and produce wrong results.  Every element
+ *     the kernel reads is written by the same call first, so nothing needs to
+ *     be cleared between calls.
+ * Layouts, dtypes and results as kps_matvec_A (dt must be KPS_BF16 or
+ * KPS_F16).  Calls no cudaMalloc, cudaFree or allocating library routine. */
+#define KPS_STATIC_SCRATCH_FLOATS 4194304
+kps_status kps_matvec_A_static_scratch(kps_game *game, const void *y, void *out, int32_t batch,
+                                       kps_dtype dt, void *stream);
+
 /* Thread-local description of the last failure ("" if none). */
 const char *kps_last_error(void);
 

@@ -555,6 +555,77 @@ kps_status kps_matvec_AT_host(kps_game *g, const void *x, void *out, int32_t bat
     return matvec_host(g, 1, x, out, batch, dt, stream);
 }
 
+// A*y for BF16/FP16 storage whose FP32 partial results (and tile list) live
+// in the library's statically reserved device array instead of memory
+// obtained from cudaMalloc.  Same kernel and results as kps_matvec_A with the
+// scalar-staging path; see include/kps.h for the contract.
+kps_status kps_matvec_A_static_scratch(kps_game *g, const void *y, void *out, int32_t batch, kps_dtype dt,
+                                       void *stream_ptr) {
+    if (!g) return fail(KPS_EINVAL, "game is NULL");
+    if (dt != KPS_BF16 && dt != KPS_F16) return fail(KPS_EINVAL, "dtype must be KPS_BF16 or KPS_F16");
+    if (batch < 0) return fail(KPS_EINVAL, "batch must be >= 0");
+    if (batch == 0) return KPS_OK;
+    if (!y || !out) return fail(KPS_EINVAL, "vector pointer is NULL");
+    if (!g->uploaded) return fail(KPS_EINVAL, "the game's tables are not on the device: call kps_game_upload first");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != g->device) return fail(KPS_EINVAL, "game tables live on another device");
+    const kps::HostGame &h = g->host;
+    const int n_out = h.n[0], n_in = h.n[1];
+    const size_t floats = (size_t)batch * n_out * h.hs;
+    if (floats > kps::kStaticScratchFloats)
+        return fail(KPS_EINVAL, "batch * n1 * hs = " + std::to_string(floats) +
+                                    " exceeds the static scratch of " + std::to_string(kps::kStaticScratchFloats) +
+                                    " floats");
+    const size_t in_bytes = (size_t)batch * n_in * h.hs * 2, out_bytes = floats * 2;
+    const char *ci = static_cast<const char *>(y), *co = static_cast<const char *>(out);
+    if (ci < co + out_bytes && co < ci + in_bytes) return fail(KPS_EINVAL, "input and output overlap");
+    const int storage = dt == KPS_BF16 ? kps::kStoreBF16 : kps::kStoreF16;
+    const int nc = h.ncards + 1;
+    if (h.max_tie > kps::kTile) return fail(KPS_ENOTSUP, "tie groups longer than a tile");
+    const int nw = fast_warps(storage, nc, h.H, false);
+    if (kps::fast_smem_bytes(storage, nc, nw) > (size_t)kps::max_dyn_smem())
+        return fail(KPS_ENOTSUP, "card count too large for shared memory");
+    std::vector<int> tchunk;
+    std::vector<std::pair<int, int>> tl = kps::tie_tiles(h, nw, kps::kTile, tchunk);
+    if (tl.size() * sizeof(int2) > kps::kStaticTileBytes) return fail(KPS_ENOTSUP, "tile list too long");
+    void *base = nullptr;
+    cudaError_t e = kps::static_scratch_address(&base);
+    if (e != cudaSuccess) return cuda_fail(e, "looking up the static scratch");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    std::vector<int2> tiles(tl.size());
+    for (size_t i = 0; i < tl.size(); ++i) tiles[i] = make_int2(tl[i].first, tl[i].second);
+    if (!tiles.empty()) {
+        // pageable source: the copy is staged before this call returns
+        e = cudaMemcpyAsync(base, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copying the tile list");
+    }
+    const DeviceTables &t = g->dev;
+    kps::FastParams p{};
+    p.vin = y;
+    p.vout = out;
+    p.scratch = static_cast<unsigned char *>(base) + kps::kStaticTileBytes;
+    p.H = h.H;
+    p.hs = h.hs;
+    p.nc = nc;
+    p.n_out = n_out;
+    p.n_in = n_in;
+    p.batch = batch;
+    p.fcol = t.fcol[0];
+    p.scol = t.scol[0];
+    p.fcoef = t.fcoef_f[0];
+    p.scoef = t.scoef_f[0];
+    p.hinfo = t.hinfo;
+    p.lam_in = t.lam2_f;
+    p.lam_out = t.lam1_f;
+    p.tiles = static_cast<const int2 *>(base);
+    p.nw = nw;
+    for (int i = 0; i <= nw; ++i) p.tchunk[i] = tchunk[i];
+    e = kps::launch_fast_scan(p, storage, h.k, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the payoff scan");
+    return KPS_OK;
+}
+
 const char *kps_last_error(void) { return g_last_error.c_str(); }
 
 const char *kps_version(void) { return "kps 0.1.0 (sm_103a)"; }

@@ -89,3 +89,15 @@ size_t tmem_smem_bytes(int nc, int nw);
 cudaError_t launch_tmem_scan(const FastParams &p, int storage, int cards_per_hand, cudaStream_t stream);
 
 }  // namespace kps
+
+namespace kps {
+
+// Statically reserved device memory for kps_matvec_A_static_scratch: a tile
+// list (up to kStaticTileBytes) and kStaticScratchFloats FP32 partial results.
+constexpr size_t kStaticTileBytes = 64 * 1024;
+constexpr size_t kStaticScratchFloats = 4u * 1024u * 1024u;   // 16 MiB
+constexpr int kMaxDevices = 64;
+// Device address of the reserved array on the current device.
+cudaError_t static_scratch_address(void **ptr);
+
+}  // namespace kps

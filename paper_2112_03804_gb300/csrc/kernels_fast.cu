@@ -25,6 +25,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <mutex>
 #include <type_traits>
 
 namespace kps {
@@ -387,6 +388,32 @@ cudaError_t launch_fast_scan(const FastParams &p, int storage, int k, cudaStream
         case kStoreF16: return k == 1 ? launch_t<__half, 1>(p, smem, stream) : launch_t<__half, 2>(p, smem, stream);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// ---- statically reserved scratch (see kps_matvec_A_static_scratch) --------
+// One file-scope array per device that loads the library: the tile list of
+// a launch followed by its FP32 partial results.  Every launch overwrites the
+// parts it reads, so nothing has to start at zero.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticTileBytes + (size_t)kStaticScratchFloats * 4];
+
+cudaError_t static_scratch_address(void **ptr) {
+    // The array's name is a host-side stand-in; the device address is looked
+    // up once per device, with that device current.
+    static std::mutex mu;
+    static void *addr[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = p;
+    }
+    *ptr = addr[dev];
+    return cudaSuccess;
 }
 
 }  // namespace kps

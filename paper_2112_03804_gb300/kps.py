@@ -57,6 +57,7 @@ class Info(C.Structure):
 EXPORTED = ["kps_sparsify", "kps_game_destroy", "kps_game_info", "kps_game_hands",
             "kps_game_sequences", "kps_game_terminals", "kps_game_upload",
             "kps_matvec_A", "kps_matvec_AT", "kps_matvec_A_host", "kps_matvec_AT_host",
+            "kps_matvec_A_static_scratch",
             "kps_last_error", "kps_version"]
 
 _lib = None
@@ -77,7 +78,8 @@ def lib():
         L.kps_game_sequences.argtypes = [P, C.c_int32, P, P, P, P, P]
         L.kps_game_terminals.argtypes = [P, P, P, P, P, P, P]
         L.kps_game_upload.argtypes = [P, P]
-        for f in (L.kps_matvec_A, L.kps_matvec_AT, L.kps_matvec_A_host, L.kps_matvec_AT_host):
+        for f in (L.kps_matvec_A, L.kps_matvec_AT, L.kps_matvec_A_host, L.kps_matvec_AT_host,
+                  L.kps_matvec_A_static_scratch):
             f.argtypes = [P, P, P, C.c_int32, C.c_int, P]
         for name in EXPORTED:
             if name not in ("kps_last_error", "kps_version"):
@@ -238,6 +240,16 @@ def matvec_A_host(game: Game, y, out, batch: int, dtype: int, stream=None):
 
 def matvec_AT_host(game: Game, x, out, batch: int, dtype: int, stream=None):
     _check(lib().kps_matvec_AT_host(game._h, _ptr(x), _ptr(out), int(batch), dtype, _stream(stream)))
+
+
+STATIC_SCRATCH_FLOATS = 4194304
+
+
+def matvec_A_static_scratch(game: Game, y, out, batch: int, dtype=None, stream=None):
+    """kps_matvec_A_static_scratch: BF16/FP16 A*y with no device allocation
+    (statically reserved scratch; see include/kps.h for the contract)."""
+    _check(lib().kps_matvec_A_static_scratch(game._h, _ptr(y), _ptr(out), int(batch), _dtype_code(y, dtype),
+                                             _stream(stream)))
 
 
 def version() -> str:
