@@ -895,8 +895,9 @@ static double bottom_up(const orc_game *g, int p, const double *gv, const double
     return total;
 }
 
-/* Regret matching: b(I,a) = R+(I,a)/sum_a R+, uniform when the sum is 0. */
-static void regret_match(const orc_game *g, int p, const double *regret, double *beh)
+/* Regret matching: b(I,a) = R+(I,a)/sum_a R+, uniform when the sum is at
+ * most theta (the noise floor of orc_rmplus; 0 gives textbook RM+). */
+static void regret_match(const orc_game *g, int p, const double *regret, double *beh, double theta)
 {
     int H = g->H;
     for (int i = 0; i < g->np[p]; i++) {
@@ -906,9 +907,33 @@ static void regret_match(const orc_game *g, int p, const double *regret, double 
             double s = 0.0;
             for (int a = 0; a < na; a++) s += regret[(size_t)(s0 + a) * H + h];
             for (int a = 0; a < na; a++)
-                beh[(size_t)(s0 + a) * H + h] = s > 0.0 ? regret[(size_t)(s0 + a) * H + h] / s : 1.0 / na;
+                beh[(size_t)(s0 + a) * H + h] = s > theta ? regret[(size_t)(s0 + a) * H + h] / s : 1.0 / na;
         }
     }
+}
+
+/* Bound on |counterfactual value| of player p: max |payoff| times the
+ * largest chance weight mass a hand of p can see,
+ *   V_p = max_t max(c1, c2) * max_h mu_p(h) * sum_h mu_q(h) / beta.
+ * A player's regret sum at or below eps * V_p is treated as zero: values
+ * that are exactly zero (an opponent whose every compatible hand has zero
+ * reach) come out of a product that subtracts card-overlap masses as
+ * rounding noise instead, and regret matching would otherwise follow that
+ * noise.  eps = 2^-40 keeps the floor far above FP64 noise and far below
+ * any regret that moves a strategy. */
+double orc_regret_floor(const orc_game *g, int p, double eps)
+{
+    double cmax = 0.0, mmax = 0.0, msum = 0.0;
+    for (int t = 0; t < g->T; t++) {
+        const onode *z = &g->nodes[g->term_node[t]];
+        if (z->c[0] > cmax) cmax = z->c[0];
+        if (z->c[1] > cmax) cmax = z->c[1];
+    }
+    for (int h = 0; h < g->H; h++) {
+        if (g->mu[p][h] > mmax) mmax = g->mu[p][h];
+        msum += g->mu[1 - p][h];
+    }
+    return eps * cmax * mmax * msum / g->beta;
 }
 
 static void uniform_beh(const orc_game *g, int p, double *beh)
@@ -954,20 +979,21 @@ double orc_rmplus(const orc_game *g, int iters, const double *beh1_0, const doub
     if (beh2_0) memcpy(b2, beh2_0, N2 * sizeof(double)); else uniform_beh(g, 1, b2);
     orc_seqform(g, 0, b1, x);
     orc_seqform(g, 1, b2, y);
+    const double th1 = orc_regret_floor(g, 0, ORC_REGRET_EPS), th2 = orc_regret_floor(g, 1, ORC_REGRET_EPS);
     double wsum = 0.0, expl = 0.0;
     for (int t = 1; t <= iters; t++) {
         /* player 1: accumulate the strategy played, then update against y */
         for (size_t i = 0; i < N1; i++) xs[i] += t * x[i];
         matvec_one(g, y, g1);
         bottom_up(g, 0, g1, b1, R1, 0);
-        regret_match(g, 0, R1, b1);
+        regret_match(g, 0, R1, b1, th1);
         orc_seqform(g, 0, b1, x);
         /* player 2 (alternating): against the updated x, gradient -A^T x */
         for (size_t i = 0; i < N2; i++) ys[i] += t * y[i];
         matvec_t_one(g, x, g2);
         for (size_t i = 0; i < N2; i++) g2[i] = -g2[i];
         bottom_up(g, 1, g2, b2, R2, 0);
-        regret_match(g, 1, R2, b2);
+        regret_match(g, 1, R2, b2, th2);
         orc_seqform(g, 1, b2, y);
         wsum += t;
         if (trace) {

@@ -116,7 +116,14 @@ double orc_technique_b(const orc_game *g, long long *cnt);
 /* Counts only (no dense matrices); valid for any size. Same cnt layout. */
 void orc_technique_b_counts(const orc_game *g, long long *cnt);
 
+/* Noise floor of regret matching for player p: eps * V_p, V_p a bound on
+ * the magnitude of p's counterfactual values (see kps_oracle.c). */
+#define ORC_REGRET_EPS (1.0 / 1099511627776.0)   /* 2^-40 */
+double orc_regret_floor(const orc_game *g, int p, double eps);
+
 /* RM+ (CFR+-style) alternating self-play with linearly weighted averages.
+ * Regret matching plays uniformly at a node whose regret sum is at most
+ * orc_regret_floor(g, p, ORC_REGRET_EPS) (exact zero in textbook RM+).
  * x0, y0: initial behavioural strategies [n][H] (NULL = uniform).
  * Runs iters iterations; writes average behavioural strategies (optional,
  * may be NULL) and returns the exploitability of the average in units of

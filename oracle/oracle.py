@@ -61,6 +61,8 @@ def lib():
         L.orc_free.argtypes = [P]
         L.orc_info.argtypes = [P, P]
         L.orc_beta.restype = C.c_double
+        L.orc_regret_floor.argtypes = [P, C.c_int, C.c_double]
+        L.orc_regret_floor.restype = C.c_double
         L.orc_beta.argtypes = [P]
         L.orc_pot0.restype = C.c_double
         L.orc_pot0.argtypes = [P]
@@ -213,6 +215,10 @@ class OracleGame:
         cnt = np.zeros(9, dtype=np.int64)
         lib().orc_technique_b_counts(self._g, _p(cnt))
         return cnt
+
+    def regret_floor(self, p: int, eps: float) -> float:
+        """eps * V_p, V_p the bound on player p's counterfactual values."""
+        return lib().orc_regret_floor(self._g, p, eps)
 
     def rmplus(self, iters: int, beh1=None, beh2=None, trace_every: int = 0):
         avg1 = np.zeros((self.n1, self.H))

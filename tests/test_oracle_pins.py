@@ -233,3 +233,13 @@ def test_synth_simplex_vectors():
     assert v.shape == (4, 6, 5)
     assert np.allclose(v[:, 0:2].sum(1), 1) and np.allclose(v[:, 2:5].sum(1), 1)
     assert np.allclose(v[:, 5], 1)
+
+
+def test_regret_floor_kuhn_by_hand():
+    """Kuhn poker: the largest contribution at a terminal is 2 (ante plus
+    bet), beliefs are 1, each player has 3 hands and 6 compatible deals, so
+    V = 2 * 1 * 3 / 6 = 1 for both players."""
+    og = OracleGame(synth.kuhn_spec())
+    assert og.regret_floor(0, 1.0) == pytest.approx(1.0, rel=1e-15)
+    assert og.regret_floor(1, 1.0) == pytest.approx(1.0, rel=1e-15)
+    assert og.regret_floor(0, 2.0 ** -40) == pytest.approx(2.0 ** -40, rel=1e-15)
