@@ -173,6 +173,93 @@ kps_status kps_matvec_A_host(kps_game *game, const void *y, void *out, int32_t b
 kps_status kps_matvec_AT_host(kps_game *game, const void *x, void *out, int32_t batch,
                               kps_dtype dt, void *stream);
 
+/* ---- Batches of games in one launch -------------------------------------
+ * A batch holds several games (uneven hand counts and betting trees) whose
+ * products run as ONE persistent kernel launch: CTAs take (game, 32-column
+ * tile) tickets from an atomic counter (or a static stride) until every
+ * tile of every game is done.  Not in the paper, whose products are per
+ * game (Prop. 1); the per-game arithmetic is that of kps_matvec_A/AT.
+ * Layout: one vector per game and player, concatenated in game order; game
+ * g's player-p vector ([n_p(g)][hs(g)], same conventions as above) starts
+ * at element off_p[g] (kps_batch_offsets).  Batch vectors must be 16-byte
+ * aligned.  The games must outlive the batch, share cards_per_hand and have
+ * no tie group longer than 32 hands.  Calls on one batch must not overlap
+ * on the GPU (they share a ticket counter); they are asynchronous on
+ * `stream`, and capturable in a CUDA graph once the batch has run (or been
+ * tuned) for that dtype. */
+typedef struct kps_batch kps_batch;
+
+typedef struct {
+    int32_t warps;        /* warps per CTA                                  */
+    int32_t grid;         /* CTAs of the persistent launch                  */
+    int32_t schedule;     /* 0 atomic ticket counter, 1 static stride       */
+    double ms_per_pair;   /* tuned time of one A and one A^T launch, or 0   */
+} kps_batch_shape;
+
+/* Uploads every game.  Errors: KPS_EINVAL (NULL, mixed cards_per_hand),
+ * KPS_ENOTSUP (tie group > 32 hands), KPS_ENOMEM. */
+kps_status kps_batch_create(kps_game *const *games, int32_t n, kps_batch **out);
+kps_status kps_batch_destroy(kps_batch *batch);
+/* off[0..n]: element offsets of each game's player-`player` vector; off[n]
+ * is the length of the batch vector.  Host only. */
+kps_status kps_batch_offsets(const kps_batch *batch, int32_t player, int64_t *off);
+/* out = A y per game (y: player-2 layout, out: player-1 layout) / A^T x. */
+kps_status kps_batch_matvec_A(kps_batch *batch, const void *y, void *out, kps_dtype dt, void *stream);
+kps_status kps_batch_matvec_AT(kps_batch *batch, const void *x, void *out, kps_dtype dt, void *stream);
+/* Autotuner: times every admissible launch shape (warps per CTA, CTAs per
+ * SM, schedule) of an A and an A^T launch with CUDA events on `stream`,
+ * keeps the fastest for `dt` and reports it in *chosen (may be NULL).
+ * Allocates temporary buffers; synchronises `stream`. */
+kps_status kps_batch_tune(kps_batch *batch, kps_dtype dt, void *stream, kps_batch_shape *chosen);
+/* The launch shape in use for `dt` (the default one if never tuned). */
+kps_status kps_batch_shape_get(kps_batch *batch, kps_dtype dt, kps_batch_shape *shape);
+/* Sets the launch shape for `dt` (ms_per_pair ignored).  Errors: KPS_EINVAL
+ * (out of range), KPS_ENOTSUP (warp count the games do not fit). */
+kps_status kps_batch_shape_set(kps_batch *batch, kps_dtype dt, const kps_batch_shape *shape);
+
+/* ---- First-order solver ---------------------------------------------------
+ * Regret matching plus with alternating updates and linearly weighted
+ * averages on every game of a batch, the gradients A y and -A^T x coming
+ * from the batched products (Sec. 2, "First-order methods", whose gradient
+ * is the per-iteration cost that the sparsification of Prop. 1 makes cheap;
+ * Sec. 5 runs such a solver).  One iteration t:
+ *   xsum += t x;  R1 <- max(0, R1 + q - v) bottom-up against g = A y;
+ *   x <- sequence form of R1 / sum R1 (uniform where the sum is 0);
+ *   ysum += t y;  the same for player 2 against g = -A^T x (the new x).
+ * `dt` is the storage type of strategies and values (KPS_F32, KPS_F64,
+ * KPS_BF16, KPS_F16); regrets, averages and arithmetic are FP32 (FP64 for
+ * KPS_F64); averages, best responses and exploitability are FP64.  The
+ * solver keeps a reference to the batch, which must outlive it. */
+typedef struct kps_solver kps_solver;
+
+/* Errors: KPS_ENOTSUP (a node with > 12 actions, too many sequences),
+ * KPS_ENOMEM.  Starts from uniform strategies (kps_solver_reset). */
+kps_status kps_solver_create(kps_batch *batch, kps_dtype dt, kps_solver **out);
+kps_status kps_solver_destroy(kps_solver *solver);
+/* Clears regrets, averages and the iteration count; the first iteration
+ * plays the behavioural strategies beh1 / beh2 (device FP32, batch player
+ * layouts: entry [sigma][h] = probability of sigma's last action at its
+ * node), or uniform strategies if both are NULL. */
+kps_status kps_solver_reset(kps_solver *solver, const float *beh1, const float *beh2, void *stream);
+/* Runs `iters` iterations as one CUDA graph (captured on first use of each
+ * count), asynchronous on `stream`. */
+kps_status kps_solver_step(kps_solver *solver, int32_t iters, void *stream);
+/* Iterations run since the last reset (host count). */
+kps_status kps_solver_iterations(const kps_solver *solver, int64_t *iters);
+/* FP64 average strategies (device, batch player layouts; either may be
+ * NULL): sequence form xsum / sum_t t, or with `behavioural` != 0 the
+ * behavioural strategy x[sigma] / x[parent] (uniform at unreached nodes).
+ * Before any iteration: the current strategies. */
+kps_status kps_solver_average(kps_solver *solver, int32_t behavioural, double *x, double *y, void *stream);
+/* The current (last) sequence-form strategies x, y in the storage type
+ * (device, batch player layouts; either may be NULL). */
+kps_status kps_solver_strategy(kps_solver *solver, void *x, void *y, void *stream);
+/* Per game (device arrays of n doubles): exploitability of the averages
+ * (BR1(ybar) + BR2(xbar)) / 2 / pot0, in units of the initial pot (Sec. 5),
+ * and the best-response values BR1, BR2 (may be NULL).  FP64 products and
+ * best responses.  Asynchronous on `stream`. */
+kps_status kps_solver_exploitability(kps_solver *solver, double *expl, double *br1, double *br2, void *stream);
+
 /* A * y for BF16 or FP16 vectors without any device allocation.  The paper
  * has no counterpart: this is a service for callers that must not allocate
  * device memory while they run, such as serving loops that reserve all of

@@ -11,10 +11,11 @@
 #include <vector>
 
 #include "../../include/kps.h"
+#include "abi_internal.h"
 #include "game.h"
 #include "kernels.h"
 
-namespace {
+namespace kps_abi {
 
 thread_local std::string g_last_error;
 
@@ -27,43 +28,11 @@ kps_status cuda_fail(cudaError_t e, const char *what) {
     return fail(KPS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// Device copies of the per-game tables, one allocation.
-struct DeviceTables {
-    void *blob = nullptr;
-    uint32_t *hinfo = nullptr;
-    float *lam1_f = nullptr, *lam2_f = nullptr;
-    double *lam1_d = nullptr, *lam2_d = nullptr;
-    // per output row: fold / showdown terminal (input sequence, payoff)
-    int *fcol[2] = {nullptr, nullptr}, *scol[2] = {nullptr, nullptr};
-    float *fcoef_f[2] = {nullptr, nullptr}, *scoef_f[2] = {nullptr, nullptr};
-    double *fcoef_d[2] = {nullptr, nullptr}, *scoef_d[2] = {nullptr, nullptr};
-};
+}  // namespace kps_abi
 
-}  // namespace
+using namespace kps_abi;
 
-struct kps_game {
-    kps::HostGame host;
-    // per output row of each direction (0 = A, 1 = A^T): terminal pairs
-    std::vector<int> fcol[2], scol[2];
-    std::vector<double> fcoef[2], scoef[2];
-    bool uploaded = false;
-    int device = -1;
-    DeviceTables dev;
-    void *stage_in = nullptr, *stage_out = nullptr;
-    size_t stage_in_bytes = 0, stage_out_bytes = 0;
-    // tie-aligned tile lists on the device, per warp count
-    struct Tiles {
-        int2 *dev = nullptr;
-        std::vector<int2> host;
-        std::vector<int> tchunk;
-    };
-    std::map<int, Tiles> tiles;
-    // FP32 partial results for half-precision outputs
-    void *scratch = nullptr;
-    size_t scratch_bytes = 0;
-};
-
-namespace {
+namespace kps_abi {
 
 size_t dtype_size(kps_dtype dt) {
     switch (dt) {
@@ -179,6 +148,40 @@ kps_status upload(kps_game *g, cudaStream_t stream) {
     return KPS_OK;
 }
 
+kps_status tiles_for(kps_game *g, int nw, cudaStream_t stream, const kps_game::Tiles **out) {
+    auto it = g->tiles.find(nw);
+    if (it == g->tiles.end()) {
+        kps_game::Tiles t;
+        std::vector<std::pair<int, int>> tl = kps::tie_tiles(g->host, nw, kps::kTile, t.tchunk);
+        std::vector<int2> host(tl.size());
+        for (size_t i = 0; i < tl.size(); ++i) host[i] = make_int2(tl[i].first, tl[i].second);
+        t.host = host;
+        cudaError_t e = cudaMalloc(&t.dev, std::max<size_t>(1, host.size()) * sizeof(int2));
+        if (e != cudaSuccess) return fail(KPS_ENOMEM, "tile table");
+        if (!host.empty()) {
+            e = cudaMemcpyAsync(t.dev, host.data(), host.size() * sizeof(int2), cudaMemcpyHostToDevice, stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) {
+                cudaFree(t.dev);
+                return cuda_fail(e, "uploading the tile table");
+            }
+        }
+        it = g->tiles.emplace(nw, std::move(t)).first;
+    }
+    *out = &it->second;
+    return KPS_OK;
+}
+
+bool tmem_chunks_fit(const kps_game::Tiles &t, int nw) {
+    const auto &tc = t.tchunk;
+    for (int k = 0; k < nw; ++k) {
+        if (tc[k] == tc[k + 1]) continue;
+        const int2 a = t.host[tc[k]], b = t.host[tc[k + 1] - 1];
+        if (b.x + b.y - a.x > kps::kTmemChunk) return false;
+    }
+    return true;
+}
+
 // Warps per CTA of the fast path: two CTAs of 4 warps per SM when they fit
 // (smaller CTAs shorten the tail of the last wave), else the largest count
 // that fits.  KPS_WARPS overrides the choice (1..8).
@@ -232,36 +235,10 @@ kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int stor
                         : vec ? kps::vec_smem_bytes(storage, sp.nc, nw) : kps::fast_smem_bytes(storage, sp.nc, nw);
     if (need > (size_t)kps::max_dyn_smem())
         return fail(KPS_ENOTSUP, "card count too large for shared memory");
-    auto it = g->tiles.find(nw);
-    if (it == g->tiles.end()) {
-        kps_game::Tiles t;
-        std::vector<std::pair<int, int>> tl = kps::tie_tiles(h, nw, kps::kTile, t.tchunk);
-        std::vector<int2> host(tl.size());
-        for (size_t i = 0; i < tl.size(); ++i) host[i] = make_int2(tl[i].first, tl[i].second);
-        t.host = host;
-        cudaError_t e = cudaMalloc(&t.dev, std::max<size_t>(1, host.size()) * sizeof(int2));
-        if (e != cudaSuccess) return fail(KPS_ENOMEM, "tile table");
-        if (!host.empty()) {
-            e = cudaMemcpyAsync(t.dev, host.data(), host.size() * sizeof(int2), cudaMemcpyHostToDevice, stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-            if (e != cudaSuccess) {
-                cudaFree(t.dev);
-                return cuda_fail(e, "uploading the tile table");
-            }
-        }
-        it = g->tiles.emplace(nw, std::move(t)).first;
-    }
-    if (path == kTmem) {
-        // every chunk must fit a warp's tensor-memory region
-        const auto &tc = it->second.tchunk;
-        bool fits = true;
-        for (int k = 0; k < nw && fits; ++k) {
-            if (tc[k] == tc[k + 1]) continue;
-            const int2 a = it->second.host[tc[k]], b = it->second.host[tc[k + 1] - 1];
-            fits = b.x + b.y - a.x <= kps::kTmemChunk;
-        }
-        if (!fits) return fail(KPS_ENOTSUP, "hand chunk too long for tensor memory");
-    }
+    const kps_game::Tiles *tiles = nullptr;
+    kps_status st = tiles_for(g, nw, stream, &tiles);
+    if (st != KPS_OK) return st;
+    if (path == kTmem && !tmem_chunks_fit(*tiles, nw)) return fail(KPS_ENOTSUP, "hand chunk too long for tensor memory");
     void *scratch = sp.vout;
     if (path != kTmem && (storage == kps::kStoreBF16 || storage == kps::kStoreF16)) {
         const size_t need = (size_t)sp.batch * sp.n_out * h.hs * sizeof(float);
@@ -292,9 +269,9 @@ kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int stor
     p.hinfo = sp.hinfo;
     p.lam_in = sp.lam_in;
     p.lam_out = sp.lam_out;
-    p.tiles = it->second.dev;
+    p.tiles = tiles->dev;
     p.nw = nw;
-    for (int i = 0; i <= nw; ++i) p.tchunk[i] = it->second.tchunk[i];
+    for (int i = 0; i <= nw; ++i) p.tchunk[i] = tiles->tchunk[i];
     (void)dir;
     (void)dt;
     cudaError_t e;
@@ -413,7 +390,7 @@ kps_status matvec_host(kps_game *g, int dir, const void *vin, void *vout, int32_
     return KPS_OK;
 }
 
-}  // namespace
+}  // namespace kps_abi
 
 extern "C" {
 

@@ -1,0 +1,72 @@
+// Internal state shared by the C ABI's translation units (abi.cu, batch.cu,
+// solver.cu): the game object, its device tables and the error helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/kps.h"
+#include "game.h"
+
+namespace kps_abi {
+
+// Records `msg` as the calling thread's last error and returns `s`.
+kps_status fail(kps_status s, const std::string &msg);
+kps_status cuda_fail(cudaError_t e, const char *what);
+
+// Device copies of the per-game tables, one allocation.
+struct DeviceTables {
+    void *blob = nullptr;
+    uint32_t *hinfo = nullptr;
+    float *lam1_f = nullptr, *lam2_f = nullptr;
+    double *lam1_d = nullptr, *lam2_d = nullptr;
+    // per output row: fold / showdown terminal (input sequence, payoff)
+    int *fcol[2] = {nullptr, nullptr}, *scol[2] = {nullptr, nullptr};
+    float *fcoef_f[2] = {nullptr, nullptr}, *scoef_f[2] = {nullptr, nullptr};
+    double *fcoef_d[2] = {nullptr, nullptr}, *scoef_d[2] = {nullptr, nullptr};
+};
+
+size_t dtype_size(kps_dtype dt);
+
+}  // namespace kps_abi
+
+struct kps_game {
+    kps::HostGame host;
+    // per output row of each direction (0 = A, 1 = A^T): terminal pairs
+    std::vector<int> fcol[2], scol[2];
+    std::vector<double> fcoef[2], scoef[2];
+    bool uploaded = false;
+    int device = -1;
+    kps_abi::DeviceTables dev;
+    void *stage_in = nullptr, *stage_out = nullptr;
+    size_t stage_in_bytes = 0, stage_out_bytes = 0;
+    // tie-aligned tile lists on the device, per warp count
+    struct Tiles {
+        int2 *dev = nullptr;
+        std::vector<int2> host;
+        std::vector<int> tchunk;
+    };
+    std::map<int, Tiles> tiles;
+    // FP32 partial results for half-precision outputs
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+namespace kps_abi {
+
+// Uploads the game's tables to the current device on first use.
+kps_status upload(kps_game *g, cudaStream_t stream);
+
+// The tie-aligned tile list of the game for `nw` warps (created and
+// uploaded on first use; synchronises `stream` then).
+kps_status tiles_for(kps_game *g, int nw, cudaStream_t stream, const kps_game::Tiles **out);
+
+// Does every warp's chunk of the `nw`-warp tile list span at most
+// kps::kTmemChunk hands?
+bool tmem_chunks_fit(const kps_game::Tiles &t, int nw);
+
+}  // namespace kps_abi

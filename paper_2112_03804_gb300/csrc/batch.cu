@@ -1,0 +1,397 @@
+// Batches of games in one persistent launch (C ABI in include/kps.h).
+//
+// A batch concatenates one player-1 and one player-2 vector per game: game
+// g's vector of player p starts off[p][g] elements into the batch vector
+// and has n_p(g) rows of hs(g) entries.  One launch of the multi-game kernel
+// covers every (game, 32-column tile) of a direction; the CTAs are
+// persistent and take tiles from an atomic ticket counter (or a static
+// stride), so uneven hand counts and tree sizes share the machine without a
+// launch per game.  The launch shape (warps per CTA, CTAs, schedule) comes
+// from the batch's own autotuner (kps_batch_tune), which times every
+// candidate with CUDA events on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "abi_internal.h"
+#include "batch_internal.h"
+#include "kernels.h"
+
+using namespace kps_abi;
+
+namespace kps_abi {
+
+namespace {
+
+
+int storage_of(kps_dtype dt) {
+    return dt == KPS_F32 ? kps::kStoreF32 : dt == KPS_F64 ? kps::kStoreF64 : dt == KPS_BF16 ? kps::kStoreBF16
+                                                                                             : kps::kStoreF16;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+// Smallest warp count whose tile lists give every game's chunks at most
+// kTmemChunk hands (tensor-memory path); 0 if none does.  Host only.
+int tmem_min_warps(kps_batch *b) {
+    for (int nw = 1; nw <= kps::kMaxWarps; ++nw) {
+        bool ok = true;
+        for (kps_game *g : b->games) {
+            if ((long long)nw * kps::kTmemChunk < g->host.H) { ok = false; break; }
+            std::vector<int> tchunk;
+            const std::vector<std::pair<int, int>> tl = kps::tie_tiles(g->host, nw, kps::kTile, tchunk);
+            for (int k = 0; k < nw && ok; ++k) {
+                if (tchunk[k] == tchunk[k + 1]) continue;
+                const auto &a = tl[tchunk[k]], &z = tl[tchunk[k + 1] - 1];
+                ok = z.first + z.second - a.first <= kps::kTmemChunk;
+            }
+            if (!ok) break;
+        }
+        if (ok) return nw;
+    }
+    return 0;
+}
+
+}  // namespace
+
+// Launch table of one (direction, FP64 or not, warp count).
+kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t stream, const BatchTable **out) {
+    const auto key = std::make_tuple(dir, f64, nw);
+    auto it = b->tables.find(key);
+    if (it != b->tables.end()) {
+        *out = &it->second;
+        return KPS_OK;
+    }
+    const int ng = (int)b->games.size();
+    std::vector<kps::FastParams> fp(ng);
+    std::vector<long long> tstart(ng + 1, 0), in_off(ng), out_off(ng);
+    std::vector<int> tgame;
+    int nc = 0;
+    for (int i = 0; i < ng; ++i) {
+        kps_game *g = b->games[i];
+        const kps::HostGame &h = g->host;
+        const kps_game::Tiles *t = nullptr;
+        kps_status st = tiles_for(g, nw, stream, &t);
+        if (st != KPS_OK) return st;
+        const DeviceTables &d = g->dev;
+        kps::FastParams &p = fp[i];
+        std::memset(&p, 0, sizeof(p));
+        p.H = h.H;
+        p.hs = h.hs;
+        p.nc = h.ncards + 1;
+        p.n_out = dir == 0 ? h.n[0] : h.n[1];
+        p.n_in = dir == 0 ? h.n[1] : h.n[0];
+        p.batch = 1;
+        p.fcol = d.fcol[dir];
+        p.scol = d.scol[dir];
+        p.fcoef = f64 ? (const void *)d.fcoef_d[dir] : (const void *)d.fcoef_f[dir];
+        p.scoef = f64 ? (const void *)d.scoef_d[dir] : (const void *)d.scoef_f[dir];
+        p.hinfo = d.hinfo;
+        const void *l1 = f64 ? (const void *)d.lam1_d : (const void *)d.lam1_f;
+        const void *l2 = f64 ? (const void *)d.lam2_d : (const void *)d.lam2_f;
+        p.lam_in = dir == 0 ? l2 : l1;
+        p.lam_out = dir == 0 ? l1 : l2;
+        p.tiles = t->dev;
+        p.nw = nw;
+        for (int k = 0; k <= nw; ++k) p.tchunk[k] = t->tchunk[k];
+        nc = std::max(nc, p.nc);
+        const int nt = (p.n_out + 31) / 32;
+        tstart[i + 1] = tstart[i] + nt;
+        for (int k = 0; k < nt; ++k) tgame.push_back(i);
+        in_off[i] = b->off[dir == 0 ? 1 : 0][i];
+        out_off[i] = b->off[dir == 0 ? 0 : 1][i];
+    }
+    if (tstart[ng] > 0x7fffffffLL) return fail(KPS_ENOTSUP, "too many column tiles in one batch");
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t o_fp = 0, o_ts = al(o_fp + sizeof(kps::FastParams) * ng), o_tg = al(o_ts + 8 * (size_t)(ng + 1)),
+                 o_in = al(o_tg + 4 * std::max<size_t>(1, tgame.size())), o_out = al(o_in + 8 * (size_t)ng),
+                 total = al(o_out + 8 * (size_t)ng);
+    std::vector<unsigned char> host(total, 0);
+    std::memcpy(host.data() + o_fp, fp.data(), sizeof(kps::FastParams) * ng);
+    std::memcpy(host.data() + o_ts, tstart.data(), 8 * (size_t)(ng + 1));
+    if (!tgame.empty()) std::memcpy(host.data() + o_tg, tgame.data(), 4 * tgame.size());
+    std::memcpy(host.data() + o_in, in_off.data(), 8 * (size_t)ng);
+    std::memcpy(host.data() + o_out, out_off.data(), 8 * (size_t)ng);
+    BatchTable tb;
+    cudaError_t e = cudaMalloc(&tb.blob, total);
+    if (e != cudaSuccess) return fail(KPS_ENOMEM, "batch launch table");
+    e = cudaMemcpyAsync(tb.blob, host.data(), total, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        cudaFree(tb.blob);
+        return cuda_fail(e, "uploading the batch launch table");
+    }
+    unsigned char *bl = static_cast<unsigned char *>(tb.blob);
+    tb.m.games = reinterpret_cast<const kps::FastParams *>(bl + o_fp);
+    tb.m.tile_start = reinterpret_cast<const long long *>(bl + o_ts);
+    tb.m.tile_game = reinterpret_cast<const int *>(bl + o_tg);
+    tb.m.in_off = reinterpret_cast<const long long *>(bl + o_in);
+    tb.m.out_off = reinterpret_cast<const long long *>(bl + o_out);
+    tb.m.ticket = b->ticket;
+    tb.m.ngames = ng;
+    tb.m.total_tiles = (int)tstart[ng];
+    tb.m.nw = nw;
+    tb.m.nc = nc;
+    tb.m.schedule = 0;
+    *out = &b->tables.emplace(key, tb).first->second;
+    return KPS_OK;
+}
+
+// The launch shape used for `dt` when the batch has not been tuned.
+kps_status batch_default_shape(kps_batch *b, kps_dtype dt, cudaStream_t stream, BatchShape *out) {
+    auto it = b->shape.find((int)dt);
+    if (it != b->shape.end()) {
+        *out = it->second;
+        return KPS_OK;
+    }
+    BatchShape s;
+    const int storage = storage_of(dt);
+    int maxH = 0, maxnc = 0;
+    for (kps_game *g : b->games) {
+        maxH = std::max(maxH, g->host.H);
+        maxnc = std::max(maxnc, g->host.ncards + 1);
+    }
+    if (dt == KPS_F64) {
+        if (maxnc > 64) return fail(KPS_ENOTSUP, "card count too large for the FP64 batch kernel");
+        s.nw = 8;
+        while (s.nw > 1 && kps::vec_smem_bytes(storage, maxnc, s.nw) > (size_t)kps::max_dyn_smem()) --s.nw;
+        s.nw = std::max(1, std::min(s.nw, (maxH + kps::kTile - 1) / kps::kTile));
+        s.per_sm = std::max(1, kps::vec_multi_ctas_per_sm(storage, b->k, maxnc, s.nw));
+    } else {
+        if (maxnc > 66) return fail(KPS_ENOTSUP, "card count too large for the tensor-memory kernel");
+        const int lo = tmem_min_warps(b);
+        if (lo == 0) return fail(KPS_ENOTSUP, "hand chunk too long for tensor memory");
+        s.nw = std::max(lo, std::min(kps::kMaxWarps, (maxH + kps::kTile - 1) / kps::kTile));
+        s.per_sm = std::max(1, kps::tmem_multi_ctas_per_sm(storage, b->k, maxnc, s.nw));
+    }
+    s.grid = sm_count() * s.per_sm;
+    s.schedule = 0;
+    b->shape[(int)dt] = s;
+    *out = s;
+    return KPS_OK;
+}
+
+kps_status batch_matvec(kps_batch *b, int dir, const void *vin, void *vout, kps_dtype dt, cudaStream_t stream) {
+    if (!b) return fail(KPS_EINVAL, "batch is NULL");
+    if (dtype_size(dt) == 0) return fail(KPS_EINVAL, "unknown dtype");
+    if (!vin || !vout) return fail(KPS_EINVAL, "vector pointer is NULL");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != b->device) return fail(KPS_EINVAL, "batch tables live on another device");
+    const size_t es = dtype_size(dt);
+    const size_t in_bytes = (size_t)b->off[dir == 0 ? 1 : 0].back() * es;
+    const size_t out_bytes = (size_t)b->off[dir == 0 ? 0 : 1].back() * es;
+    const char *ci = static_cast<const char *>(vin), *co = static_cast<const char *>(vout);
+    if (ci < co + out_bytes && co < ci + in_bytes) return fail(KPS_EINVAL, "input and output overlap");
+    if (((reinterpret_cast<uintptr_t>(vin) | reinterpret_cast<uintptr_t>(vout)) & 15) != 0)
+        return fail(KPS_EINVAL, "batch vectors must be 16-byte aligned");
+    BatchShape s;
+    kps_status st = batch_default_shape(b, dt, stream, &s);
+    if (st != KPS_OK) return st;
+    const BatchTable *t = nullptr;
+    st = batch_table(b, dir, dt == KPS_F64, s.nw, stream, &t);
+    if (st != KPS_OK) return st;
+    kps::MultiParams m = t->m;
+    m.vin = vin;
+    m.vout = vout;
+    m.schedule = s.schedule;
+    cudaError_t e = cudaSuccess;
+    if (s.schedule == 0) e = cudaMemsetAsync(b->ticket, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the tile ticket");
+    const int storage = storage_of(dt);
+    e = dt == KPS_F64 ? kps::launch_vec_multi(m, storage, b->k, s.grid, stream)
+                      : kps::launch_tmem_multi(m, storage, b->k, s.grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the batched payoff scan");
+    return KPS_OK;
+}
+
+}  // namespace kps_abi
+
+extern "C" {
+
+kps_status kps_batch_create(kps_game *const *games, int32_t n, kps_batch **out) {
+    if (!out) return fail(KPS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!games || n <= 0) return fail(KPS_EINVAL, "a batch needs at least one game");
+    kps_batch *b = new (std::nothrow) kps_batch;
+    if (!b) return fail(KPS_ENOMEM, "batch object");
+    b->games.assign(games, games + n);
+    b->k = games[0] ? games[0]->host.k : 0;
+    for (int p = 0; p < 2; ++p) b->off[p].assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        kps_game *g = games[i];
+        if (!g) { delete b; return fail(KPS_EINVAL, "game " + std::to_string(i) + " is NULL"); }
+        if (g->host.k != b->k) { delete b; return fail(KPS_EINVAL, "games of a batch must share cards_per_hand"); }
+        if (g->host.max_tie > kps::kTile) {
+            delete b;
+            return fail(KPS_ENOTSUP, "game " + std::to_string(i) + " has a tie group longer than 32 hands");
+        }
+        kps_status st = upload(g, nullptr);
+        if (st != KPS_OK) { delete b; return st; }
+        for (int p = 0; p < 2; ++p) b->off[p][i + 1] = b->off[p][i] + (long long)g->host.n[p] * g->host.hs;
+    }
+    cudaGetDevice(&b->device);
+    cudaError_t e = cudaMalloc(&b->ticket, 256);
+    if (e != cudaSuccess) { delete b; return fail(KPS_ENOMEM, "ticket counter"); }
+    *out = b;
+    return KPS_OK;
+}
+
+kps_status kps_batch_destroy(kps_batch *b) {
+    if (!b) return KPS_OK;
+    for (auto &kv : b->tables) cudaFree(kv.second.blob);
+    if (b->ticket) cudaFree(b->ticket);
+    delete b;
+    return KPS_OK;
+}
+
+kps_status kps_batch_offsets(const kps_batch *b, int32_t player, int64_t *off) {
+    if (!b || !off || player < 0 || player > 1) return fail(KPS_EINVAL, "bad argument");
+    for (size_t i = 0; i < b->off[player].size(); ++i) off[i] = b->off[player][i];
+    return KPS_OK;
+}
+
+kps_status kps_batch_matvec_A(kps_batch *b, const void *y, void *out, kps_dtype dt, void *stream) {
+    return batch_matvec(b, 0, y, out, dt, static_cast<cudaStream_t>(stream));
+}
+
+kps_status kps_batch_matvec_AT(kps_batch *b, const void *x, void *out, kps_dtype dt, void *stream) {
+    return batch_matvec(b, 1, x, out, dt, static_cast<cudaStream_t>(stream));
+}
+
+kps_status kps_batch_tune(kps_batch *b, kps_dtype dt, void *stream_ptr, kps_batch_shape *chosen) {
+    if (!b) return fail(KPS_EINVAL, "batch is NULL");
+    if (dtype_size(dt) == 0) return fail(KPS_EINVAL, "unknown dtype");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    BatchShape base;
+    kps_status st = batch_default_shape(b, dt, stream, &base);
+    if (st != KPS_OK) return st;
+    const int storage = storage_of(dt);
+    int maxnc = 0, maxH = 0;
+    for (kps_game *g : b->games) {
+        maxnc = std::max(maxnc, g->host.ncards + 1);
+        maxH = std::max(maxH, g->host.H);
+    }
+    // candidates: every admissible warp count, both schedules, one or all
+    // resident CTAs per SM
+    int lo = 1;
+    if (dt != KPS_F64) lo = tmem_min_warps(b);
+    const int hi = std::min(kps::kMaxWarps, std::max(lo, (maxH + kps::kTile - 1) / kps::kTile));
+    std::vector<BatchShape> cands;
+    for (int nw = lo; nw <= hi; ++nw) {
+        if (dt == KPS_F64 && kps::vec_smem_bytes(storage, maxnc, nw) > (size_t)kps::max_dyn_smem()) continue;
+        const int per = dt == KPS_F64 ? kps::vec_multi_ctas_per_sm(storage, b->k, maxnc, nw)
+                                      : kps::tmem_multi_ctas_per_sm(storage, b->k, maxnc, nw);
+        if (per < 1) continue;
+        for (int sched = 0; sched < 2; ++sched)
+            for (int mul = 1; mul <= per; mul = mul == per ? per + 1 : per) {
+                BatchShape s;
+                s.nw = nw;
+                s.per_sm = mul;
+                s.grid = sm_count() * mul;
+                s.schedule = sched;
+                cands.push_back(s);
+            }
+    }
+    if (cands.empty()) return fail(KPS_ENOTSUP, "no launch shape fits this batch");
+    const size_t es = dtype_size(dt);
+    void *vin = nullptr, *vout = nullptr;
+    const size_t nin = std::max(b->off[0].back(), b->off[1].back());
+    cudaError_t e = cudaMalloc(&vin, nin * es);
+    if (e == cudaSuccess) e = cudaMalloc(&vout, nin * es);
+    if (e != cudaSuccess) {
+        cudaFree(vin);
+        return fail(KPS_ENOMEM, "tuning buffers");
+    }
+    cudaMemsetAsync(vin, 0, nin * es, stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = -1.f;
+    BatchShape bs = base;
+    for (const BatchShape &c : cands) {
+        b->shape[(int)dt] = c;
+        float tot = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 4 && ok; ++rep) {
+            cudaEventRecord(e0, stream);
+            ok = batch_matvec(b, 0, vin, vout, dt, stream) == KPS_OK && batch_matvec(b, 1, vin, vout, dt, stream) == KPS_OK;
+            cudaEventRecord(e1, stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;   // the first run builds tables and warms up
+        }
+        if (!ok) continue;
+        if (best < 0.f || tot < best) {
+            best = tot;
+            bs = c;
+            bs.ms = tot / 3.f;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(vin);
+    cudaFree(vout);
+    b->shape[(int)dt] = bs;
+    e = cudaGetLastError();
+    if (best < 0.f) return fail(KPS_ECUDA, "every candidate launch shape failed");
+    if (chosen) {
+        chosen->warps = bs.nw;
+        chosen->grid = bs.grid;
+        chosen->schedule = bs.schedule;
+        chosen->ms_per_pair = bs.ms;
+    }
+    return KPS_OK;
+}
+
+kps_status kps_batch_shape_get(kps_batch *b, kps_dtype dt, kps_batch_shape *shape) {
+    if (!b || !shape) return fail(KPS_EINVAL, "bad argument");
+    BatchShape s;
+    kps_status st = batch_default_shape(b, dt, nullptr, &s);
+    if (st != KPS_OK) return st;
+    shape->warps = s.nw;
+    shape->grid = s.grid;
+    shape->schedule = s.schedule;
+    shape->ms_per_pair = s.ms;
+    return KPS_OK;
+}
+
+kps_status kps_batch_shape_set(kps_batch *b, kps_dtype dt, const kps_batch_shape *shape) {
+    if (!b || !shape) return fail(KPS_EINVAL, "bad argument");
+    if (dtype_size(dt) == 0) return fail(KPS_EINVAL, "unknown dtype");
+    BatchShape cur;
+    kps_status st = batch_default_shape(b, dt, nullptr, &cur);
+    if (st != KPS_OK) return st;
+    if (shape->schedule != 0 && shape->schedule != 1) return fail(KPS_EINVAL, "schedule must be 0 or 1");
+    if (shape->grid < 1) return fail(KPS_EINVAL, "grid must be >= 1");
+    const int nw = shape->warps;
+    if (nw < 1 || nw > kps::kMaxWarps) return fail(KPS_EINVAL, "warps must be in 1..8");
+    int maxnc = 0;
+    for (kps_game *g : b->games) maxnc = std::max(maxnc, g->host.ncards + 1);
+    if (dt == KPS_F64) {
+        if (kps::vec_smem_bytes(storage_of(dt), maxnc, nw) > (size_t)kps::max_dyn_smem())
+            return fail(KPS_ENOTSUP, "warp count needs too much shared memory");
+    } else if (nw < tmem_min_warps(b)) {
+        return fail(KPS_ENOTSUP, "warp count leaves a hand chunk too long for tensor memory");
+    }
+    BatchShape s = cur;
+    s.nw = nw;
+    s.grid = shape->grid;
+    s.schedule = shape->schedule;
+    s.ms = 0.0;
+    b->shape[(int)dt] = s;
+    return KPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// Internal state of a batch of games (batch.cu) shared with the solver.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "abi_internal.h"
+#include "kernels.h"
+
+namespace kps_abi {
+
+// Launch shape of the multi-game kernel for one dtype.
+struct BatchShape {
+    int nw = 8;         // warps per CTA
+    int per_sm = 1;     // CTAs per SM
+    int grid = 0;       // CTAs of the persistent launch
+    int schedule = 0;   // 0 ticket counter, 1 static stride
+    double ms = 0.0;    // tuned time of one A and one A^T launch (0 = untuned)
+};
+
+// Device launch table of one (direction, FP64 or not, warp count).
+struct BatchTable {
+    void *blob = nullptr;
+    kps::MultiParams m{};
+};
+
+}  // namespace kps_abi
+
+struct kps_batch {
+    std::vector<kps_game *> games;   // not owned
+    int k = 0;                       // cards per hand (shared)
+    int device = -1;
+    std::vector<long long> off[2];   // element offsets of each game's vector, [ngames + 1]
+    int *ticket = nullptr;           // tile ticket counter (device)
+    std::map<std::tuple<int, bool, int>, kps_abi::BatchTable> tables;
+    std::map<int, kps_abi::BatchShape> shape;   // per dtype
+};
+
+namespace kps_abi {
+
+kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t stream, const BatchTable **out);
+kps_status batch_default_shape(kps_batch *b, kps_dtype dt, cudaStream_t stream, BatchShape *out);
+// dir 0: out = A y per game (y player-2 layout, out player-1 layout); dir 1: A^T.
+kps_status batch_matvec(kps_batch *b, int dir, const void *vin, void *vout, kps_dtype dt, cudaStream_t stream);
+
+}  // namespace kps_abi

@@ -101,3 +101,35 @@ constexpr int kMaxDevices = 64;
 cudaError_t static_scratch_address(void **ptr);
 
 }  // namespace kps
+
+namespace kps {
+
+// Several games in one persistent launch (uneven hand counts and trees).
+// games[g] holds game g's parameters built for `nw` warps, with vin/vout
+// unused: its vectors start in_off[g] / out_off[g] elements after vin /
+// vout.  Column tile j of the launch belongs to game tile_game[j] and is
+// that game's tile j - tile_start[game].  With schedule 0 the CTAs take
+// tiles from the ticket counter *ticket (zeroed before the launch), with
+// schedule 1 CTA b takes tiles b, b + grid, b + 2 grid, ...
+struct MultiParams {
+    const FastParams *games;        // [ngames]
+    const long long *tile_start;    // [ngames + 1]
+    const int *tile_game;           // [total_tiles]
+    const long long *in_off, *out_off;  // [ngames]
+    const void *vin;
+    void *vout;
+    int *ticket;
+    int ngames;
+    int total_tiles;
+    int nw;                         // warps per CTA
+    int nc;                         // largest per-card row count of the games
+    int schedule;
+};
+
+cudaError_t launch_tmem_multi(const MultiParams &m, int storage, int cards_per_hand, int grid, cudaStream_t stream);
+cudaError_t launch_vec_multi(const MultiParams &m, int storage, int cards_per_hand, int grid, cudaStream_t stream);
+// Resident CTAs per SM of the multi-game kernels for the given shape.
+int tmem_multi_ctas_per_sm(int storage, int cards_per_hand, int nc, int nw);
+int vec_multi_ctas_per_sm(int storage, int cards_per_hand, int nc, int nw);
+
+}  // namespace kps

@@ -347,22 +347,25 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
     }
 }
 
+// Shared-memory slot of the CTA's tensor-memory base address.
+__device__ __forceinline__ uint32_t *tm_slot(unsigned char *smem_raw, int nw) {
+    float *sums = reinterpret_cast<float *>(smem_raw + 32 * sizeof(Col)) + 2 * 32;
+    return reinterpret_cast<uint32_t *>(sums + (size_t)nw * 3 * 32);
+}
+
+// One tile of 32 output columns (col = ctile * 32 + lane) of game p.  Ends
+// with every tensor-memory access of the tile complete.
 template <typename S, int K2>
-__global__ void __launch_bounds__(32 * kMaxWarps)
-tmem_scan_kernel(const FastParams p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int hs = p.hs, nw = p.nw;
+__device__ __forceinline__ void tm_tile(const FastParams &p, long long ctile, unsigned char *smem_raw,
+                                        uint32_t tmem) {
+    const int hs = p.hs;
     Col *ci = reinterpret_cast<Col *>(smem_raw);
     float *fco_s = reinterpret_cast<float *>(smem_raw + 32 * sizeof(Col));
     float *sco_s = fco_s + 32;
     float *sums = sco_s + 32;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sums + (size_t)nw * 3 * 32);
-    // two warps share a lane quadrant when more than four run: 512 columns
-    const uint32_t ncols = nw > 4 ? 2 * kRegion : kRegion;
-    if (threadIdx.x < 32) tm_alloc(tmem_slot, ncols);
     int kinds = 0;
     if (threadIdx.x < 32) {
-        const long long col = (long long)blockIdx.x * 32 + threadIdx.x;
+        const long long col = ctile * 32 + threadIdx.x;
         Col c;
         float f = 0.f, s = 0.f;
         if (col < (long long)p.n_out * p.batch) {
@@ -404,14 +407,66 @@ tmem_scan_kernel(const FastParams p) {
     cta.sums = sums;
     cta.uni = __syncthreads_and(same) != 0;
     cta.nvalid = __syncthreads_count(valid);
-    cta.tmem = *tmem_slot;
+    cta.tmem = tmem;
     if (has_f && has_s) tm_body<S, K2, kKindFS>(p, smem_raw, cta, fco_s, sco_s);
     else if (has_s) tm_body<S, K2, kKindS>(p, smem_raw, cta, fco_s, sco_s);
     else tm_body<S, K2, kKindF>(p, smem_raw, cta, fco_s, sco_s);
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
-    if (threadIdx.x < 32) tm_dealloc(cta.tmem, ncols);
+}
+
+template <typename S, int K2>
+__global__ void __launch_bounds__(32 * kMaxWarps)
+tmem_scan_kernel(const FastParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *tmem_slot = tm_slot(smem_raw, p.nw);
+    // two warps share a lane quadrant when more than four run: 512 columns
+    const uint32_t ncols = p.nw > 4 ? 2 * kRegion : kRegion;
+    if (threadIdx.x < 32) tm_alloc(tmem_slot, ncols);
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    tm_tile<S, K2>(p, blockIdx.x, smem_raw, tmem);
+    if (threadIdx.x < 32) tm_dealloc(tmem, ncols);
+}
+
+// Persistent launch over the column tiles of several games.
+template <typename S, int K2>
+__global__ void __launch_bounds__(32 * kMaxWarps)
+tmem_multi_kernel(const MultiParams m) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ FastParams sp;
+    __shared__ long long s_tile;
+    __shared__ int s_game;
+    uint32_t *tmem_slot = tm_slot(smem_raw, m.nw);
+    const uint32_t ncols = m.nw > 4 ? 2 * kRegion : kRegion;
+    if (threadIdx.x < 32) tm_alloc(tmem_slot, ncols);
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    int next = blockIdx.x;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = m.schedule == 0 ? atomicAdd(m.ticket, 1) : next;
+            next += gridDim.x;
+            int g = -1;
+            if (t < m.total_tiles) {
+                g = m.tile_game[t];
+                sp = m.games[g];
+                sp.vin = static_cast<const S *>(m.vin) + m.in_off[g];
+                sp.vout = static_cast<S *>(m.vout) + m.out_off[g];
+                s_tile = t - m.tile_start[g];
+            }
+            s_game = g;
+        }
+        __syncthreads();
+        if (s_game < 0) break;
+        tm_tile<S, K2>(sp, s_tile, smem_raw, tmem);
+    }
+    if (threadIdx.x < 32) tm_dealloc(tmem, ncols);
 }
 
 template <typename S, int K2>
@@ -431,6 +486,29 @@ cudaError_t launch_t(const FastParams &p, size_t smem, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
+template <typename S, int K2>
+cudaError_t launch_multi_t(const MultiParams &m, size_t smem, int grid, cudaStream_t stream) {
+    static size_t configured = 0;
+    auto fn = tmem_multi_kernel<S, K2>;
+    if (configured < smem) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    if (m.total_tiles <= 0) return cudaSuccess;
+    fn<<<grid, 32 * m.nw, smem, stream>>>(m);
+    return cudaGetLastError();
+}
+
+template <typename S, int K2>
+int ctas_t(size_t smem, int nw) {
+    auto fn = tmem_multi_kernel<S, K2>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * nw, smem) != cudaSuccess) return 0;
+    return n;
+}
+
 }  // namespace
 
 size_t tmem_smem_bytes(int nc, int nw) { return tm_header_bytes(nw) + (size_t)nw * tm_warp_floats(nc) * 4; }
@@ -445,6 +523,35 @@ cudaError_t launch_tmem_scan(const FastParams &p, int storage, int k, cudaStream
         case kStoreF16: return k == 1 ? launch_t<__half, 1>(p, smem, stream) : launch_t<__half, 2>(p, smem, stream);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_tmem_multi(const MultiParams &m, int storage, int k, int grid, cudaStream_t stream) {
+    if (m.nc > 66 || m.nw < 1 || m.nw > kMaxWarps || grid < 1) return cudaErrorInvalidValue;
+    const size_t smem = tmem_smem_bytes(m.nc, m.nw);
+    switch (storage) {
+        case kStoreF32:
+            return k == 1 ? launch_multi_t<float, 1>(m, smem, grid, stream) : launch_multi_t<float, 2>(m, smem, grid, stream);
+        case kStoreBF16:
+            return k == 1 ? launch_multi_t<__nv_bfloat16, 1>(m, smem, grid, stream)
+                          : launch_multi_t<__nv_bfloat16, 2>(m, smem, grid, stream);
+        case kStoreF16:
+            return k == 1 ? launch_multi_t<__half, 1>(m, smem, grid, stream) : launch_multi_t<__half, 2>(m, smem, grid, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int tmem_multi_ctas_per_sm(int storage, int k, int nc, int nw) {
+    const size_t smem = tmem_smem_bytes(nc, nw);
+    int n = 0;
+    switch (storage) {
+        case kStoreF32: n = k == 1 ? ctas_t<float, 1>(smem, nw) : ctas_t<float, 2>(smem, nw); break;
+        case kStoreBF16: n = k == 1 ? ctas_t<__nv_bfloat16, 1>(smem, nw) : ctas_t<__nv_bfloat16, 2>(smem, nw); break;
+        case kStoreF16: n = k == 1 ? ctas_t<__half, 1>(smem, nw) : ctas_t<__half, 2>(smem, nw); break;
+        default: return 0;
+    }
+    // tensor memory: 512 columns per SM
+    const int by_tmem = nw > 4 ? 1 : 2;
+    return n < by_tmem ? n : by_tmem;
 }
 
 }  // namespace kps

@@ -456,10 +456,9 @@ __device__ __forceinline__ void scan_body(const FastParams &p, unsigned char *sm
     }
 }
 
+// One tile of 32 output columns (col = ctile * 32 + lane) of game p.
 template <typename S, int K2>
-__global__ void __launch_bounds__(32 * kMaxWarps)
-vec_scan_kernel(const FastParams p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void vec_tile(const FastParams &p, long long ctile, unsigned char *smem_raw) {
     const int hs = p.hs;
     Col *ci = reinterpret_cast<Col *>(smem_raw);
     S *fco_s = reinterpret_cast<S *>(smem_raw + 32 * sizeof(Col));
@@ -467,7 +466,7 @@ vec_scan_kernel(const FastParams p) {
     S *sums = sco_s + 32;
     int kinds = 0;
     if (threadIdx.x < 32) {
-        const long long col = (long long)blockIdx.x * 32 + threadIdx.x;
+        const long long col = ctile * 32 + threadIdx.x;
         Col c;
         S f = S(0), s = S(0);
         if (col < (long long)p.n_out * p.batch) {
@@ -507,6 +506,44 @@ vec_scan_kernel(const FastParams p) {
     if (has_f && has_s) scan_body<S, K2, kKindFS>(p, smem_raw, ci, fco_s, sco_s, sums, uni, nvalid);
     else if (has_s) scan_body<S, K2, kKindS>(p, smem_raw, ci, fco_s, sco_s, sums, uni, nvalid);
     else scan_body<S, K2, kKindF>(p, smem_raw, ci, fco_s, sco_s, sums, uni, nvalid);
+    __syncthreads();
+}
+
+template <typename S, int K2>
+__global__ void __launch_bounds__(32 * kMaxWarps)
+vec_scan_kernel(const FastParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    vec_tile<S, K2>(p, blockIdx.x, smem_raw);
+}
+
+// Persistent launch over the column tiles of several games.
+template <typename S, int K2>
+__global__ void __launch_bounds__(32 * kMaxWarps)
+vec_multi_kernel(const MultiParams m) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ FastParams sp;
+    __shared__ long long s_tile;
+    __shared__ int s_game;
+    int next = blockIdx.x;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = m.schedule == 0 ? atomicAdd(m.ticket, 1) : next;
+            next += gridDim.x;
+            int g = -1;
+            if (t < m.total_tiles) {
+                g = m.tile_game[t];
+                sp = m.games[g];
+                sp.vin = static_cast<const S *>(m.vin) + m.in_off[g];
+                sp.vout = static_cast<S *>(m.vout) + m.out_off[g];
+                sp.scratch = sp.vout;   // partial results pass through the output rows
+                s_tile = t - m.tile_start[g];
+            }
+            s_game = g;
+        }
+        __syncthreads();
+        if (s_game < 0) break;
+        vec_tile<S, K2>(sp, s_tile, smem_raw);
+    }
 }
 
 template <typename S, int K2>
@@ -526,6 +563,29 @@ cudaError_t launch_t(const FastParams &p, size_t smem, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
+template <typename S, int K2>
+cudaError_t launch_multi_t(const MultiParams &m, size_t smem, int grid, cudaStream_t stream) {
+    static size_t configured = 0;
+    auto fn = vec_multi_kernel<S, K2>;
+    if (configured < smem) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    if (m.total_tiles <= 0) return cudaSuccess;
+    fn<<<grid, 32 * m.nw, smem, stream>>>(m);
+    return cudaGetLastError();
+}
+
+template <typename S, int K2>
+int ctas_t(size_t smem, int nw) {
+    auto fn = vec_multi_kernel<S, K2>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * nw, smem) != cudaSuccess) return 0;
+    return n;
+}
+
 }  // namespace
 
 size_t vec_smem_bytes(int storage, int nc, int nw) {
@@ -541,6 +601,27 @@ cudaError_t launch_vec_scan(const FastParams &p, int storage, int k, cudaStream_
         case kStoreF32: return k == 1 ? launch_t<float, 1>(p, smem, stream) : launch_t<float, 2>(p, smem, stream);
         case kStoreF64: return k == 1 ? launch_t<double, 1>(p, smem, stream) : launch_t<double, 2>(p, smem, stream);
         default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_vec_multi(const MultiParams &m, int storage, int k, int grid, cudaStream_t stream) {
+    if (m.nc > kZPitch - 1 || m.nw < 1 || m.nw > kMaxWarps || grid < 1) return cudaErrorInvalidValue;
+    const size_t smem = vec_smem_bytes(storage, m.nc, m.nw);
+    switch (storage) {
+        case kStoreF32:
+            return k == 1 ? launch_multi_t<float, 1>(m, smem, grid, stream) : launch_multi_t<float, 2>(m, smem, grid, stream);
+        case kStoreF64:
+            return k == 1 ? launch_multi_t<double, 1>(m, smem, grid, stream) : launch_multi_t<double, 2>(m, smem, grid, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int vec_multi_ctas_per_sm(int storage, int k, int nc, int nw) {
+    const size_t smem = vec_smem_bytes(storage, nc, nw);
+    switch (storage) {
+        case kStoreF32: return k == 1 ? ctas_t<float, 1>(smem, nw) : ctas_t<float, 2>(smem, nw);
+        case kStoreF64: return k == 1 ? ctas_t<double, 1>(smem, nw) : ctas_t<double, 2>(smem, nw);
+        default: return 0;
     }
 }
 

@@ -1,0 +1,678 @@
+// First-order equilibrium solver on a batch of games (C ABI in include/kps.h).
+//
+// Every iteration of a first-order method needs the gradients A y and
+// -A^T x (Sec. 2, "First-order methods"); everything else is local to one
+// hand of one player.  The solver is regret matching plus (RM+) with
+// alternating updates and linearly weighted averages:
+//   t <- t + 1
+//   player 1: xsum += t x;  g = A y;  bottom-up over player 1's decision
+//     nodes (children first): q(I,a) = g[sigma(I,a)] + sum of the values of
+//     player 1's next decisions under (I,a), v(I) = sum_a b(I,a) q(I,a),
+//     R(I,a) <- max(0, R(I,a) + q(I,a) - v(I));  b <- R / sum_a R
+//     (uniform when the sum is at most the noise floor theta_p);
+//     x <- sequence form of b (x[sigma(I,a)] = x[parent(I)] b(I,a));
+//   player 2: the same against the new x with g = -A^T x.
+// The noise floor: a value that is exactly zero (the opponent's compatible
+// hands all have zero reach while hands sharing a card do not) leaves the
+// product, which subtracts card-overlap masses, as rounding noise, and
+// regret matching would follow the noise.  theta_p = eps * V_p with V_p =
+// max |payoff| * max_h mu_p(h) * sum_h mu_q(h) / beta, a bound on p's
+// counterfactual values, and eps = 2^-40 (FP64) or 2^-16 (FP32 arithmetic)
+// treats regret sums at the noise level as zero.
+// The exploitability of the averages xbar = xsum / sum t, ybar (FP64) is
+// (BR1(ybar) + BR2(xbar)) / 2 / pot0, the best responses taking the max
+// over actions in the same bottom-up walk (Sec. 5 measures average
+// exploitability in units of the initial pot).
+//
+// One thread owns one hand of one game: regrets, values and strategies of
+// a player are [sequence][hand] rows of that game, so a warp's loads and
+// stores of one sequence are coalesced.  Per-thread running values (child
+// values bottom-up, then new sequence-form entries top-down) live in shared
+// memory, [sequence][thread].  Strategies and values are stored in the
+// solver's storage type (FP32, FP64, BF16 or FP16); regrets, averages and
+// all arithmetic are FP32 (FP64 for FP64 storage); the exploitability path
+// is FP64 throughout.  The iteration count lives on the device so that a
+// captured CUDA graph of k iterations can be replayed.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "abi_internal.h"
+#include "batch_internal.h"
+#include "kernels.h"
+
+using namespace kps_abi;
+
+namespace {
+
+constexpr int kThreads = 64;     // hands per block
+constexpr int kMaxActions = 12;  // fold, check/call, up to 8 bets, all-in
+
+struct SolverGame {
+    int H, hs;
+    int n[2];
+    int node_off[2], nnodes[2];
+    long long off[2];
+    int block0;       // first block of the game
+    double pot0;
+    double theta[2];  // regret-matching noise floor of each player
+};
+
+template <typename S> struct Cv;
+template <> struct Cv<float> {
+    __device__ static float ld(const float *p) { return *p; }
+    __device__ static float st(float x) { return x; }
+};
+template <> struct Cv<double> {
+    __device__ static double ld(const double *p) { return *p; }
+    __device__ static double st(double x) { return x; }
+};
+template <> struct Cv<__nv_bfloat16> {
+    __device__ static float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    __device__ static __nv_bfloat16 st(float x) { return __float2bfloat16_rn(x); }
+};
+template <> struct Cv<__half> {
+    __device__ static float ld(const __half *p) { return __half2float(*p); }
+    __device__ static __half st(float x) { return __float2half_rn(x); }
+};
+
+struct Where {
+    int game, h;
+};
+
+__device__ __forceinline__ Where locate(const SolverGame *games, const int *block_game) {
+    Where w;
+    w.game = block_game[blockIdx.x];
+    w.h = (blockIdx.x - games[w.game].block0) * kThreads + threadIdx.x;
+    return w;
+}
+
+// Regret matching of one node: b[a] = R+[a] / sum, uniform if the sum is
+// at most the noise floor theta.
+template <typename C>
+__device__ __forceinline__ void regret_match(const C *r, int na, C *b, C theta) {
+    C sum = C(0);
+#pragma unroll
+    for (int a = 0; a < kMaxActions; ++a)
+        if (a < na) sum += r[a];
+#pragma unroll
+    for (int a = 0; a < kMaxActions; ++a)
+        if (a < na) b[a] = sum > theta ? r[a] / sum : C(1) / C(na);
+}
+
+template <typename S, typename C>
+struct UpdateArgs {
+    const SolverGame *games;
+    const int *block_game;
+    const int4 *nodes;       // {first sequence, actions, parent sequence, 0}
+    int player;
+    C sign;                  // +1: g = A y; -1: g = A^T x (the value is -g)
+    const S *g;              // values, player layout
+    C *regret;
+    S *x;                    // sequence-form strategy (read: played; write: next)
+    C *xsum;                 // sum over iterations of t * x
+    const float *beh0;       // initial behavioural strategy
+    const long long *iter;   // completed iterations
+    const int *has_init;
+};
+
+// One RM+ half-iteration of one player (see the file comment).
+template <typename S, typename C>
+__global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S, C> u) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const Where w = locate(u.games, u.block_game);
+    const SolverGame &G = u.games[w.game];
+    if (w.h >= G.H) return;
+    const int p = u.player, n = G.n[p], hs = G.hs, tid = threadIdx.x;
+    const long long base = G.off[p] + w.h;
+    const long long t = *u.iter + 1;
+    const bool init = *u.has_init != 0 && t == 1;
+    const int4 *nodes = u.nodes + G.node_off[p];
+    const int nn = G.nnodes[p];
+    const C theta = C(G.theta[p]);
+    for (int s = 0; s < n; ++s) {
+        const long long i = base + (long long)s * hs;
+        u.xsum[i] += C(t) * C(Cv<S>::ld(u.x + i));
+        buf[s * kThreads + tid] = C(0);
+    }
+    // bottom-up: values and regrets
+    for (int k = nn - 1; k >= 0; --k) {
+        const int4 nd = nodes[k];
+        const int s0 = nd.x, na = nd.y, par = nd.z;
+        C r[kMaxActions], b[kMaxActions], q[kMaxActions];
+#pragma unroll
+        for (int a = 0; a < kMaxActions; ++a)
+            if (a < na) {
+                const long long i = base + (long long)(s0 + a) * hs;
+                r[a] = u.regret[i];
+                q[a] = u.sign * C(Cv<S>::ld(u.g + i)) + buf[(s0 + a) * kThreads + tid];
+            }
+        if (init) {
+#pragma unroll
+            for (int a = 0; a < kMaxActions; ++a)
+                if (a < na) b[a] = C(u.beh0[base + (long long)(s0 + a) * hs]);
+        } else {
+            regret_match<C>(r, na, b, theta);
+        }
+        C v = C(0);
+#pragma unroll
+        for (int a = 0; a < kMaxActions; ++a)
+            if (a < na) v += b[a] * q[a];
+#pragma unroll
+        for (int a = 0; a < kMaxActions; ++a)
+            if (a < na) {
+                const C rn = r[a] + q[a] - v;
+                u.regret[base + (long long)(s0 + a) * hs] = rn > C(0) ? rn : C(0);
+            }
+        if (par >= 0) buf[par * kThreads + tid] += v;
+    }
+    // top-down: next behavioural strategy and its sequence form
+    for (int k = 0; k < nn; ++k) {
+        const int4 nd = nodes[k];
+        const int s0 = nd.x, na = nd.y, par = nd.z;
+        C r[kMaxActions], b[kMaxActions];
+#pragma unroll
+        for (int a = 0; a < kMaxActions; ++a)
+            if (a < na) r[a] = u.regret[base + (long long)(s0 + a) * hs];
+        regret_match<C>(r, na, b, theta);
+        const C xp = par >= 0 ? buf[par * kThreads + tid] : C(1);
+#pragma unroll
+        for (int a = 0; a < kMaxActions; ++a)
+            if (a < na) {
+                const C xv = xp * b[a];
+                buf[(s0 + a) * kThreads + tid] = xv;
+                u.x[base + (long long)(s0 + a) * hs] = Cv<S>::st(xv);
+            }
+    }
+}
+
+// x <- sequence form of the initial behavioural strategy (uniform if none).
+template <typename S, typename C>
+__global__ void __launch_bounds__(kThreads) seqform_kernel(const UpdateArgs<S, C> u) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const Where w = locate(u.games, u.block_game);
+    const SolverGame &G = u.games[w.game];
+    if (w.h >= G.H) return;
+    const int p = u.player, hs = G.hs, tid = threadIdx.x;
+    const long long base = G.off[p] + w.h;
+    const bool init = *u.has_init != 0;
+    const int4 *nodes = u.nodes + G.node_off[p];
+    for (int k = 0; k < G.nnodes[p]; ++k) {
+        const int4 nd = nodes[k];
+        const int s0 = nd.x, na = nd.y, par = nd.z;
+        const C xp = par >= 0 ? buf[par * kThreads + tid] : C(1);
+        for (int a = 0; a < na; ++a) {
+            const long long i = base + (long long)(s0 + a) * hs;
+            const C b = init ? C(u.beh0[i]) : C(1) / C(na);
+            buf[(s0 + a) * kThreads + tid] = xp * b;
+            u.x[i] = Cv<S>::st(xp * b);
+        }
+    }
+}
+
+__global__ void bump_kernel(long long *iter) { *iter += 1; }
+
+// FP64 averages: sequence form xsum / sum_t t (the current strategy before
+// any iteration), or behavioural (x[sigma] / x[parent], uniform where the
+// parent is never reached).
+template <typename S, typename C>
+__global__ void __launch_bounds__(kThreads) average_kernel(const UpdateArgs<S, C> u, double *out, int behavioural) {
+    const Where w = locate(u.games, u.block_game);
+    const SolverGame &G = u.games[w.game];
+    if (w.h >= G.H) return;
+    const int p = u.player, hs = G.hs;
+    const long long base = G.off[p] + w.h;
+    const long long t = *u.iter;
+    const double wsum = 0.5 * (double)t * (double)(t + 1);
+    auto avg = [&](int s) -> double {
+        const long long i = base + (long long)s * hs;
+        return t > 0 ? (double)u.xsum[i] / wsum : (double)Cv<S>::ld(u.x + i);
+    };
+    const int4 *nodes = u.nodes + G.node_off[p];
+    for (int k = 0; k < G.nnodes[p]; ++k) {
+        const int4 nd = nodes[k];
+        const int s0 = nd.x, na = nd.y, par = nd.z;
+        const double xp = par >= 0 ? avg(par) : 1.0;
+        for (int a = 0; a < na; ++a) {
+            const double xa = avg(s0 + a);
+            double v = xa;
+            if (behavioural) v = xp > 0.0 ? xa / xp : 1.0 / na;
+            out[base + (long long)(s0 + a) * hs] = v;
+        }
+    }
+}
+
+struct BrArgs {
+    const SolverGame *games;
+    const int *block_game;
+    const int4 *nodes;
+    int player;
+    double sign;
+    double *g;          // FP64 values, player layout (accumulated in place)
+    double *partial;    // [blocks]
+};
+
+// Best response value of every hand: bottom-up max over the player's
+// actions; the sum over the block's hands goes to partial[block].
+__global__ void __launch_bounds__(kThreads) best_response_kernel(const BrArgs a) {
+    __shared__ double red[kThreads];
+    const Where w = locate(a.games, a.block_game);
+    const SolverGame &G = a.games[w.game];
+    double root = 0.0;
+    if (w.h < G.H) {
+        const int p = a.player, hs = G.hs;
+        const long long base = G.off[p] + w.h;
+        const int4 *nodes = a.nodes + G.node_off[p];
+        // child values are added into the parent's value entry: the parent's
+        // node comes earlier in pre-order, so it is read after all of them
+        for (int k = G.nnodes[p] - 1; k >= 0; --k) {
+            const int4 nd = nodes[k];
+            const int s0 = nd.x, na = nd.y, par = nd.z;
+            double v = -1e300;
+            for (int q = 0; q < na; ++q) {
+                const double val = a.sign * a.g[base + (long long)(s0 + q) * hs];
+                v = val > v ? val : v;
+            }
+            if (par >= 0) a.g[base + (long long)par * hs] += a.sign * v;
+            else root += v;
+        }
+    }
+    red[threadIdx.x] = root;
+    __syncthreads();
+    for (int st = kThreads / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.partial[blockIdx.x] = red[0];
+}
+
+// expl[g] = (BR1 + BR2) / 2 / pot0, sums over each game's blocks in order.
+__global__ void expl_kernel(const SolverGame *games, int ngames, const int *nblocks, const double *part1,
+                            const double *part2, double *expl, double *br1, double *br2) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngames) return;
+    const int b0 = games[g].block0, nb = nblocks[g];
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = b0; b < b0 + nb; ++b) {
+        s1 += part1[b];
+        s2 += part2[b];
+    }
+    if (br1) br1[g] = s1;
+    if (br2) br2[g] = s2;
+    expl[g] = 0.5 * (s1 + s2) / games[g].pot0;
+}
+
+}  // namespace
+
+struct kps_solver {
+    kps_batch *batch = nullptr;
+    kps_dtype dt = KPS_F32;
+    int nblocks = 0, nmax = 0;
+    void *blob = nullptr;           // games, block_game, nblocks, nodes
+    SolverGame *games = nullptr;
+    int *block_game = nullptr, *game_blocks = nullptr;
+    int4 *nodes = nullptr;
+    // state, per player (concatenated layouts)
+    void *g[2] = {nullptr, nullptr}, *x[2] = {nullptr, nullptr};
+    void *regret[2] = {nullptr, nullptr}, *xsum[2] = {nullptr, nullptr};
+    float *beh0[2] = {nullptr, nullptr};
+    double *xa[2] = {nullptr, nullptr}, *g64[2] = {nullptr, nullptr};
+    double *partial[2] = {nullptr, nullptr};
+    long long *iter = nullptr;      // [0] iterations, then has_init as int
+    int *has_init = nullptr;
+    long long iters_host = 0;
+    cudaStream_t cap = nullptr;     // capture stream
+    std::map<int, cudaGraphExec_t> graphs;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+size_t elem_size(kps_dtype dt) { return dtype_size(dt); }
+size_t compute_size(kps_dtype dt) { return dt == KPS_F64 ? 8 : 4; }
+
+template <typename S, typename C>
+UpdateArgs<S, C> make_args(kps_solver *s, int p) {
+    UpdateArgs<S, C> u;
+    u.games = s->games;
+    u.block_game = s->block_game;
+    u.nodes = s->nodes;
+    u.player = p;
+    u.sign = p == 0 ? C(1) : C(-1);
+    u.g = static_cast<const S *>(s->g[p]);
+    u.regret = static_cast<C *>(s->regret[p]);
+    u.x = static_cast<S *>(s->x[p]);
+    u.xsum = static_cast<C *>(s->xsum[p]);
+    u.beh0 = s->beh0[p];
+    u.iter = s->iter;
+    u.has_init = s->has_init;
+    return u;
+}
+
+// Raises a kernel's dynamic shared-memory limit once per size (never
+// inside a stream capture: the solver warms every kernel up first).
+cudaError_t smem_limit(const void *kernel, size_t smem) {
+    static std::mutex mu;
+    static std::map<const void *, size_t> done;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &have = done[kernel];
+    if (smem <= 48 * 1024 || smem <= have) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) have = smem;
+    return e;
+}
+
+template <typename S, typename C, typename K>
+cudaError_t launch_node_kernel(kps_solver *s, K kernel, const UpdateArgs<S, C> &u, size_t smem, cudaStream_t st) {
+    cudaError_t e = smem_limit(reinterpret_cast<const void *>(kernel), smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<s->nblocks, kThreads, smem, st>>>(u);
+    return cudaGetLastError();
+}
+
+template <typename S, typename C>
+cudaError_t update_t(kps_solver *s, int p, cudaStream_t st) {
+    const size_t smem = (size_t)s->nmax * kThreads * sizeof(C);
+    return launch_node_kernel(s, rm_update_kernel<S, C>, make_args<S, C>(s, p), smem, st);
+}
+
+template <typename S, typename C>
+cudaError_t seqform_t(kps_solver *s, int p, cudaStream_t st) {
+    const size_t smem = (size_t)s->nmax * kThreads * sizeof(C);
+    return launch_node_kernel(s, seqform_kernel<S, C>, make_args<S, C>(s, p), smem, st);
+}
+
+template <typename S, typename C>
+cudaError_t average_t(kps_solver *s, int p, double *out, int behavioural, cudaStream_t st) {
+    average_kernel<S, C><<<s->nblocks, kThreads, 0, st>>>(make_args<S, C>(s, p), out, behavioural);
+    return cudaGetLastError();
+}
+
+// Dispatch on the storage type.
+#define KPS_DISPATCH(dt, F, ...)                                                        \
+    ((dt) == KPS_F32    ? F<float, float>(__VA_ARGS__)                                  \
+     : (dt) == KPS_F64  ? F<double, double>(__VA_ARGS__)                                \
+     : (dt) == KPS_BF16 ? F<__nv_bfloat16, float>(__VA_ARGS__)                          \
+                        : F<__half, float>(__VA_ARGS__))
+
+kps_status one_iteration(kps_solver *s, cudaStream_t st) {
+    kps_status r = batch_matvec(s->batch, 0, s->x[1], s->g[0], s->dt, st);
+    if (r != KPS_OK) return r;
+    cudaError_t e = KPS_DISPATCH(s->dt, update_t, s, 0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "player-1 update");
+    r = batch_matvec(s->batch, 1, s->x[0], s->g[1], s->dt, st);
+    if (r != KPS_OK) return r;
+    e = KPS_DISPATCH(s->dt, update_t, s, 1, st);
+    if (e != cudaSuccess) return cuda_fail(e, "player-2 update");
+    bump_kernel<<<1, 1, 0, st>>>(s->iter);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "iteration counter");
+    return KPS_OK;
+}
+
+void free_solver(kps_solver *s) {
+    for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    for (void *p : s->allocs) cudaFree(p);
+    if (s->cap) cudaStreamDestroy(s->cap);
+    delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+kps_status kps_solver_create(kps_batch *b, kps_dtype dt, kps_solver **out) {
+    if (!out) return fail(KPS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!b) return fail(KPS_EINVAL, "batch is NULL");
+    if (dtype_size(dt) == 0) return fail(KPS_EINVAL, "unknown dtype");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != b->device) return fail(KPS_EINVAL, "batch tables live on another device");
+    kps_solver *s = new (std::nothrow) kps_solver;
+    if (!s) return fail(KPS_ENOMEM, "solver object");
+    s->batch = b;
+    s->dt = dt;
+    const int ng = (int)b->games.size();
+    std::vector<SolverGame> games(ng);
+    std::vector<int> block_game, game_blocks(ng);
+    std::vector<int4> nodes;
+    for (int i = 0; i < ng; ++i) {
+        const kps::HostGame &h = b->games[i]->host;
+        SolverGame &G = games[i];
+        G.H = h.H;
+        G.hs = h.hs;
+        G.pot0 = h.pot0;
+        G.block0 = (int)block_game.size();
+        {
+            double cmax = 0.0;
+            for (const kps::Terminal &z : h.terms) cmax = std::max(cmax, std::max(z.c1, z.c2));
+            const double eps = dt == KPS_F64 ? 1.0 / 1099511627776.0 : 1.0 / 65536.0;
+            for (int p = 0; p < 2; ++p) {
+                const std::vector<double> &mp = p == 0 ? h.mu1 : h.mu2, &mq = p == 0 ? h.mu2 : h.mu1;
+                double mmax = 0.0, msum = 0.0;
+                for (double v : mp) mmax = std::max(mmax, v);
+                for (double v : mq) msum += v;
+                G.theta[p] = eps * cmax * mmax * msum / h.beta;
+            }
+        }
+        const int nb = (h.H + kThreads - 1) / kThreads;
+        game_blocks[i] = nb;
+        for (int k = 0; k < nb; ++k) block_game.push_back(i);
+        for (int p = 0; p < 2; ++p) {
+            G.n[p] = h.n[p];
+            G.off[p] = b->off[p][i];
+            G.node_off[p] = (int)nodes.size();
+            G.nnodes[p] = h.nodes[p];
+            s->nmax = std::max(s->nmax, h.n[p]);
+            // first sequence of every node (sequences of a node are consecutive)
+            std::vector<int> first(h.nodes[p], -1);
+            for (int q = 0; q < h.n[p]; ++q)
+                if (first[h.seqs[p][q].node] < 0) first[h.seqs[p][q].node] = q;
+            for (int k = 0; k < h.nodes[p]; ++k) {
+                const int na = h.nodes_nact[p][k];
+                if (na > kMaxActions || first[k] < 0) {
+                    free_solver(s);
+                    return fail(KPS_ENOTSUP, "a decision node has more than 12 actions");
+                }
+                nodes.push_back(make_int4(first[k], na, h.seqs[p][first[k]].parent, 0));
+            }
+        }
+    }
+    s->nblocks = (int)block_game.size();
+    const size_t csz = compute_size(dt);
+    if ((size_t)s->nmax * kThreads * csz > (size_t)kps::max_dyn_smem()) {
+        free_solver(s);
+        return fail(KPS_ENOTSUP, "too many sequences per player for the solver's shared memory");
+    }
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t o_g = 0, o_bg = al(sizeof(SolverGame) * ng), o_gb = al(o_bg + 4 * block_game.size()),
+                 o_nd = al(o_gb + 4 * (size_t)ng), o_it = al(o_nd + sizeof(int4) * std::max<size_t>(1, nodes.size())),
+                 total = al(o_it + 16);
+    std::vector<unsigned char> host(total, 0);
+    std::memcpy(host.data() + o_g, games.data(), sizeof(SolverGame) * ng);
+    std::memcpy(host.data() + o_bg, block_game.data(), 4 * block_game.size());
+    std::memcpy(host.data() + o_gb, game_blocks.data(), 4 * (size_t)ng);
+    if (!nodes.empty()) std::memcpy(host.data() + o_nd, nodes.data(), sizeof(int4) * nodes.size());
+    auto alloc = [&](size_t bytes, void **p) -> bool {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 256)) != cudaSuccess) return false;
+        s->allocs.push_back(*p);
+        return true;
+    };
+    if (!alloc(total, &s->blob)) { free_solver(s); return fail(KPS_ENOMEM, "solver tables"); }
+    cudaError_t e = cudaMemcpy(s->blob, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { free_solver(s); return cuda_fail(e, "uploading solver tables"); }
+    unsigned char *bl = static_cast<unsigned char *>(s->blob);
+    s->games = reinterpret_cast<SolverGame *>(bl + o_g);
+    s->block_game = reinterpret_cast<int *>(bl + o_bg);
+    s->game_blocks = reinterpret_cast<int *>(bl + o_gb);
+    s->nodes = reinterpret_cast<int4 *>(bl + o_nd);
+    s->iter = reinterpret_cast<long long *>(bl + o_it);
+    s->has_init = reinterpret_cast<int *>(bl + o_it + 8);
+    const size_t es = elem_size(dt);
+    for (int p = 0; p < 2; ++p) {
+        const size_t len = (size_t)b->off[p].back();
+        bool ok = alloc(len * es, &s->g[p]) && alloc(len * es, &s->x[p]) && alloc(len * csz, &s->regret[p]) &&
+                  alloc(len * csz, &s->xsum[p]) && alloc(len * 4, reinterpret_cast<void **>(&s->beh0[p])) &&
+                  alloc(len * 8, reinterpret_cast<void **>(&s->xa[p])) &&
+                  alloc(len * 8, reinterpret_cast<void **>(&s->g64[p])) &&
+                  alloc((size_t)s->nblocks * 8, reinterpret_cast<void **>(&s->partial[p]));
+        if (!ok) { free_solver(s); return fail(KPS_ENOMEM, "solver state"); }
+    }
+    e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { free_solver(s); return cuda_fail(e, "capture stream"); }
+    // launch tables of the products the solver uses, built before any capture
+    for (kps_dtype d : {dt, KPS_F64}) {
+        BatchShape sh;
+        kps_status st = batch_default_shape(b, d, nullptr, &sh);
+        for (int dir = 0; dir < 2 && st == KPS_OK; ++dir) {
+            const BatchTable *t = nullptr;
+            st = batch_table(b, dir, d == KPS_F64, sh.nw, nullptr, &t);
+        }
+        if (st != KPS_OK) { free_solver(s); return st; }
+    }
+    // one iteration outside any capture sets every kernel attribute; then start over
+    kps_status st = kps_solver_reset(s, nullptr, nullptr, nullptr);
+    if (st == KPS_OK) st = one_iteration(s, nullptr);
+    if (st == KPS_OK) st = kps_solver_reset(s, nullptr, nullptr, nullptr);
+    if (st != KPS_OK) { free_solver(s); return st; }
+    *out = s;
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_solver(s);
+        *out = nullptr;
+        return cuda_fail(e, "solver set-up");
+    }
+    return KPS_OK;
+}
+
+kps_status kps_solver_destroy(kps_solver *s) {
+    if (s) free_solver(s);
+    return KPS_OK;
+}
+
+kps_status kps_solver_reset(kps_solver *s, const float *beh1, const float *beh2, void *stream_ptr) {
+    if (!s) return fail(KPS_EINVAL, "solver is NULL");
+    if ((beh1 == nullptr) != (beh2 == nullptr)) return fail(KPS_EINVAL, "give both initial strategies or neither");
+    cudaStream_t st = static_cast<cudaStream_t>(stream_ptr);
+    const size_t es = elem_size(s->dt), csz = compute_size(s->dt);
+    const int init = beh1 ? 1 : 0;
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+        const size_t len = (size_t)s->batch->off[p].back();
+        e = cudaMemsetAsync(s->regret[p], 0, len * csz, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->xsum[p], 0, len * csz, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->x[p], 0, len * es, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->g[p], 0, len * es, st);
+        if (e == cudaSuccess && init)
+            e = cudaMemcpyAsync(s->beh0[p], p == 0 ? beh1 : beh2, len * 4, cudaMemcpyDeviceToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->iter, 0, 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->has_init, init ? 0x01 : 0x00, 1, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(reinterpret_cast<char *>(s->has_init) + 1, 0, 3, st);
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = KPS_DISPATCH(s->dt, seqform_t, s, p, st);
+    if (e != cudaSuccess) return cuda_fail(e, "resetting the solver");
+    s->iters_host = 0;
+    return KPS_OK;
+}
+
+kps_status kps_solver_step(kps_solver *s, int32_t iters, void *stream_ptr) {
+    if (!s) return fail(KPS_EINVAL, "solver is NULL");
+    if (iters < 0) return fail(KPS_EINVAL, "iters must be >= 0");
+    if (iters == 0) return KPS_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream_ptr);
+    auto it = s->graphs.find(iters);
+    if (it == s->graphs.end()) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "beginning graph capture");
+        kps_status r = KPS_OK;
+        for (int k = 0; k < iters && r == KPS_OK; ++k) r = one_iteration(s, s->cap);
+        e = cudaStreamEndCapture(s->cap, &graph);
+        if (r != KPS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "ending graph capture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "instantiating the iteration graph");
+        it = s->graphs.emplace(iters, exec).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the iteration graph");
+    s->iters_host += iters;
+    return KPS_OK;
+}
+
+kps_status kps_solver_iterations(const kps_solver *s, int64_t *t) {
+    if (!s || !t) return fail(KPS_EINVAL, "bad argument");
+    *t = s->iters_host;
+    return KPS_OK;
+}
+
+kps_status kps_solver_average(kps_solver *s, int32_t behavioural, double *x, double *y, void *stream_ptr) {
+    if (!s) return fail(KPS_EINVAL, "solver is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream_ptr);
+    for (int p = 0; p < 2; ++p) {
+        double *dst = p == 0 ? x : y;
+        if (!dst) continue;
+        cudaError_t e = KPS_DISPATCH(s->dt, average_t, s, p, dst, behavioural ? 1 : 0, st);
+        if (e != cudaSuccess) return cuda_fail(e, "averaging");
+    }
+    return KPS_OK;
+}
+
+kps_status kps_solver_strategy(kps_solver *s, void *x, void *y, void *stream_ptr) {
+    if (!s) return fail(KPS_EINVAL, "solver is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream_ptr);
+    const size_t es = elem_size(s->dt);
+    for (int p = 0; p < 2; ++p) {
+        void *dst = p == 0 ? x : y;
+        if (!dst) continue;
+        cudaError_t e = cudaMemcpyAsync(dst, s->x[p], (size_t)s->batch->off[p].back() * es, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "copying the strategy");
+    }
+    return KPS_OK;
+}
+
+kps_status kps_solver_exploitability(kps_solver *s, double *expl, double *br1, double *br2, void *stream_ptr) {
+    if (!s || !expl) return fail(KPS_EINVAL, "bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream_ptr);
+    for (int p = 0; p < 2; ++p) {
+        cudaError_t e = KPS_DISPATCH(s->dt, average_t, s, p, s->xa[p], 0, st);
+        if (e != cudaSuccess) return cuda_fail(e, "averaging");
+    }
+    kps_status r = batch_matvec(s->batch, 0, s->xa[1], s->g64[0], KPS_F64, st);
+    if (r == KPS_OK) r = batch_matvec(s->batch, 1, s->xa[0], s->g64[1], KPS_F64, st);
+    if (r != KPS_OK) return r;
+    for (int p = 0; p < 2; ++p) {
+        BrArgs a;
+        a.games = s->games;
+        a.block_game = s->block_game;
+        a.nodes = s->nodes;
+        a.player = p;
+        a.sign = p == 0 ? 1.0 : -1.0;
+        a.g = s->g64[p];
+        a.partial = s->partial[p];
+        best_response_kernel<<<s->nblocks, kThreads, 0, st>>>(a);
+    }
+    const int ng = (int)s->batch->games.size();
+    expl_kernel<<<(ng + 127) / 128, 128, 0, st>>>(s->games, ng, s->game_blocks, s->partial[0], s->partial[1], expl, br1,
+                                                  br2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "best response");
+    return KPS_OK;
+}
+
+}  // extern "C"

@@ -54,10 +54,22 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchShape(C.Structure):
+    _fields_ = [("warps", C.c_int32), ("grid", C.c_int32), ("schedule", C.c_int32),
+                ("ms_per_pair", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTED = ["kps_sparsify", "kps_game_destroy", "kps_game_info", "kps_game_hands",
             "kps_game_sequences", "kps_game_terminals", "kps_game_upload",
             "kps_matvec_A", "kps_matvec_AT", "kps_matvec_A_host", "kps_matvec_AT_host",
             "kps_matvec_A_static_scratch",
+            "kps_batch_create", "kps_batch_destroy", "kps_batch_offsets", "kps_batch_matvec_A",
+            "kps_batch_matvec_AT", "kps_batch_tune", "kps_batch_shape_get", "kps_batch_shape_set",
+            "kps_solver_create", "kps_solver_destroy", "kps_solver_reset", "kps_solver_step",
+            "kps_solver_iterations", "kps_solver_average", "kps_solver_strategy", "kps_solver_exploitability",
             "kps_last_error", "kps_version"]
 
 _lib = None
@@ -81,6 +93,22 @@ def lib():
         for f in (L.kps_matvec_A, L.kps_matvec_AT, L.kps_matvec_A_host, L.kps_matvec_AT_host,
                   L.kps_matvec_A_static_scratch):
             f.argtypes = [P, P, P, C.c_int32, C.c_int, P]
+        L.kps_batch_create.argtypes = [P, C.c_int32, C.POINTER(C.c_void_p)]
+        L.kps_batch_destroy.argtypes = [P]
+        L.kps_batch_offsets.argtypes = [P, C.c_int32, P]
+        L.kps_batch_matvec_A.argtypes = [P, P, P, C.c_int, P]
+        L.kps_batch_matvec_AT.argtypes = [P, P, P, C.c_int, P]
+        L.kps_batch_tune.argtypes = [P, C.c_int, P, C.POINTER(BatchShape)]
+        L.kps_batch_shape_get.argtypes = [P, C.c_int, C.POINTER(BatchShape)]
+        L.kps_batch_shape_set.argtypes = [P, C.c_int, C.POINTER(BatchShape)]
+        L.kps_solver_create.argtypes = [P, C.c_int, C.POINTER(C.c_void_p)]
+        L.kps_solver_destroy.argtypes = [P]
+        L.kps_solver_reset.argtypes = [P, P, P, P]
+        L.kps_solver_step.argtypes = [P, C.c_int32, P]
+        L.kps_solver_iterations.argtypes = [P, C.POINTER(C.c_int64)]
+        L.kps_solver_average.argtypes = [P, C.c_int32, P, P, P]
+        L.kps_solver_exploitability.argtypes = [P, P, P, P, P]
+        L.kps_solver_strategy.argtypes = [P, P, P, P]
         for name in EXPORTED:
             if name not in ("kps_last_error", "kps_version"):
                 getattr(L, name).restype = C.c_int
@@ -250,6 +278,99 @@ def matvec_A_static_scratch(game: Game, y, out, batch: int, dtype=None, stream=N
     (statically reserved scratch; see include/kps.h for the contract)."""
     _check(lib().kps_matvec_A_static_scratch(game._h, _ptr(y), _ptr(out), int(batch), _dtype_code(y, dtype),
                                              _stream(stream)))
+
+
+class Batch:
+    """Several games whose products run as one persistent launch
+    (``kps_batch_*``).  Keeps the games alive while it lives."""
+
+    def __init__(self, games):
+        self.games = list(games)
+        arr = (C.c_void_p * len(self.games))(*[g.handle for g in self.games])
+        h = C.c_void_p()
+        _check(lib().kps_batch_create(arr, len(self.games), C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().kps_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def offsets(self, player: int) -> np.ndarray:
+        off = np.zeros(len(self.games) + 1, dtype=np.int64)
+        _check(lib().kps_batch_offsets(self._h, player, off.ctypes.data))
+        return off
+
+    def matvec_A(self, y, out, dtype=None, stream=None):
+        _check(lib().kps_batch_matvec_A(self._h, _ptr(y), _ptr(out), _dtype_code(y, dtype), _stream(stream)))
+
+    def matvec_AT(self, x, out, dtype=None, stream=None):
+        _check(lib().kps_batch_matvec_AT(self._h, _ptr(x), _ptr(out), _dtype_code(x, dtype), _stream(stream)))
+
+    def tune(self, dtype: int, stream=None) -> dict:
+        sh = BatchShape()
+        _check(lib().kps_batch_tune(self._h, dtype, _stream(stream), C.byref(sh)))
+        return sh.as_dict()
+
+    def shape(self, dtype: int) -> dict:
+        sh = BatchShape()
+        _check(lib().kps_batch_shape_get(self._h, dtype, C.byref(sh)))
+        return sh.as_dict()
+
+    def set_shape(self, dtype: int, warps: int, grid: int, schedule: int):
+        sh = BatchShape(warps, grid, schedule, 0.0)
+        _check(lib().kps_batch_shape_set(self._h, dtype, C.byref(sh)))
+
+
+class Solver:
+    """RM+ solver over a batch (``kps_solver_*``)."""
+
+    def __init__(self, batch: Batch, dtype: int):
+        self.batch = batch
+        h = C.c_void_p()
+        _check(lib().kps_solver_create(batch._h, dtype, C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().kps_solver_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, beh1=None, beh2=None, stream=None):
+        _check(lib().kps_solver_reset(self._h, _ptr(beh1), _ptr(beh2), _stream(stream)))
+
+    def step(self, iters: int, stream=None):
+        _check(lib().kps_solver_step(self._h, int(iters), _stream(stream)))
+
+    def iterations(self) -> int:
+        t = C.c_int64()
+        _check(lib().kps_solver_iterations(self._h, C.byref(t)))
+        return t.value
+
+    def average(self, x, y, behavioural: bool = False, stream=None):
+        _check(lib().kps_solver_average(self._h, 1 if behavioural else 0, _ptr(x), _ptr(y), _stream(stream)))
+
+    def strategy(self, x, y, stream=None):
+        _check(lib().kps_solver_strategy(self._h, _ptr(x), _ptr(y), _stream(stream)))
+
+    def exploitability(self, expl, br1=None, br2=None, stream=None):
+        _check(lib().kps_solver_exploitability(self._h, _ptr(expl), _ptr(br1), _ptr(br2), _stream(stream)))
 
 
 def version() -> str:
