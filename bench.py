@@ -44,6 +44,11 @@ def _args():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--workload", default="matvec", choices=["matvec", "batch", "solver"],
+                    help="matvec: the headline line; batch / solver: print only that measurement")
+    ap.add_argument("--games", type=int, default=4096, help="games of the batched workload")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the batched and solver measurements in the headline line")
     return ap.parse_args()
 
 
@@ -276,6 +281,110 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+BATCH_WORKLOAD = ("uneven river endgames in one persistent launch: boards of 3-5 cards (1176/1128/1081 "
+                  "hands), 13-209 terminals, one fp32 vector per game and player")
+
+
+def measure_batch(ngames: int, steps: int, warmup: int, rank: int = 0):
+    """Batched products over `ngames` uneven games (one A and one A^T launch
+    per step, captured in a CUDA graph), launch shape from the autotuner."""
+    import torch
+    from paper_2112_03804_gb300 import kps, synth
+    specs = synth.batch_specs(seed=4 + 7919 * rank, n=ngames)
+    games = [kps.Game(sp) for sp in specs]
+    b = kps.Batch(games)
+    stream = torch.cuda.current_stream()
+    off = [b.offsets(p) for p in (0, 1)]
+    vec = {}
+    for p in (0, 1):
+        flat = np.zeros(int(off[p][-1]), dtype=np.float32)
+        for i, g in enumerate(games):
+            inf = g.info()
+            v = synth.simplex_vectors(g.sequences(p)["nact"], inf["H"], 1, seed=11 * i + p, dtype=np.float32)[0]
+            w = np.zeros((v.shape[0], inf["hs"]), dtype=np.float32)
+            w[:, :inf["H"]] = v
+            flat[off[p][i]:off[p][i + 1]] = w.reshape(-1)
+        vec[p] = torch.from_numpy(flat).cuda()
+    out = {p: torch.empty(int(off[p][-1]), device="cuda") for p in (0, 1)}
+    shape = b.tune(kps.F32, stream)
+    # one step = A y and A^T x for every game, captured once as a graph
+    b.matvec_A(vec[1], out[0], stream=stream)
+    b.matvec_AT(vec[0], out[1], stream=stream)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        b.matvec_A(vec[1], out[0], stream=side)
+        b.matvec_AT(vec[0], out[1], stream=side)
+    torch.cuda.synchronize()
+    for _ in range(max(warmup, 3)):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    alg = 0.0
+    for g in games:
+        inf = g.info()
+        alg += 4.0 * inf["H"] * (inf["n1"] + inf["n2"])
+    return {"workload": BATCH_WORKLOAD, "games": ngames, "matvecs_per_s": 2 * ngames / (ms / 1e3),
+            "ms_per_step": ms, "alg_bytes_per_step": alg, "achieved_gbs": alg / (ms / 1e3) / 1e9,
+            "launch_shape": {k: shape[k] for k in ("warps", "grid", "schedule")},
+            "tuned_ms_per_pair": shape["ms_per_pair"], "cuda_graph": True,
+            "l2": "inputs larger than L2" if alg > 2.6e8 else "inputs smaller than L2"}
+
+
+def measure_solver(target: float = 1e-3, block: int = 25, max_iters: int = 4000):
+    """RM+ on the tiny Kronecker game (6 one-card hands) until the FP64
+    exploitability of the averages is below `target` of the pot, per storage
+    type; error against the FP64-storage run at every checkpoint."""
+    import torch
+    from paper_2112_03804_gb300 import kps, synth
+    spec = synth.tiny_spec()
+    g = kps.Game(spec)
+    b = kps.Batch([g])
+    res = {}
+    traces = {}
+    names = {kps.F64: "f64", kps.F32: "f32", kps.BF16: "bf16", kps.F16: "f16"}
+    for dt in (kps.F64, kps.F32, kps.BF16, kps.F16):
+        s = kps.Solver(b, dt)
+        e = torch.zeros(1, dtype=torch.float64, device="cuda")
+        s.step(block)          # capture the graph outside the timed run
+        s.reset()
+        torch.cuda.synchronize()
+        tr = []
+        it = 0
+        t0 = time.perf_counter()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        while it < max_iters:
+            s.step(block)
+            it += block
+            s.exploitability(e)
+            v = float(e.item())
+            tr.append(v)
+            if v < target:
+                break
+        ev1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        traces[dt] = tr
+        res[names[dt]] = {"iters_to_target": it if tr[-1] < target else None, "final_expl": tr[-1],
+                          "wall_ms": 1e3 * wall, "gpu_ms": ev0.elapsed_time(ev1)}
+        s.close()
+    ref = traces[kps.F64]
+    for dt in (kps.F32, kps.BF16, kps.F16):
+        n = min(len(ref), len(traces[dt]))
+        res[names[dt]]["max_abs_err_vs_f64"] = float(np.max(np.abs(np.array(traces[dt][:n]) - np.array(ref[:n]))))
+    return {"game": "tiny Kronecker game: 3 ranks x 2 suits, one card each (6 hands), 7+7 sequences",
+            "target_expl_pot": target, "check_every": block, "by_storage": res}
+
+
 def _e2e(g, y, x, oy, ox, stream, args, world):
     import torch
     from paper_2112_03804_gb300 import kps
@@ -327,6 +436,12 @@ def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec):
         del line["e2e"]
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_seconds)
+    if not args.no_secondary:
+        for key, fn in (("batched", lambda: measure_batch(args.games, 10, 3)), ("solver", measure_solver)):
+            try:
+                line[key] = fn()
+            except Exception as exc:   # reported, never silently dropped
+                line[key] = {"error": f"{type(exc).__name__}: {exc}"}
     print(json.dumps(line), flush=True)
 
 
@@ -334,6 +449,14 @@ def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        import torch
+        torch.cuda.set_device(_dist()[2])
+        print(json.dumps(measure_batch(args.games, args.steps, args.warmup)), flush=True)
+    elif args.workload == "solver":
+        import torch
+        torch.cuda.set_device(_dist()[2])
+        print(json.dumps(measure_solver()), flush=True)
     else:
         run_ours(args)
 
