@@ -967,6 +967,13 @@ double orc_exploitability(const orc_game *g, const double *x, const double *y,
 double orc_rmplus(const orc_game *g, int iters, const double *beh1_0, const double *beh2_0,
                   double *avg_beh1, double *avg_beh2, double *trace, int trace_every)
 {
+    return orc_rmplus_warm(g, iters, beh1_0, beh2_0, 0.0, 0, avg_beh1, avg_beh2, trace, trace_every);
+}
+
+double orc_rmplus_warm(const orc_game *g, int iters, const double *beh1_0, const double *beh2_0,
+                       double kappa, int t0, double *avg_beh1, double *avg_beh2, double *trace,
+                       int trace_every)
+{
     int H = g->H, n1 = g->n[0], n2 = g->n[1];
     size_t N1 = (size_t)n1 * H, N2 = (size_t)n2 * H;
     double *b1 = (double *)malloc(N1 * sizeof(double)), *b2 = (double *)malloc(N2 * sizeof(double));
@@ -980,8 +987,14 @@ double orc_rmplus(const orc_game *g, int iters, const double *beh1_0, const doub
     orc_seqform(g, 0, b1, x);
     orc_seqform(g, 1, b2, y);
     const double th1 = orc_regret_floor(g, 0, ORC_REGRET_EPS), th2 = orc_regret_floor(g, 1, ORC_REGRET_EPS);
-    double wsum = 0.0, expl = 0.0;
-    for (int t = 1; t <= iters; t++) {
+    /* warm start: regrets proportional to the initial strategy, which then
+     * counts as played for iterations 1..t0 in the linear average */
+    const double r1 = kappa * orc_regret_floor(g, 0, 1.0), r2 = kappa * orc_regret_floor(g, 1, 1.0);
+    const double w0 = 0.5 * (double)t0 * (double)(t0 + 1);
+    for (size_t i = 0; i < N1; i++) { R1[i] = r1 * b1[i]; xs[i] = w0 * x[i]; }
+    for (size_t i = 0; i < N2; i++) { R2[i] = r2 * b2[i]; ys[i] = w0 * y[i]; }
+    double wsum = w0, expl = 0.0;
+    for (int t = t0 + 1; t <= t0 + iters; t++) {
         /* player 1: accumulate the strategy played, then update against y */
         for (size_t i = 0; i < N1; i++) xs[i] += t * x[i];
         matvec_one(g, y, g1);
@@ -997,11 +1010,11 @@ double orc_rmplus(const orc_game *g, int iters, const double *beh1_0, const doub
         orc_seqform(g, 1, b2, y);
         wsum += t;
         if (trace) {
-            trace[t - 1] = 0.0;
-            if (trace_every > 0 && t % trace_every == 0) {
+            trace[t - t0 - 1] = 0.0;
+            if (trace_every > 0 && (t - t0) % trace_every == 0) {
                 for (size_t i = 0; i < N1; i++) xa[i] = xs[i] / wsum;
                 for (size_t i = 0; i < N2; i++) ya[i] = ys[i] / wsum;
-                trace[t - 1] = orc_exploitability(g, xa, ya, NULL, NULL);
+                trace[t - t0 - 1] = orc_exploitability(g, xa, ya, NULL, NULL);
             }
         }
     }

@@ -134,6 +134,15 @@ double orc_rmplus(const orc_game *g, int iters, const double *beh1_0,
                   const double *beh2_0, double *avg_beh1, double *avg_beh2,
                   double *trace, int trace_every);
 
+/* The same loop started warm: regrets R_p = kappa * V_p * b_p (V_p =
+ * orc_regret_floor(g, p, 1.0), so regret matching returns b_p), the initial
+ * strategy counted as played at iterations 1..t0 (weight t0 (t0 + 1) / 2 in
+ * the linear average), then iterations t0 + 1 .. t0 + iters.  kappa = 0,
+ * t0 = 0 is orc_rmplus.  trace[k] belongs to iteration t0 + k + 1. */
+double orc_rmplus_warm(const orc_game *g, int iters, const double *beh1_0, const double *beh2_0,
+                       double kappa, int t0, double *avg_beh1, double *avg_beh2, double *trace,
+                       int trace_every);
+
 /* Best-response values: br1 = max_x x^T A y, br2 = max_y -x^T A y for
  * sequence-form x [n1][H], y [n2][H].  Returns (br1 + br2)/2/pot0. */
 double orc_exploitability(const orc_game *g, const double *x, const double *y,

@@ -63,6 +63,8 @@ def lib():
         L.orc_beta.restype = C.c_double
         L.orc_regret_floor.argtypes = [P, C.c_int, C.c_double]
         L.orc_regret_floor.restype = C.c_double
+        L.orc_rmplus_warm.argtypes = [P, C.c_int, P, P, C.c_double, C.c_int, P, P, P, C.c_int]
+        L.orc_rmplus_warm.restype = C.c_double
         L.orc_beta.argtypes = [P]
         L.orc_pot0.restype = C.c_double
         L.orc_pot0.argtypes = [P]
@@ -227,6 +229,17 @@ class OracleGame:
         b1 = None if beh1 is None else np.ascontiguousarray(beh1, dtype=np.float64)
         b2 = None if beh2 is None else np.ascontiguousarray(beh2, dtype=np.float64)
         e = lib().orc_rmplus(self._g, iters, _p(b1), _p(b2), _p(avg1), _p(avg2), _p(trace), trace_every)
+        return e, avg1, avg2, trace[:iters]
+
+    def rmplus_warm(self, iters: int, beh1, beh2, kappa: float, t0: int, trace_every: int = 0):
+        """RM+ started warm (see orc_rmplus_warm)."""
+        avg1 = np.zeros((self.n1, self.H))
+        avg2 = np.zeros((self.n2, self.H))
+        trace = np.zeros(max(iters, 1))
+        b1 = None if beh1 is None else np.ascontiguousarray(beh1, dtype=np.float64)
+        b2 = None if beh2 is None else np.ascontiguousarray(beh2, dtype=np.float64)
+        e = lib().orc_rmplus_warm(self._g, iters, _p(b1), _p(b2), kappa, t0, _p(avg1), _p(avg2), _p(trace),
+                                  trace_every)
         return e, avg1, avg2, trace[:iters]
 
     def exploitability(self, x: np.ndarray, y: np.ndarray):

@@ -243,3 +243,35 @@ def test_regret_floor_kuhn_by_hand():
     assert og.regret_floor(0, 1.0) == pytest.approx(1.0, rel=1e-15)
     assert og.regret_floor(1, 1.0) == pytest.approx(1.0, rel=1e-15)
     assert og.regret_floor(0, 2.0 ** -40) == pytest.approx(2.0 ** -40, rel=1e-15)
+
+
+def _kuhn_equilibrium():
+    """The equilibrium of Kuhn poker with alpha = 0 (closed form): player 1
+    always checks, folds J and calls K facing a bet, calls with Q 1/3;
+    player 2 bets K and bluffs J 1/3 after a check, calls K and Q 1/3."""
+    b1 = np.array([[1, 1, 1], [0, 0, 0], [1, 2 / 3, 0], [0, 1 / 3, 1]], dtype=float)
+    b2 = np.array([[2 / 3, 1, 0], [1 / 3, 0, 1], [1, 2 / 3, 0], [0, 1 / 3, 1]], dtype=float)
+    return b1, b2
+
+
+def test_kuhn_equilibrium_is_a_fixed_point_of_warm_rmplus():
+    """Warm start at an equilibrium: regrets kappa V b (regret matching gives
+    b back) stay proportional to b because the supported actions are
+    indifferent, so the iterates and the average stay at the equilibrium;
+    a cold start is far from it after the same iterations.  With kappa = 0
+    and a large t0 the average is dominated by the initial strategy."""
+    g = _kuhn()
+    b1, b2 = _kuhn_equilibrium()
+    e0, _, _ = g.exploitability(g.seqform(0, b1), g.seqform(1, b2))
+    assert abs(e0) < 1e-14
+    e_warm, a1, a2, _ = g.rmplus_warm(10, b1, b2, kappa=1.0, t0=50)
+    assert e_warm < 1e-12
+    assert np.max(np.abs(a1 - b1)) < 1e-9 and np.max(np.abs(a2 - b2)) < 1e-9
+    e_cold, _, _, _ = g.rmplus(10)
+    assert e_cold > 1e-2
+    e_avg, _, _, _ = g.rmplus_warm(10, b1, b2, kappa=0.0, t0=1_000_000)
+    assert e_avg < 1e-3
+    # kappa = 0, t0 = 0 is plain RM+ from the given strategy
+    e1, c1, c2, _ = g.rmplus_warm(7, b1, b2, kappa=0.0, t0=0)
+    e2, d1, d2, _ = g.rmplus(7, b1, b2)
+    assert e1 == e2 and np.array_equal(c1, d1) and np.array_equal(c2, d2)
