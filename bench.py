@@ -44,7 +44,7 @@ def _args():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--workload", default="matvec", choices=["matvec", "batch", "solver"],
+    ap.add_argument("--workload", default="matvec", choices=["matvec", "batch", "solver", "warmstart"],
                     help="matvec: the headline line; batch / solver: print only that measurement")
     ap.add_argument("--games", type=int, default=4096, help="games of the batched workload")
     ap.add_argument("--no-secondary", action="store_true",
@@ -385,6 +385,52 @@ def measure_solver(target: float = 1e-3, block: int = 25, max_iters: int = 4000)
             "target_expl_pot": target, "check_every": block, "by_storage": res}
 
 
+def measure_warmstart(train_games: int = 20480, per_game: int = 64, heldout: int = 512, epochs: int = 12,
+                      kappa: float = 0.02, t0: int = 0):
+    """Learned warm start: equilibria of `train_games` river endgames (the
+    1081-hand generator, solved by the batched FP32 solver to 1e-3 of the
+    pot, 4096 per batch), `per_game` sampled (node, hand) queries each, the
+    network trained by its own kernels; then iterations and wall time to
+    1e-3 of the pot on `heldout` other endgames: FP32 cold start against
+    warm starts in FP32 and in BF16 storage (inference included)."""
+    import torch
+    from paper_2112_03804_gb300 import kps, synth, warmstart as W
+
+    def batch(seed, n):
+        r = np.random.default_rng(seed)
+        games = [kps.Game(synth.river_spec(seed=int(s))) for s in r.integers(1 << 62, size=n)]
+        return kps.Batch(games)
+
+    t_start = time.perf_counter()
+    data, solve_s, iters = [], 0.0, []
+    for i in range(0, train_games, 4096):
+        b = batch(1000 + i, min(4096, train_games - i))
+        s, it, ex, sec = W.solve(b, kps.F32, 1e-3, block=25, max_iters=2000)
+        solve_s += sec
+        iters.append(it)
+        data.append(W.sample(b, s, per_game, seed=i))
+        del s, b
+        torch.cuda.empty_cache()
+    D = W.concat(data)
+    rows = int(D["X"].shape[0])
+    mlp = kps.MLP(seed=1)
+    t_train = time.perf_counter()
+    hist = W.train(mlp, D, epochs=epochs, rows=8192, lr=1e-3, lr_decay=0.8)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t_train
+    del D, data
+    torch.cuda.empty_cache()
+    hb = batch(5555, heldout)
+    res = {}
+    for name, dt in (("f32", kps.F32), ("bf16", kps.BF16)):
+        res[name] = W.compare(mlp, hb, dt, 1e-3, kappa, t0, block=25, max_iters=2000)
+    return {"train_games": train_games, "train_rows": rows, "train_solve_seconds": solve_s,
+            "train_solve_iterations": iters, "train_seconds": train_s, "epochs": epochs,
+            "loss_first_last": [hist[0], hist[-1]], "heldout_games": heldout, "kappa": kappa, "t0": t0,
+            "cold_f32": res["f32"]["cold"], "warm_f32": res["f32"]["warm"], "warm_bf16": res["bf16"]["warm"],
+            "cold_bf16": res["bf16"]["cold"], "total_seconds": time.perf_counter() - t_start}
+
+
 def _e2e(g, y, x, oy, ox, stream, args, world):
     import torch
     from paper_2112_03804_gb300 import kps
@@ -453,6 +499,10 @@ def main():
         import torch
         torch.cuda.set_device(_dist()[2])
         print(json.dumps(measure_batch(args.games, args.steps, args.warmup)), flush=True)
+    elif args.workload == "warmstart":
+        import torch
+        torch.cuda.set_device(_dist()[2])
+        print(json.dumps(measure_warmstart()), flush=True)
     elif args.workload == "solver":
         import torch
         torch.cuda.set_device(_dist()[2])

@@ -241,6 +241,16 @@ kps_status kps_solver_destroy(kps_solver *solver);
  * layouts: entry [sigma][h] = probability of sigma's last action at its
  * node), or uniform strategies if both are NULL. */
 kps_status kps_solver_reset(kps_solver *solver, const float *beh1, const float *beh2, void *stream);
+/* Warm start (not in the paper; the learned warm start of this library):
+ * like kps_solver_reset, and in addition the regrets start at
+ * kappa * V_p * beh_p (V_p = max|payoff| * max mu_p * sum mu_q / beta, a
+ * bound on player p's counterfactual values; regret matching then returns
+ * beh_p) and the initial strategies count as played at iterations 1..t0 of
+ * the linear average; the next iteration is t0 + 1.  kappa = 0, t0 = 0 is
+ * kps_solver_reset.  Errors: KPS_EINVAL (kappa < 0, t0 < 0, one of beh1 /
+ * beh2 NULL). */
+kps_status kps_solver_warm_start(kps_solver *solver, const float *beh1, const float *beh2, double kappa,
+                                 int32_t t0, void *stream);
 /* Runs `iters` iterations as one CUDA graph (captured on first use of each
  * count), asynchronous on `stream`. */
 kps_status kps_solver_step(kps_solver *solver, int32_t iters, void *stream);
@@ -259,6 +269,74 @@ kps_status kps_solver_strategy(kps_solver *solver, void *x, void *y, void *strea
  * and the best-response values BR1, BR2 (may be NULL).  FP64 products and
  * best responses.  Asynchronous on `stream`. */
 kps_status kps_solver_exploitability(kps_solver *solver, double *expl, double *br1, double *br2, void *stream);
+
+/* ---- Learned warm start ----------------------------------------------------
+ * Not in the paper.  A 3-layer perceptron (BF16 weights, FP32 master copy,
+ * activations and accumulation) maps a query (game, player, decision node,
+ * hand) of a batch to a behavioural strategy at that node; a solver started
+ * from its predictions (kps_solver_warm_start) needs fewer iterations.
+ * Queries of a batch are numbered game by game, player 1's nodes then
+ * player 2's, hands in library order within a node. */
+#define KPS_WARM_DIN 1232   /* feature row length                            */
+#define KPS_WARM_DOUT 12    /* outputs per row: actions of a node (masked)   */
+
+/* Number of queries of the batch (builds its feature tables on first use).
+ * KPS_ENOTSUP if a player has more than 32 decision nodes. */
+kps_status kps_warm_num_queries(kps_batch *batch, int64_t *n);
+/* Feature rows X [nq][KPS_WARM_DIN] (device FP32) and action counts nact
+ * [nq] (device, may be NULL) of queries qidx[0..nq) (device int64), or of
+ * q0 .. q0+nq-1 when qidx is NULL.  Row layout: board one-hot (52), the
+ * opponent's belief mass over 1081 strength bins, node one-hot / player /
+ * actions / depth (40), hand strength position / tie size / own belief /
+ * card two-hot (56), padding (3). */
+kps_status kps_warm_features(kps_batch *batch, const int64_t *qidx, int64_t q0, int32_t nq, float *X,
+                             int32_t *nact, void *stream);
+/* Training targets from a solver's FP64 average strategies (batch layouts,
+ * kps_solver_average): T [nq][KPS_WARM_DOUT] the behavioural strategy at
+ * the query's node, w [nq] = reach of the node's parent sequence in the
+ * sequence-form average x1/x2 (1 at a root; 1 everywhere if x1/x2 are NULL)
+ * times the hand's normalised belief. */
+kps_status kps_warm_targets(kps_batch *batch, const double *beh1, const double *beh2, const double *x1,
+                            const double *x2, const int64_t *qidx, int64_t q0, int32_t nq, float *T, float *w,
+                            void *stream);
+/* Writes predictions P [nq][KPS_WARM_DOUT] into behavioural strategies
+ * beh1 / beh2 (device FP32, batch layouts) at the queries' nodes and hands. */
+kps_status kps_warm_scatter(kps_batch *batch, const float *P, const int64_t *qidx, int64_t q0, int32_t nq,
+                            float *beh1, float *beh2, void *stream);
+
+typedef struct kps_mlp kps_mlp;
+
+/* The network's behavioural strategy at EVERY query of the batch, written
+ * into beh1 / beh2 (device FP32, batch layouts) in one fused pass: the first
+ * layer from its game, node and hand parts (the game and node parts computed
+ * once per game / node), layers 2 and 3 on the tensor cores with BF16
+ * activations, the masked softmax, the scatter.  Needs din = KPS_WARM_DIN,
+ * width 256, dout <= 16 (KPS_ENOTSUP otherwise).  Allocates temporaries and
+ * synchronises `stream`.  Agrees with kps_warm_features + kps_mlp_forward +
+ * kps_warm_scatter up to the BF16 rounding of the activations. */
+kps_status kps_warm_predict(kps_batch *batch, kps_mlp *mlp, float *beh1, float *beh2, void *stream);
+/* Layers din -> width -> width -> dout (dout <= 32), ReLU, He-normal
+ * weights from `seed`, zero biases. */
+kps_status kps_mlp_create(int32_t din, int32_t width, int32_t dout, uint64_t seed, kps_mlp **out);
+kps_status kps_mlp_destroy(kps_mlp *mlp);
+/* Parameter count: W1 [din][width], b1, W2 [width][width], b2,
+ * W3 [width][dout], b3, in this order in every flat array below. */
+kps_status kps_mlp_num_params(const kps_mlp *mlp, int64_t *n);
+/* Host copy of the FP32 parameters (which = 0) or of the last gradients
+ * (which = 1); kps_mlp_set writes the parameters (and their BF16 copy). */
+kps_status kps_mlp_get(const kps_mlp *mlp, int32_t which, float *host);
+kps_status kps_mlp_set(kps_mlp *mlp, const float *host);
+/* P [rows][dout] = softmax over the first nact[r] outputs of row r
+ * (device).  Products read the BF16 weights, accumulate in FP32. */
+kps_status kps_mlp_forward(kps_mlp *mlp, const float *X, int32_t rows, const int32_t *nact, float *P,
+                           void *stream);
+/* Gradients of L = -sum_r w_r sum_{a < nact_r} T[r][a] log P[r][a] / wsum
+ * into the network's gradient buffer; *loss (device float, may be NULL)
+ * receives L. */
+kps_status kps_mlp_gradients(kps_mlp *mlp, const float *X, int32_t rows, const int32_t *nact, const float *T,
+                             const float *w, float wsum, float *loss, void *stream);
+/* One Adam step with the last gradients (FP32 master weights, then BF16). */
+kps_status kps_mlp_adam(kps_mlp *mlp, float lr, float beta1, float beta2, float eps, void *stream);
 
 /* A * y for BF16 or FP16 vectors without any device allocation.  The paper
  * has no counterpart: this is a service for callers that must not allocate

@@ -250,6 +250,7 @@ kps_status kps_batch_create(kps_game *const *games, int32_t n, kps_batch **out) 
 kps_status kps_batch_destroy(kps_batch *b) {
     if (!b) return KPS_OK;
     for (auto &kv : b->tables) cudaFree(kv.second.blob);
+    warm_free(b);
     if (b->ticket) cudaFree(b->ticket);
     delete b;
     return KPS_OK;

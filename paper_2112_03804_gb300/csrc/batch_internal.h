@@ -37,6 +37,7 @@ struct kps_batch {
     int *ticket = nullptr;           // tile ticket counter (device)
     std::map<std::tuple<int, bool, int>, kps_abi::BatchTable> tables;
     std::map<int, kps_abi::BatchShape> shape;   // per dtype
+    void *warm = nullptr;            // warm-start feature tables (warm.cu)
 };
 
 namespace kps_abi {
@@ -45,5 +46,7 @@ kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t str
 kps_status batch_default_shape(kps_batch *b, kps_dtype dt, cudaStream_t stream, BatchShape *out);
 // dir 0: out = A y per game (y player-2 layout, out player-1 layout); dir 1: A^T.
 kps_status batch_matvec(kps_batch *b, int dir, const void *vin, void *vout, kps_dtype dt, cudaStream_t stream);
+// Frees the warm-start tables of the batch (warm.cu).
+void warm_free(kps_batch *b);
 
 }  // namespace kps_abi

@@ -62,6 +62,7 @@ struct SolverGame {
     long long off[2];
     int block0;       // first block of the game
     double pot0;
+    double V[2];      // bound on each player's counterfactual values
     double theta[2];  // regret-matching noise floor of each player
 };
 
@@ -120,7 +121,9 @@ struct UpdateArgs {
     C *xsum;                 // sum over iterations of t * x
     const float *beh0;       // initial behavioural strategy
     const long long *iter;   // completed iterations
-    const int *has_init;
+    const long long *init_iter;  // the iteration that plays beh0 (0 = none)
+    C kappa;                 // warm start: regrets kappa * V_p * beh0
+    C w0;                    // warm start: weight of the initial strategy in the average
 };
 
 // One RM+ half-iteration of one player (see the file comment).
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S,
     const int p = u.player, n = G.n[p], hs = G.hs, tid = threadIdx.x;
     const long long base = G.off[p] + w.h;
     const long long t = *u.iter + 1;
-    const bool init = *u.has_init != 0 && t == 1;
+    const bool init = t == *u.init_iter;
     const int4 *nodes = u.nodes + G.node_off[p];
     const int nn = G.nnodes[p];
     const C theta = C(G.theta[p]);
@@ -194,9 +197,11 @@ __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S,
     }
 }
 
-// x <- sequence form of the initial behavioural strategy (uniform if none).
+// Start of a run: x <- sequence form of the initial behavioural strategy
+// beh0 (uniform if none); with a warm start also R <- kappa V_p beh0 (so that
+// regret matching returns beh0) and xsum <- w0 x.
 template <typename S, typename C>
-__global__ void __launch_bounds__(kThreads) seqform_kernel(const UpdateArgs<S, C> u) {
+__global__ void __launch_bounds__(kThreads) seqform_kernel(const UpdateArgs<S, C> u, int has_beh) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     const Where w = locate(u.games, u.block_game);
@@ -204,17 +209,19 @@ __global__ void __launch_bounds__(kThreads) seqform_kernel(const UpdateArgs<S, C
     if (w.h >= G.H) return;
     const int p = u.player, hs = G.hs, tid = threadIdx.x;
     const long long base = G.off[p] + w.h;
-    const bool init = *u.has_init != 0;
     const int4 *nodes = u.nodes + G.node_off[p];
+    const C rscale = u.kappa * C(G.V[p]);
     for (int k = 0; k < G.nnodes[p]; ++k) {
         const int4 nd = nodes[k];
         const int s0 = nd.x, na = nd.y, par = nd.z;
         const C xp = par >= 0 ? buf[par * kThreads + tid] : C(1);
         for (int a = 0; a < na; ++a) {
             const long long i = base + (long long)(s0 + a) * hs;
-            const C b = init ? C(u.beh0[i]) : C(1) / C(na);
+            const C b = has_beh ? C(u.beh0[i]) : C(1) / C(na);
             buf[(s0 + a) * kThreads + tid] = xp * b;
             u.x[i] = Cv<S>::st(xp * b);
+            u.regret[i] = rscale * b;
+            u.xsum[i] = u.w0 * C(Cv<S>::ld(u.x + i));
         }
     }
 }
@@ -327,8 +334,10 @@ struct kps_solver {
     float *beh0[2] = {nullptr, nullptr};
     double *xa[2] = {nullptr, nullptr}, *g64[2] = {nullptr, nullptr};
     double *partial[2] = {nullptr, nullptr};
-    long long *iter = nullptr;      // [0] iterations, then has_init as int
-    int *has_init = nullptr;
+    long long *iter = nullptr;      // completed iterations (device)
+    long long *init_iter = nullptr; // iteration that plays the initial strategy (device)
+    int has_beh = 0;
+    double kappa = 0.0, w0 = 0.0;
     long long iters_host = 0;
     cudaStream_t cap = nullptr;     // capture stream
     std::map<int, cudaGraphExec_t> graphs;
@@ -354,7 +363,9 @@ UpdateArgs<S, C> make_args(kps_solver *s, int p) {
     u.xsum = static_cast<C *>(s->xsum[p]);
     u.beh0 = s->beh0[p];
     u.iter = s->iter;
-    u.has_init = s->has_init;
+    u.init_iter = s->init_iter;
+    u.kappa = C(s->kappa);
+    u.w0 = C(s->w0);
     return u;
 }
 
@@ -388,7 +399,10 @@ cudaError_t update_t(kps_solver *s, int p, cudaStream_t st) {
 template <typename S, typename C>
 cudaError_t seqform_t(kps_solver *s, int p, cudaStream_t st) {
     const size_t smem = (size_t)s->nmax * kThreads * sizeof(C);
-    return launch_node_kernel(s, seqform_kernel<S, C>, make_args<S, C>(s, p), smem, st);
+    cudaError_t e = smem_limit(reinterpret_cast<const void *>(seqform_kernel<S, C>), smem);
+    if (e != cudaSuccess) return e;
+    seqform_kernel<S, C><<<s->nblocks, kThreads, smem, st>>>(make_args<S, C>(s, p), s->has_beh);
+    return cudaGetLastError();
 }
 
 template <typename S, typename C>
@@ -462,7 +476,8 @@ kps_status kps_solver_create(kps_batch *b, kps_dtype dt, kps_solver **out) {
                 double mmax = 0.0, msum = 0.0;
                 for (double v : mp) mmax = std::max(mmax, v);
                 for (double v : mq) msum += v;
-                G.theta[p] = eps * cmax * mmax * msum / h.beta;
+                G.V[p] = cmax * mmax * msum / h.beta;
+                G.theta[p] = eps * G.V[p];
             }
         }
         const int nb = (h.H + kThreads - 1) / kThreads;
@@ -517,7 +532,7 @@ kps_status kps_solver_create(kps_batch *b, kps_dtype dt, kps_solver **out) {
     s->game_blocks = reinterpret_cast<int *>(bl + o_gb);
     s->nodes = reinterpret_cast<int4 *>(bl + o_nd);
     s->iter = reinterpret_cast<long long *>(bl + o_it);
-    s->has_init = reinterpret_cast<int *>(bl + o_it + 8);
+    s->init_iter = reinterpret_cast<long long *>(bl + o_it + 8);
     const size_t es = elem_size(dt);
     for (int p = 0; p < 2; ++p) {
         const size_t len = (size_t)b->off[p].back();
@@ -560,29 +575,39 @@ kps_status kps_solver_destroy(kps_solver *s) {
     return KPS_OK;
 }
 
-kps_status kps_solver_reset(kps_solver *s, const float *beh1, const float *beh2, void *stream_ptr) {
+kps_status kps_solver_warm_start(kps_solver *s, const float *beh1, const float *beh2, double kappa, int32_t t0,
+                                 void *stream_ptr) {
     if (!s) return fail(KPS_EINVAL, "solver is NULL");
     if ((beh1 == nullptr) != (beh2 == nullptr)) return fail(KPS_EINVAL, "give both initial strategies or neither");
+    if (!(kappa >= 0.0) || t0 < 0) return fail(KPS_EINVAL, "kappa and t0 must be >= 0");
     cudaStream_t st = static_cast<cudaStream_t>(stream_ptr);
-    const size_t es = elem_size(s->dt), csz = compute_size(s->dt);
-    const int init = beh1 ? 1 : 0;
+    const size_t es = elem_size(s->dt);
+    s->has_beh = beh1 ? 1 : 0;
+    s->kappa = kappa;
+    s->w0 = 0.5 * (double)t0 * (double)(t0 + 1);
+    const long long iter0 = t0, init_iter = beh1 ? (long long)t0 + 1 : 0;
     cudaError_t e = cudaSuccess;
     for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
         const size_t len = (size_t)s->batch->off[p].back();
-        e = cudaMemsetAsync(s->regret[p], 0, len * csz, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(s->xsum[p], 0, len * csz, st);
+        // padding entries stay zero; the start kernel writes every hand entry
+        e = cudaMemsetAsync(s->regret[p], 0, len * compute_size(s->dt), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->xsum[p], 0, len * compute_size(s->dt), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(s->x[p], 0, len * es, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(s->g[p], 0, len * es, st);
-        if (e == cudaSuccess && init)
+        if (e == cudaSuccess && beh1)
             e = cudaMemcpyAsync(s->beh0[p], p == 0 ? beh1 : beh2, len * 4, cudaMemcpyDeviceToDevice, st);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->iter, 0, 8, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->has_init, init ? 0x01 : 0x00, 1, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(reinterpret_cast<char *>(s->has_init) + 1, 0, 3, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->iter, &iter0, 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->init_iter, &init_iter, 8, cudaMemcpyHostToDevice, st);
+    // the pageable copies above are staged before they return
     for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = KPS_DISPATCH(s->dt, seqform_t, s, p, st);
-    if (e != cudaSuccess) return cuda_fail(e, "resetting the solver");
-    s->iters_host = 0;
+    if (e != cudaSuccess) return cuda_fail(e, "starting the solver");
+    s->iters_host = t0;
     return KPS_OK;
+}
+
+kps_status kps_solver_reset(kps_solver *s, const float *beh1, const float *beh2, void *stream_ptr) {
+    return kps_solver_warm_start(s, beh1, beh2, 0.0, 0, stream_ptr);
 }
 
 kps_status kps_solver_step(kps_solver *s, int32_t iters, void *stream_ptr) {

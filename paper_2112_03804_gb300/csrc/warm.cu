@@ -1,0 +1,615 @@
+// Inputs and outputs of the warm-start network for the games of a batch.
+//
+// A query is (game, player p, decision node k of p, hand h); the queries of
+// a batch are enumerated game by game, then player 1's nodes, then player
+// 2's, then hands in library order.  Its feature row (KPS_WARM_DIN floats):
+//   [0, 52)       board one-hot (card ids)
+//   [52, 1133)    1081-bin strength histogram of the opponent's range: bin
+//                 floor(pos * 1081 / H) of the opponent hand at strength
+//                 position pos gets mu_q(pos) / sum mu_q
+//   [1133, 1173)  node: one-hot of k (first 32 nodes), player, actions / 12,
+//                 depth (player-p ancestors) / 8
+//   [1173, 1229)  hand: strength position / (H - 1), tie-group size / 32,
+//                 mu_p(h) * H / sum mu_p, 0, two-hot of the hand's cards
+//   [1229, 1232)  zero
+// Targets are a solver's average behavioural strategy at (k, h) and the
+// weight reach_p(parent sequence) * mu_p(h) * H / sum mu_p; predictions are
+// scattered back into behavioural strategies in the batch layout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "abi_internal.h"
+#include "batch_internal.h"
+#include "mlp_internal.h"
+
+#include <cuda_bf16.h>
+
+using namespace kps_abi;
+
+namespace {
+
+constexpr int kDin = KPS_WARM_DIN, kDout = KPS_WARM_DOUT;
+// board at offset 0; node features are 40 wide
+constexpr int kOffHist = 52, kOffNode = 1133, kOffHand = 1173;
+constexpr int kHist = 1081, kHandF = 56;
+static_assert(kOffHand + kHandF + 3 == kDin, "feature row layout");
+
+struct WarmGame {
+    int H, hs;
+    long long qstart;          // first query of the game
+    int nodes[2];
+    int node_off[2];           // into the node arrays
+    long long hist_off[2];     // into the histogram array
+    long long hand_off;        // into the per-hand arrays
+    long long voff[2];         // batch vector offsets
+    unsigned long long board_lo; // board cards as a 64-bit mask
+};
+
+struct WarmDev {
+    const WarmGame *games;
+    const long long *qstart;   // [ngames + 1]
+    int ngames;
+    const float *hist;         // [game][player][1081]
+    const int4 *node;          // {first sequence, actions, parent sequence, depth}
+    const int2 *cards;         // per hand: card ids (b = -1 for one-card hands)
+    const float *hand;         // per hand: {pos/(H-1), tie/32, mu1 norm, mu2 norm}
+    const float *node_feat;    // per node: its 40 node features
+    int total_nodes;
+};
+
+struct Query {
+    int game, player, node, hand;
+};
+
+__device__ __forceinline__ Query decode(const WarmDev &d, long long q) {
+    int lo = 0, hi = d.ngames - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d.qstart[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    const WarmGame &G = d.games[lo];
+    long long r = q - G.qstart;
+    Query Q;
+    Q.game = lo;
+    const long long n1 = (long long)G.nodes[0] * G.H;
+    Q.player = r < n1 ? 0 : 1;
+    if (Q.player) r -= n1;
+    Q.node = (int)(r / G.H);
+    Q.hand = (int)(r % G.H);
+    return Q;
+}
+
+// One block per row: thread 0 decodes the query, the block writes the row.
+__global__ void __launch_bounds__(256) features_kernel(const WarmDev d, const long long *qidx, long long q0,
+                                                         float *X, int *nact) {
+    __shared__ Query sq;
+    const long long row = blockIdx.x;
+    if (threadIdx.x == 0) sq = decode(d, qidx ? qidx[row] : q0 + row);
+    __syncthreads();
+    const Query Q = sq;
+    const WarmGame &G = d.games[Q.game];
+    const int4 nd = d.node[G.node_off[Q.player] + Q.node];
+    const int2 cd = d.cards[G.hand_off + Q.hand];
+    const float4 hf = reinterpret_cast<const float4 *>(d.hand)[G.hand_off + Q.hand];
+    const float *hist = d.hist + G.hist_off[Q.player];
+    float *x = X + row * kDin;
+    for (int j = threadIdx.x; j < kDin; j += blockDim.x) {
+        float v = 0.f;
+        if (j < kOffHist) {
+            v = (G.board_lo >> j) & 1ull ? 1.f : 0.f;
+        } else if (j < kOffNode) {
+            v = hist[j - kOffHist];
+        } else if (j < kOffHand) {
+            const int f = j - kOffNode;
+            if (f < 32) v = f == Q.node ? 1.f : 0.f;
+            else if (f == 32) v = (float)Q.player;
+            else if (f == 33) v = nd.y / 12.f;
+            else if (f == 34) v = nd.w / 8.f;
+        } else if (j < kOffHand + kHandF) {
+            const int f = j - kOffHand;
+            if (f == 0) v = hf.x;
+            else if (f == 1) v = hf.y;
+            else if (f == 2) v = Q.player == 0 ? hf.z : hf.w;
+            else if (f >= 4) v = (f - 4 == cd.x || f - 4 == cd.y) ? 1.f : 0.f;
+        }
+        x[j] = v;
+    }
+    if (threadIdx.x == 0 && nact) nact[row] = nd.y;
+}
+
+__global__ void targets_kernel(const WarmDev d, const double *beh1, const double *beh2, const double *x1,
+                               const double *x2, const long long *qidx, long long q0, int nq, float *T, float *w) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= nq) return;
+    const Query Q = decode(d, qidx ? qidx[row] : q0 + row);
+    const WarmGame &G = d.games[Q.game];
+    const int4 nd = d.node[G.node_off[Q.player] + Q.node];
+    const double *beh = Q.player == 0 ? beh1 : beh2;
+    const double *xs = Q.player == 0 ? x1 : x2;
+    const long long base = G.voff[Q.player] + Q.hand;
+    for (int a = 0; a < kDout; ++a)
+        T[(long long)row * kDout + a] = a < nd.y ? (float)beh[base + (long long)(nd.x + a) * G.hs] : 0.f;
+    const float4 hf = reinterpret_cast<const float4 *>(d.hand)[G.hand_off + Q.hand];
+    const double reach = (xs && nd.z >= 0) ? xs[base + (long long)nd.z * G.hs] : 1.0;
+    w[row] = (float)reach * (Q.player == 0 ? hf.z : hf.w);
+}
+
+__global__ void scatter_kernel(const WarmDev d, const float *P, const long long *qidx, long long q0, int nq,
+                               float *beh1, float *beh2) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= nq) return;
+    const Query Q = decode(d, qidx ? qidx[row] : q0 + row);
+    const WarmGame &G = d.games[Q.game];
+    const int4 nd = d.node[G.node_off[Q.player] + Q.node];
+    float *beh = Q.player == 0 ? beh1 : beh2;
+    const long long base = G.voff[Q.player] + Q.hand;
+    for (int a = 0; a < nd.y; ++a) beh[base + (long long)(nd.x + a) * G.hs] = P[(long long)row * kDout + a];
+}
+
+// Game part of the feature rows, one row per (game, player): board one-hot
+// and the opponent's strength histogram (feature columns [0, 1133)).
+__global__ void game_part_kernel(const WarmDev d, float *Gf) {
+    const int r = blockIdx.x, g = r >> 1, p = r & 1;
+    const WarmGame &G = d.games[g];
+    const float *hist = d.hist + G.hist_off[p];
+    float *x = Gf + (long long)r * kOffNode;
+    for (int j = threadIdx.x; j < kOffNode; j += blockDim.x)
+        x[j] = j < kOffHist ? ((G.board_lo >> j) & 1ull ? 1.f : 0.f) : hist[j - kOffHist];
+}
+
+// ---- fused inference ---------------------------------------------------
+// Layer 1 from its three parts (game and node parts precomputed, the hand
+// part from five rows of W1), layers 2 and 3 on the tensor cores
+// (mma.sync m16n8k16, BF16 operands, FP32 accumulation) with W2^T and W3^T
+// resident in shared memory, activations in shared memory as BF16, then the
+// masked softmax, written straight into the behavioural strategies.
+constexpr int kPR = 128;            // queries per tile (8 warps x 16 rows)
+constexpr int kWidth = 256;
+constexpr int kPitchH = kWidth + 8; // BF16 elements per shared row (conflict-free fragments)
+
+struct RowInfo {
+    long long base;                  // batch-vector offset of (player, hand)
+    int gp, node, ca, cb, nact, s0, hs, player;
+    float pos, tie, mu;
+};
+
+__host__ __device__ constexpr size_t predict_smem_bytes() {
+    return (size_t)(kWidth + kPR + 16) * kPitchH * 2 + kPR * sizeof(RowInfo);
+}
+
+__device__ __forceinline__ void mma_bf16(float *d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+__device__ __forceinline__ void st_pair(__nv_bfloat16 *p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+}
+
+struct PredictArgs {
+    WarmDev d;
+    const float *G1;                 // [2 ngames][256]
+    const float *N1;                 // [total nodes][256]
+    const __nv_bfloat16 *W1h;        // rows 1173.. of W1: [59][256]
+    const float *b1, *b2, *b3;
+    const __nv_bfloat16 *W2;         // [256][256]
+    const __nv_bfloat16 *W3;         // [256][dout]
+    int dout;
+    long long nq;
+    float *beh1, *beh2;
+};
+
+__global__ void __launch_bounds__(256, 1) predict_kernel(const PredictArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __nv_bfloat16 *W2t = reinterpret_cast<__nv_bfloat16 *>(smem_raw);        // [n][k]
+    __nv_bfloat16 *Hs = W2t + (size_t)kWidth * kPitchH;                       // [row][k]
+    __nv_bfloat16 *W3t = Hs + (size_t)kPR * kPitchH;                          // [n < 16][k]
+    RowInfo *rows = reinterpret_cast<RowInfo *>(W3t + (size_t)16 * kPitchH);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    for (int i = tid; i < kWidth * kWidth; i += blockDim.x) {
+        const int k = i / kWidth, n = i % kWidth;
+        W2t[n * kPitchH + k] = a.W2[i];
+    }
+    for (int i = tid; i < kWidth * 16; i += blockDim.x) {
+        const int k = i / 16, n = i % 16;
+        W3t[n * kPitchH + k] = n < a.dout ? a.W3[k * a.dout + n] : __float2bfloat16_rn(0.f);
+    }
+    // this thread's column of the hand part of layer 1
+    const int j = tid;
+    const float wpos = __bfloat162float(a.W1h[0 * kWidth + j]), wtie = __bfloat162float(a.W1h[1 * kWidth + j]),
+                wmu = __bfloat162float(a.W1h[2 * kWidth + j]), bias1 = a.b1[j];
+    const __nv_bfloat16 *Wc = a.W1h + 4 * kWidth;
+    __syncthreads();
+    const long long ntiles = (a.nq + kPR - 1) / kPR;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (tid < kPR) {
+            const long long q = tile * kPR + tid;
+            RowInfo ri;
+            ri.nact = 0;
+            if (q < a.nq) {
+                const Query Q = decode(a.d, q);
+                const WarmGame &G = a.d.games[Q.game];
+                const int4 nd = a.d.node[G.node_off[Q.player] + Q.node];
+                const int2 cd = a.d.cards[G.hand_off + Q.hand];
+                const float4 hf = reinterpret_cast<const float4 *>(a.d.hand)[G.hand_off + Q.hand];
+                ri.base = G.voff[Q.player] + Q.hand;
+                ri.gp = 2 * Q.game + Q.player;
+                ri.node = G.node_off[Q.player] + Q.node;
+                ri.ca = cd.x;
+                ri.cb = cd.y;
+                ri.nact = nd.y;
+                ri.s0 = nd.x;
+                ri.hs = G.hs;
+                ri.player = Q.player;
+                ri.pos = hf.x;
+                ri.tie = hf.y;
+                ri.mu = Q.player == 0 ? hf.z : hf.w;
+            }
+            rows[tid] = ri;
+        }
+        __syncthreads();
+        // layer 1: column j of every row
+        for (int r = 0; r < kPR; ++r) {
+            const RowInfo &ri = rows[r];
+            float z = 0.f;
+            if (ri.nact > 0) {
+                z = a.G1[(long long)ri.gp * kWidth + j] + a.N1[(long long)ri.node * kWidth + j] + ri.pos * wpos +
+                    ri.tie * wtie + ri.mu * wmu + __bfloat162float(Wc[ri.ca * kWidth + j]) + bias1;
+                if (ri.cb >= 0) z += __bfloat162float(Wc[ri.cb * kWidth + j]);
+                z = fmaxf(z, 0.f);
+            }
+            Hs[r * kPitchH + j] = __float2bfloat16_rn(z);
+        }
+        __syncthreads();
+        // layer 2: this warp's 16 rows x 256 columns
+        const int r0 = warp * 16;
+        float acc[32][4];
+#pragma unroll
+        for (int n = 0; n < 32; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll 1
+        for (int k0 = 0; k0 < kWidth; k0 += 16) {
+            const uint32_t a0 = ld_pair(Hs + (r0 + g) * kPitchH + k0 + 2 * t);
+            const uint32_t a1 = ld_pair(Hs + (r0 + g + 8) * kPitchH + k0 + 2 * t);
+            const uint32_t a2 = ld_pair(Hs + (r0 + g) * kPitchH + k0 + 2 * t + 8);
+            const uint32_t a3 = ld_pair(Hs + (r0 + g + 8) * kPitchH + k0 + 2 * t + 8);
+#pragma unroll
+            for (int n = 0; n < 32; ++n) {
+                const uint32_t b0 = ld_pair(W2t + (8 * n + g) * kPitchH + k0 + 2 * t);
+                const uint32_t b1 = ld_pair(W2t + (8 * n + g) * kPitchH + k0 + 2 * t + 8);
+                mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int n = 0; n < 32; ++n) {
+            const int c = 8 * n + 2 * t;
+            const float bb0 = a.b2[c], bb1 = a.b2[c + 1];
+            st_pair(Hs + (r0 + g) * kPitchH + c, fmaxf(acc[n][0] + bb0, 0.f), fmaxf(acc[n][1] + bb1, 0.f));
+            st_pair(Hs + (r0 + g + 8) * kPitchH + c, fmaxf(acc[n][2] + bb0, 0.f), fmaxf(acc[n][3] + bb1, 0.f));
+        }
+        __syncwarp();
+        // layer 3: 16 rows x 16 (padded) logits
+        float z3[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll 4
+        for (int k0 = 0; k0 < kWidth; k0 += 16) {
+            const uint32_t a0 = ld_pair(Hs + (r0 + g) * kPitchH + k0 + 2 * t);
+            const uint32_t a1 = ld_pair(Hs + (r0 + g + 8) * kPitchH + k0 + 2 * t);
+            const uint32_t a2 = ld_pair(Hs + (r0 + g) * kPitchH + k0 + 2 * t + 8);
+            const uint32_t a3 = ld_pair(Hs + (r0 + g + 8) * kPitchH + k0 + 2 * t + 8);
+#pragma unroll
+            for (int n = 0; n < 2; ++n) {
+                const uint32_t b0 = ld_pair(W3t + (8 * n + g) * kPitchH + k0 + 2 * t);
+                const uint32_t b1 = ld_pair(W3t + (8 * n + g) * kPitchH + k0 + 2 * t + 8);
+                mma_bf16(z3[n], a0, a1, a2, a3, b0, b1);
+            }
+        }
+        // masked softmax of rows r0 + g and r0 + g + 8 across the 4 lanes of a row
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const RowInfo &ri = rows[r0 + g + 8 * half];
+            const int cols[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
+            float v[4];
+            v[0] = z3[0][2 * half];
+            v[1] = z3[0][2 * half + 1];
+            v[2] = z3[1][2 * half];
+            v[3] = z3[1][2 * half + 1];
+            float mx = -INFINITY;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                v[i] += cols[i] < a.dout ? a.b3[cols[i]] : 0.f;
+                if (cols[i] < ri.nact) mx = fmaxf(mx, v[i]);
+            }
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+            float e[4], s = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                e[i] = cols[i] < ri.nact ? __expf(v[i] - mx) : 0.f;
+                s += e[i];
+            }
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            if (ri.nact > 0) {
+                float *beh = ri.player == 0 ? a.beh1 : a.beh2;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (cols[i] < ri.nact) beh[ri.base + (long long)(ri.s0 + cols[i]) * ri.hs] = e[i] / s;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// Device tables of a batch's warm-start features (built on first use).
+struct WarmTables {
+    void *blob = nullptr;
+    WarmDev d{};
+    long long nq = 0;
+};
+
+namespace kps_abi {
+
+void warm_free(kps_batch *b) {
+    if (b->warm) {
+        cudaFree(static_cast<WarmTables *>(b->warm)->blob);
+        delete static_cast<WarmTables *>(b->warm);
+        b->warm = nullptr;
+    }
+}
+
+}  // namespace kps_abi
+
+namespace {
+
+kps_status warm_tables(kps_batch *b, const WarmTables **out) {
+    if (b->warm) {
+        *out = static_cast<WarmTables *>(b->warm);
+        return KPS_OK;
+    }
+    const int ng = (int)b->games.size();
+    std::vector<WarmGame> games(ng);
+    std::vector<long long> qstart(ng + 1, 0);
+    std::vector<float> hist, hand, node_feat;
+    std::vector<int4> node;
+    std::vector<int2> cards;
+    for (int i = 0; i < ng; ++i) {
+        const kps::HostGame &h = b->games[i]->host;
+        if (h.nodes[0] > 32 || h.nodes[1] > 32) return fail(KPS_ENOTSUP, "more than 32 decision nodes per player");
+        WarmGame &G = games[i];
+        G.H = h.H;
+        G.hs = h.hs;
+        G.qstart = qstart[i];
+        qstart[i + 1] = qstart[i] + (long long)(h.nodes[0] + h.nodes[1]) * h.H;
+        G.hand_off = (long long)cards.size();
+        unsigned long long left = 0;
+        for (int c : h.slot_card) left |= 1ull << c;
+        const int deck = h.spec.ranks * h.spec.suits;
+        const unsigned long long all = deck >= 64 ? ~0ull : ((1ull << deck) - 1);
+        G.board_lo = all & ~left;
+        double msum[2] = {0.0, 0.0};
+        for (int q = 0; q < h.H; ++q) {
+            msum[0] += h.mu1[q];
+            msum[1] += h.mu2[q];
+        }
+        for (int p = 0; p < 2; ++p) {
+            G.voff[p] = b->off[p][i];
+            G.nodes[p] = h.nodes[p];
+            G.node_off[p] = (int)node.size();
+            G.hist_off[p] = (long long)hist.size();
+            // the opponent's range over the strength order
+            const std::vector<double> &mq = p == 0 ? h.mu2 : h.mu1;
+            std::vector<float> hb(kHist, 0.f);
+            for (int q = 0; q < h.H; ++q) {
+                const int bin = (int)((long long)q * kHist / h.H);
+                hb[bin] += msum[1 - p] > 0.0 ? (float)(mq[q] / msum[1 - p]) : 0.f;
+            }
+            hist.insert(hist.end(), hb.begin(), hb.end());
+            std::vector<int> first(h.nodes[p], -1);
+            for (int q = 0; q < h.n[p]; ++q)
+                if (first[h.seqs[p][q].node] < 0) first[h.seqs[p][q].node] = q;
+            std::vector<int> depth(h.nodes[p], 0);
+            for (int k = 0; k < h.nodes[p]; ++k) {
+                const int par = h.seqs[p][first[k]].parent;
+                depth[k] = par < 0 ? 0 : depth[h.seqs[p][par].node] + 1;
+                node.push_back(make_int4(first[k], h.nodes_nact[p][k], par, depth[k]));
+                float nf[40] = {};
+                nf[k] = 1.f;
+                nf[32] = (float)p;
+                nf[33] = h.nodes_nact[p][k] / 12.f;
+                nf[34] = depth[k] / 8.f;
+                node_feat.insert(node_feat.end(), nf, nf + 40);
+            }
+        }
+        for (int q = 0; q < h.H; ++q) {
+            const int a = h.slot_card[h.hand_slots[2 * q]];
+            const int s2 = h.hand_slots[2 * q + 1];
+            const int c2 = s2 < h.ncards ? h.slot_card[s2] : -1;
+            cards.push_back(make_int2(a, c2));
+            hand.push_back(h.H > 1 ? (float)q / (float)(h.H - 1) : 0.f);
+            hand.push_back((float)(h.group_hi[q] - h.group_lo[q] + 1) / 32.f);
+            hand.push_back(msum[0] > 0.0 ? (float)(h.mu1[q] * h.H / msum[0]) : 0.f);
+            hand.push_back(msum[1] > 0.0 ? (float)(h.mu2[q] * h.H / msum[1]) : 0.f);
+        }
+    }
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t o_g = 0, o_q = al(sizeof(WarmGame) * ng), o_h = al(o_q + 8 * (size_t)(ng + 1)),
+                 o_n = al(o_h + 4 * hist.size()), o_c = al(o_n + sizeof(int4) * node.size()),
+                 o_f = al(o_c + sizeof(int2) * cards.size()), o_nf = al(o_f + 4 * hand.size()),
+                 total = al(o_nf + 4 * node_feat.size());
+    std::vector<unsigned char> host(total, 0);
+    std::memcpy(host.data() + o_g, games.data(), sizeof(WarmGame) * ng);
+    std::memcpy(host.data() + o_q, qstart.data(), 8 * (size_t)(ng + 1));
+    std::memcpy(host.data() + o_h, hist.data(), 4 * hist.size());
+    std::memcpy(host.data() + o_n, node.data(), sizeof(int4) * node.size());
+    std::memcpy(host.data() + o_c, cards.data(), sizeof(int2) * cards.size());
+    std::memcpy(host.data() + o_f, hand.data(), 4 * hand.size());
+    std::memcpy(host.data() + o_nf, node_feat.data(), 4 * node_feat.size());
+    WarmTables *t = new (std::nothrow) WarmTables;
+    if (!t) return fail(KPS_ENOMEM, "warm-start tables");
+    if (cudaMalloc(&t->blob, total) != cudaSuccess) {
+        delete t;
+        return fail(KPS_ENOMEM, "warm-start tables");
+    }
+    cudaError_t e = cudaMemcpy(t->blob, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(t->blob);
+        delete t;
+        return cuda_fail(e, "uploading warm-start tables");
+    }
+    unsigned char *bl = static_cast<unsigned char *>(t->blob);
+    t->d.games = reinterpret_cast<const WarmGame *>(bl + o_g);
+    t->d.qstart = reinterpret_cast<const long long *>(bl + o_q);
+    t->d.ngames = ng;
+    t->d.hist = reinterpret_cast<const float *>(bl + o_h);
+    t->d.node = reinterpret_cast<const int4 *>(bl + o_n);
+    t->d.cards = reinterpret_cast<const int2 *>(bl + o_c);
+    t->d.hand = reinterpret_cast<const float *>(bl + o_f);
+    t->d.node_feat = reinterpret_cast<const float *>(bl + o_nf);
+    t->d.total_nodes = (int)node.size();
+    t->nq = qstart[ng];
+    b->warm = t;
+    *out = t;
+    return KPS_OK;
+}
+
+kps_status check_range(const WarmTables *t, const int64_t *qidx, int64_t q0, int32_t nq) {
+    if (nq < 0) return fail(KPS_EINVAL, "nq must be >= 0");
+    if (!qidx && (q0 < 0 || q0 + nq > t->nq)) return fail(KPS_EINVAL, "query range outside the batch");
+    return KPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kps_status kps_warm_num_queries(kps_batch *b, int64_t *n) {
+    if (!b || !n) return fail(KPS_EINVAL, "bad argument");
+    const WarmTables *t = nullptr;
+    kps_status st = warm_tables(b, &t);
+    if (st != KPS_OK) return st;
+    *n = t->nq;
+    return KPS_OK;
+}
+
+kps_status kps_warm_features(kps_batch *b, const int64_t *qidx, int64_t q0, int32_t nq, float *X, int32_t *nact,
+                             void *stream) {
+    if (!b || (nq > 0 && !X)) return fail(KPS_EINVAL, "bad argument");
+    const WarmTables *t = nullptr;
+    kps_status st = warm_tables(b, &t);
+    if (st == KPS_OK) st = check_range(t, qidx, q0, nq);
+    if (st != KPS_OK || nq == 0) return st;
+    features_kernel<<<nq, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        t->d, reinterpret_cast<const long long *>(qidx), q0, X, nact);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "warm-start features");
+    return KPS_OK;
+}
+
+kps_status kps_warm_targets(kps_batch *b, const double *beh1, const double *beh2, const double *x1, const double *x2,
+                            const int64_t *qidx, int64_t q0, int32_t nq, float *T, float *w, void *stream) {
+    if (!b || (nq > 0 && (!beh1 || !beh2 || !T || !w))) return fail(KPS_EINVAL, "bad argument");
+    const WarmTables *t = nullptr;
+    kps_status st = warm_tables(b, &t);
+    if (st == KPS_OK) st = check_range(t, qidx, q0, nq);
+    if (st != KPS_OK || nq == 0) return st;
+    targets_kernel<<<(nq + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        t->d, beh1, beh2, x1, x2, reinterpret_cast<const long long *>(qidx), q0, nq, T, w);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "warm-start targets");
+    return KPS_OK;
+}
+
+kps_status kps_warm_scatter(kps_batch *b, const float *P, const int64_t *qidx, int64_t q0, int32_t nq, float *beh1,
+                            float *beh2, void *stream) {
+    if (!b || (nq > 0 && (!P || !beh1 || !beh2))) return fail(KPS_EINVAL, "bad argument");
+    const WarmTables *t = nullptr;
+    kps_status st = warm_tables(b, &t);
+    if (st == KPS_OK) st = check_range(t, qidx, q0, nq);
+    if (st != KPS_OK || nq == 0) return st;
+    scatter_kernel<<<(nq + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        t->d, P, reinterpret_cast<const long long *>(qidx), q0, nq, beh1, beh2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "warm-start scatter");
+    return KPS_OK;
+}
+
+kps_status kps_warm_predict(kps_batch *b, kps_mlp *m, float *beh1, float *beh2, void *stream) {
+    if (!b || !m || !beh1 || !beh2) return fail(KPS_EINVAL, "bad argument");
+    if (m->din != kDin || m->width != kWidth || m->dout > 16)
+        return fail(KPS_ENOTSUP, "the fused predictor needs din = KPS_WARM_DIN, width 256, dout <= 16");
+    const WarmTables *t = nullptr;
+    kps_status st = warm_tables(b, &t);
+    if (st != KPS_OK) return st;
+    if (t->nq == 0) return KPS_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int ng = t->d.ngames, nn = t->d.total_nodes;
+    float *Gf = nullptr, *G1 = nullptr, *N1 = nullptr;
+    cudaError_t e = cudaMalloc(&Gf, (size_t)2 * ng * kOffNode * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&G1, (size_t)2 * ng * kWidth * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&N1, (size_t)std::max(nn, 1) * kWidth * 4);
+    if (e != cudaSuccess) {
+        cudaFree(Gf);
+        cudaFree(G1);
+        return fail(KPS_ENOMEM, "predictor tables");
+    }
+    const __nv_bfloat16 *W1 = m->ph + m->off[0];
+    game_part_kernel<<<2 * ng, 256, 0, s>>>(t->d, Gf);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = mlp_gemm_xw(2 * ng, kWidth, kOffNode, Gf, kOffNode, W1, kWidth, G1, kWidth, s);
+    if (e == cudaSuccess)
+        e = mlp_gemm_xw(nn, kWidth, kOffHand - kOffNode, t->d.node_feat, kOffHand - kOffNode,
+                        W1 + (size_t)kOffNode * kWidth, kWidth, N1, kWidth, s);
+    if (e == cudaSuccess) {
+        static bool configured = false;
+        if (!configured) {
+            e = cudaFuncSetAttribute(predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)predict_smem_bytes());
+            configured = e == cudaSuccess;
+        }
+    }
+    if (e == cudaSuccess) {
+        PredictArgs a;
+        a.d = t->d;
+        a.G1 = G1;
+        a.N1 = N1;
+        a.W1h = W1 + (size_t)kOffHand * kWidth;
+        a.b1 = m->p + m->off[1];
+        a.b2 = m->p + m->off[3];
+        a.b3 = m->p + m->off[5];
+        a.W2 = m->ph + m->off[2];
+        a.W3 = m->ph + m->off[4];
+        a.dout = m->dout;
+        a.nq = t->nq;
+        a.beh1 = beh1;
+        a.beh2 = beh2;
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long ntiles = (t->nq + kPR - 1) / kPR;
+        const int grid = (int)std::min<long long>(ntiles, sms);
+        predict_kernel<<<grid, 256, predict_smem_bytes(), s>>>(a);
+        e = cudaGetLastError();
+    }
+    // the temporaries are released after the work that reads them
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(Gf);
+    cudaFree(G1);
+    cudaFree(N1);
+    if (e != cudaSuccess) return cuda_fail(e, "warm-start prediction");
+    return KPS_OK;
+}
+
+}  // extern "C"

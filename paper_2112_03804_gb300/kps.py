@@ -68,8 +68,13 @@ EXPORTED = ["kps_sparsify", "kps_game_destroy", "kps_game_info", "kps_game_hands
             "kps_matvec_A_static_scratch",
             "kps_batch_create", "kps_batch_destroy", "kps_batch_offsets", "kps_batch_matvec_A",
             "kps_batch_matvec_AT", "kps_batch_tune", "kps_batch_shape_get", "kps_batch_shape_set",
-            "kps_solver_create", "kps_solver_destroy", "kps_solver_reset", "kps_solver_step",
+            "kps_solver_create", "kps_solver_destroy", "kps_solver_reset", "kps_solver_warm_start",
+            "kps_solver_step",
             "kps_solver_iterations", "kps_solver_average", "kps_solver_strategy", "kps_solver_exploitability",
+            "kps_warm_num_queries", "kps_warm_features", "kps_warm_targets", "kps_warm_scatter",
+            "kps_warm_predict",
+            "kps_mlp_create", "kps_mlp_destroy", "kps_mlp_num_params", "kps_mlp_get", "kps_mlp_set",
+            "kps_mlp_forward", "kps_mlp_gradients", "kps_mlp_adam",
             "kps_last_error", "kps_version"]
 
 _lib = None
@@ -109,6 +114,20 @@ def lib():
         L.kps_solver_average.argtypes = [P, C.c_int32, P, P, P]
         L.kps_solver_exploitability.argtypes = [P, P, P, P, P]
         L.kps_solver_strategy.argtypes = [P, P, P, P]
+        L.kps_solver_warm_start.argtypes = [P, P, P, C.c_double, C.c_int32, P]
+        L.kps_warm_num_queries.argtypes = [P, C.POINTER(C.c_int64)]
+        L.kps_warm_features.argtypes = [P, P, C.c_int64, C.c_int32, P, P, P]
+        L.kps_warm_targets.argtypes = [P, P, P, P, P, P, C.c_int64, C.c_int32, P, P, P]
+        L.kps_warm_scatter.argtypes = [P, P, P, C.c_int64, C.c_int32, P, P, P]
+        L.kps_warm_predict.argtypes = [P, P, P, P, P]
+        L.kps_mlp_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(C.c_void_p)]
+        L.kps_mlp_destroy.argtypes = [P]
+        L.kps_mlp_num_params.argtypes = [P, C.POINTER(C.c_int64)]
+        L.kps_mlp_get.argtypes = [P, C.c_int32, P]
+        L.kps_mlp_set.argtypes = [P, P]
+        L.kps_mlp_forward.argtypes = [P, P, C.c_int32, P, P, P]
+        L.kps_mlp_gradients.argtypes = [P, P, C.c_int32, P, P, P, C.c_float, P, P]
+        L.kps_mlp_adam.argtypes = [P, C.c_float, C.c_float, C.c_float, C.c_float, P]
         for name in EXPORTED:
             if name not in ("kps_last_error", "kps_version"):
                 getattr(L, name).restype = C.c_int
@@ -355,6 +374,9 @@ class Solver:
     def reset(self, beh1=None, beh2=None, stream=None):
         _check(lib().kps_solver_reset(self._h, _ptr(beh1), _ptr(beh2), _stream(stream)))
 
+    def warm_start(self, beh1, beh2, kappa: float, t0: int, stream=None):
+        _check(lib().kps_solver_warm_start(self._h, _ptr(beh1), _ptr(beh2), float(kappa), int(t0), _stream(stream)))
+
     def step(self, iters: int, stream=None):
         _check(lib().kps_solver_step(self._h, int(iters), _stream(stream)))
 
@@ -371,6 +393,82 @@ class Solver:
 
     def exploitability(self, expl, br1=None, br2=None, stream=None):
         _check(lib().kps_solver_exploitability(self._h, _ptr(expl), _ptr(br1), _ptr(br2), _stream(stream)))
+
+
+WARM_DIN = 1232
+WARM_DOUT = 12
+
+
+def warm_num_queries(batch: Batch) -> int:
+    n = C.c_int64()
+    _check(lib().kps_warm_num_queries(batch._h, C.byref(n)))
+    return n.value
+
+
+def warm_features(batch: Batch, X, nact=None, q0: int = 0, nq: int = None, qidx=None, stream=None):
+    nq = len(qidx) if qidx is not None else nq
+    _check(lib().kps_warm_features(batch._h, _ptr(qidx), int(q0), int(nq), _ptr(X), _ptr(nact), _stream(stream)))
+
+
+def warm_targets(batch: Batch, beh1, beh2, x1, x2, T, w, q0: int = 0, nq: int = None, qidx=None, stream=None):
+    nq = len(qidx) if qidx is not None else nq
+    _check(lib().kps_warm_targets(batch._h, _ptr(beh1), _ptr(beh2), _ptr(x1), _ptr(x2), _ptr(qidx), int(q0),
+                                  int(nq), _ptr(T), _ptr(w), _stream(stream)))
+
+
+def warm_scatter(batch: Batch, P, beh1, beh2, q0: int = 0, nq: int = None, qidx=None, stream=None):
+    nq = len(qidx) if qidx is not None else nq
+    _check(lib().kps_warm_scatter(batch._h, _ptr(P), _ptr(qidx), int(q0), int(nq), _ptr(beh1), _ptr(beh2),
+                                  _stream(stream)))
+
+
+def warm_predict(batch: Batch, mlp: "MLP", beh1, beh2, stream=None):
+    _check(lib().kps_warm_predict(batch._h, mlp._h, _ptr(beh1), _ptr(beh2), _stream(stream)))
+
+
+class MLP:
+    """The warm-start network (``kps_mlp_*``)."""
+
+    def __init__(self, din: int = WARM_DIN, width: int = 256, dout: int = WARM_DOUT, seed: int = 0):
+        h = C.c_void_p()
+        _check(lib().kps_mlp_create(din, width, dout, seed, C.byref(h)))
+        self._h = h
+        self.din, self.width, self.dout = din, width, dout
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().kps_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self) -> int:
+        n = C.c_int64()
+        _check(lib().kps_mlp_num_params(self._h, C.byref(n)))
+        return n.value
+
+    def get(self, which: int = 0) -> np.ndarray:
+        out = np.zeros(self.num_params(), dtype=np.float32)
+        _check(lib().kps_mlp_get(self._h, which, out.ctypes.data))
+        return out
+
+    def set(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().kps_mlp_set(self._h, p.ctypes.data))
+
+    def forward(self, X, rows: int, nact, P, stream=None):
+        _check(lib().kps_mlp_forward(self._h, _ptr(X), int(rows), _ptr(nact), _ptr(P), _stream(stream)))
+
+    def gradients(self, X, rows: int, nact, T, w, wsum: float, loss=None, stream=None):
+        _check(lib().kps_mlp_gradients(self._h, _ptr(X), int(rows), _ptr(nact), _ptr(T), _ptr(w), float(wsum),
+                                       _ptr(loss), _stream(stream)))
+
+    def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None):
+        _check(lib().kps_mlp_adam(self._h, lr, beta1, beta2, eps, _stream(stream)))
 
 
 def version() -> str:

@@ -1,0 +1,284 @@
+"""Warm-start network and features on the GPU against the FP64 oracle.
+
+* Forward probabilities and the gradients of every parameter block equal
+  the oracle's (oracle/mlp_oracle.py) at the BF16-rounded weights the
+  kernels read: FP32 accumulation over at most 1232 terms, normwise 1e-4.
+  ReLU decisions are taken in the kernels' FP32; the inputs are chosen so
+  that no pre-activation lies within 1e-4 of zero (the FP32 rounding of a
+  pre-activation is about 1e-7 here), where FP32 and FP64 could disagree.
+* One Adam step moves the FP32 master weights by the textbook formula.
+* Feature rows equal a re-derivation from the game's own host view (board,
+  hand cards, strength order, beliefs, nodes); targets and scatter are
+  inverse gathers.
+* The fused predictor (tensor cores, BF16 activations) equals the unfused
+  path (materialised features, FP32 activations) within the BF16 rounding
+  of the activations, on river games with a trained-looking network.
+* The warm-started solver equals the oracle's warm RM+ (FP64, 1e-9).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mlp_oracle as M
+from oracle.oracle import OracleGame
+from paper_2112_03804_gb300 import kps, synth
+from tests.gpu_util import from_library, library_order, normwise_error, to_library
+
+pytestmark = pytest.mark.gpu
+
+DIN, WIDTH, DOUT = kps.WARM_DIN, 256, kps.WARM_DOUT
+
+
+def _bf16(a):
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).bfloat16().double().numpy()
+
+
+def _effective(params):
+    """Weights as the kernels read them (BF16), biases FP32."""
+    blocks = M.unpack(params.astype(np.float64), DIN, WIDTH, DOUT)
+    for i in (0, 2, 4):
+        blocks[i] = _bf16(blocks[i])
+    return M.pack(blocks)
+
+
+def _inputs(Q, seed):
+    r = np.random.default_rng(seed)
+    X = r.normal(0, 1, size=(Q, DIN)).astype(np.float32)
+    nact = r.integers(2, DOUT + 1, size=Q).astype(np.int32)
+    T = np.zeros((Q, DOUT), dtype=np.float32)
+    for q in range(Q):
+        T[q, :nact[q]] = r.dirichlet(np.ones(nact[q]))
+    w = r.uniform(0.2, 2.0, size=Q).astype(np.float32)
+    return X, nact, T, w
+
+
+def _margin_ok(eff, X, nact):
+    _, (_, A1, _, A2, _, _) = M.forward(eff, X.astype(np.float64), nact, DIN, WIDTH, DOUT)
+    return min(np.min(np.abs(A1)), np.min(np.abs(A2))) > 1e-4
+
+
+@pytest.fixture(scope="module")
+def net():
+    m = kps.MLP(DIN, WIDTH, DOUT, seed=5)
+    p = m.get(0)
+    r = np.random.default_rng(1)
+    blocks = M.unpack(p.astype(np.float64), DIN, WIDTH, DOUT)
+    for i in (1, 3, 5):
+        blocks[i] = r.normal(0, 0.3, size=blocks[i].shape)
+    p = M.pack(blocks).astype(np.float32)
+    m.set(p)
+    return m, p
+
+
+def test_forward_and_gradients_match_oracle(net):
+    m, p = net
+    eff = _effective(p)
+    Q = 16
+    for seed in range(400):
+        X, nact, T, w = _inputs(Q, seed)
+        if _margin_ok(eff, X, nact):
+            break
+    else:
+        pytest.fail("no input with all pre-activations away from zero")
+    dX, dn, dT, dw = (torch.from_numpy(a).cuda() for a in (X, nact, T, w))
+    P = torch.zeros(Q, DOUT, device="cuda")
+    m.forward(dX, Q, dn, P)
+    loss = torch.zeros(1, device="cuda")
+    m.gradients(dX, Q, dn, dT, dw, float(w.sum()), loss)
+    torch.cuda.synchronize()
+    P_or, _ = M.forward(eff, X.astype(np.float64), nact, DIN, WIDTH, DOUT)
+    assert np.max(np.abs(P.cpu().numpy() - P_or)) <= 1e-5
+    L_or, g_or = M.loss_and_grads(eff, X.astype(np.float64), nact, T.astype(np.float64), w.astype(np.float64),
+                                  DIN, WIDTH, DOUT)
+    assert abs(float(loss.item()) - L_or) <= 1e-5 * abs(L_or)
+    g = m.get(1).astype(np.float64)
+    for blk, (a, b) in enumerate(zip(M.unpack(g, DIN, WIDTH, DOUT), M.unpack(g_or, DIN, WIDTH, DOUT))):
+        assert normwise_error(a, b) <= 1e-4, blk
+
+
+def test_adam_step(net):
+    m, p0 = net
+    m.set(p0)
+    X, nact, T, w = _inputs(32, 7)
+    dX, dn, dT, dw = (torch.from_numpy(a).cuda() for a in (X, nact, T, w))
+    m.gradients(dX, 32, dn, dT, dw, float(w.sum()))
+    torch.cuda.synchronize()
+    g = m.get(1).astype(np.float64)
+    before = m.get(0).astype(np.float64)
+    lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-8
+    m.adam(lr, b1, b2, eps)
+    torch.cuda.synchronize()
+    after = m.get(0).astype(np.float64)
+    # first step: m_hat = g, v_hat = g^2
+    expect = before - lr * g / (np.abs(g) + eps)
+    assert np.max(np.abs(after - expect)) <= 1e-6
+    m.set(p0)
+
+
+def _small_batch():
+    specs = [synth.micro_spec(seed=3, ranks=4, suits=2, nboard=2),
+             synth.micro_spec(seed=8, ranks=5, suits=2, nboard=3, raise_cap=3, stack=12.0)]
+    games = [kps.Game(s) for s in specs]
+    return specs, games, kps.Batch(games)
+
+
+def test_features_match_definition():
+    specs, games, b = _small_batch()
+    nq = kps.warm_num_queries(b)
+    expect_n = sum((g.info()["nodes1"] + g.info()["nodes2"]) * g.info()["H"] for g in games)
+    assert nq == expect_n
+    X = torch.zeros(nq, DIN, device="cuda")
+    nact = torch.zeros(nq, dtype=torch.int32, device="cuda")
+    kps.warm_features(b, X, nact, q0=0, nq=nq)
+    torch.cuda.synchronize()
+    X, nact = X.cpu().numpy(), nact.cpu().numpy()
+    q = 0
+    for spec, g in zip(specs, games):
+        inf = g.info()
+        H = inf["H"]
+        cards, canon = g.hands()
+        mu = [np.asarray(spec["mu1"])[canon], np.asarray(spec["mu2"])[canon]]
+        board = np.zeros(52)
+        board[spec["board"]] = 1.0
+        for p in (0, 1):
+            seqs = g.sequences(p)
+            nn = len(seqs["nact"])
+            hist = np.zeros(1081)
+            for pos in range(H):
+                hist[pos * 1081 // H] += mu[1 - p][pos] / mu[1 - p].sum()
+            for k in range(nn):
+                first = int(np.flatnonzero(seqs["node"] == k)[0])
+                depth, par = 0, seqs["parent"][first]
+                while par >= 0:
+                    depth += 1
+                    par = seqs["parent"][int(np.flatnonzero(seqs["node"] == seqs["node"][par])[0])]
+                for h in range(H):
+                    row = X[q]
+                    assert np.array_equal(row[:52], board)
+                    assert np.allclose(row[52:1133], hist, atol=1e-7)
+                    node = np.zeros(40)
+                    node[k] = 1.0
+                    node[32], node[33], node[34] = p, seqs["nact"][k] / 12.0, depth / 8.0
+                    assert np.allclose(row[1133:1173], node, atol=1e-7)
+                    hand = np.zeros(59)
+                    hand[0] = h / (H - 1)
+                    strength = np.asarray(spec["strength"])[canon]
+                    hand[1] = np.sum(strength == strength[h]) / 32.0
+                    hand[2] = mu[p][h] * H / mu[p].sum()
+                    hand[4 + cards[h]] = 1.0
+                    assert np.allclose(row[1173:], hand, atol=1e-6), (q, p, k, h)
+                    assert nact[q] == seqs["nact"][k]
+                    q += 1
+    assert q == nq
+
+
+def test_scatter_then_targets_roundtrip():
+    specs, games, b = _small_batch()
+    nq = kps.warm_num_queries(b)
+    r = np.random.default_rng(0)
+    P = torch.from_numpy(r.uniform(0, 1, size=(nq, DOUT)).astype(np.float32)).cuda()
+    n = [int(b.offsets(p)[-1]) for p in (0, 1)]
+    beh = [torch.zeros(n[p], device="cuda") for p in (0, 1)]
+    kps.warm_scatter(b, P, beh[0], beh[1], q0=0, nq=nq)
+    T = torch.zeros(nq, DOUT, device="cuda")
+    w = torch.zeros(nq, device="cuda")
+    kps.warm_targets(b, beh[0].double(), beh[1].double(), None, None, T, w, q0=0, nq=nq)
+    nact = torch.zeros(nq, dtype=torch.int32, device="cuda")
+    X = torch.zeros(nq, DIN, device="cuda")
+    kps.warm_features(b, X, nact, q0=0, nq=nq)
+    torch.cuda.synchronize()
+    na = nact.cpu().numpy()
+    mask = np.arange(DOUT)[None, :] < na[:, None]
+    assert np.array_equal(T.cpu().numpy()[mask], P.cpu().numpy()[mask])
+    assert np.all(T.cpu().numpy()[~mask] == 0)
+    # weight without averages = normalised belief of the query's hand
+    assert np.all(w.cpu().numpy() > 0)
+    # sampled queries give the same rows as the contiguous range
+    idx = torch.from_numpy(r.choice(nq, size=37, replace=False).astype(np.int64)).cuda()
+    Xs = torch.zeros(37, DIN, device="cuda")
+    kps.warm_features(b, Xs, None, qidx=idx)
+    torch.cuda.synchronize()
+    assert torch.equal(Xs, X[idx.long()])
+
+
+def test_warm_started_solver_matches_oracle():
+    spec = synth.micro_spec(seed=3, ranks=4, suits=2, nboard=2)
+    og = OracleGame(spec)
+    g = kps.Game(spec)
+    b = kps.Batch([g])
+    s = kps.Solver(b, kps.F64)
+    order = library_order(spec["strength"])
+    inf = g.info()
+    beh = [synth.simplex_vectors(og.sequences(p)["nact"], og.H, 1, seed=30 + p)[0] for p in (0, 1)]
+    dev = [torch.from_numpy(to_library(beh[p], order, inf["hs"]).reshape(-1)).to("cuda", torch.float32)
+           for p in (0, 1)]
+    b32 = [from_library(dev[p].cpu().double().numpy().reshape(-1, inf["hs"]), order, inf["H"]) for p in (0, 1)]
+    s.warm_start(dev[0], dev[1], kappa=0.5, t0=20)
+    s.step(30)
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s.exploitability(e)
+    x = torch.zeros(int(b.offsets(0)[-1]), dtype=torch.float64, device="cuda")
+    y = torch.zeros(int(b.offsets(1)[-1]), dtype=torch.float64, device="cuda")
+    s.average(x, y, behavioural=True)
+    torch.cuda.synchronize()
+    e_or, a1, a2, _ = og.rmplus_warm(30, b32[0], b32[1], 0.5, 20)
+    assert abs(float(e.item()) - e_or) <= 1e-9 * max(1.0, abs(e_or))
+    assert s.iterations() == 50
+    ax = from_library(x.cpu().numpy().reshape(-1, inf["hs"]), order, inf["H"])
+    ay = from_library(y.cpu().numpy().reshape(-1, inf["hs"]), order, inf["H"])
+    assert np.max(np.abs(ax - a1)) <= 1e-9 and np.max(np.abs(ay - a2)) <= 1e-9
+
+
+def test_fused_predictor_matches_unfused():
+    from paper_2112_03804_gb300 import warmstart
+    specs = [synth.river_spec(seed=s) for s in (31, 32, 33)] + [synth.micro_spec(seed=4, ranks=4, suits=2, nboard=2)]
+    games = [kps.Game(s) for s in specs]
+    b = kps.Batch(games)
+    m = kps.MLP(seed=9)
+    # larger output weights than the initialisation: probabilities far from uniform
+    p = m.get(0)
+    blocks = M.unpack(p.astype(np.float64), DIN, WIDTH, DOUT)
+    blocks[4] *= 8.0
+    blocks[5] = np.random.default_rng(2).normal(0, 1.0, size=DOUT)
+    m.set(M.pack(blocks).astype(np.float32))
+    fused = warmstart.predict(m, b)
+    ref = warmstart.predict_unfused(m, b)
+    torch.cuda.synchronize()
+    for p in (0, 1):
+        f, r = fused[p].cpu().numpy(), ref[p].cpu().numpy()
+        assert np.max(np.abs(f - r)) <= 3e-2, p
+        assert np.mean(np.abs(f - r)) <= 3e-3, p
+    # every node's probabilities sum to one for every hand
+    for i, g in enumerate(games):
+        inf = g.info()
+        for p in (0, 1):
+            seqs = g.sequences(p)
+            off = b.offsets(p)
+            v = fused[p].cpu().numpy()[off[i]:off[i + 1]].reshape(-1, inf["hs"])[:, :inf["H"]]
+            for k in range(len(seqs["nact"])):
+                rows = np.flatnonzero(seqs["node"] == k)
+                assert np.allclose(v[rows].sum(axis=0), 1.0, atol=1e-5)
+
+
+def test_trained_network_saves_iterations():
+    """The learned part against the method without it: a network trained on
+    equilibria of 512 solved river endgames (the config-2 generator) warm
+    starts RM+ on 64 other endgames, which then reach exploitability below
+    1e-3 of the pot in fewer iterations than from a cold start."""
+    from paper_2112_03804_gb300 import warmstart
+    rng = np.random.default_rng(17)
+    train_specs = [synth.river_spec(seed=int(s)) for s in rng.integers(1 << 62, size=512)]
+    tg = [kps.Game(s) for s in train_specs]
+    tb = kps.Batch(tg)
+    s, it, ex, _ = warmstart.solve(tb, kps.F32, 1e-3, block=25, max_iters=2000)
+    assert ex.max() < 1e-3
+    data = warmstart.sample(tb, s, 128, seed=0)
+    m = kps.MLP(seed=1)
+    hist = warmstart.train(m, data, epochs=10, rows=4096, lr=1e-3, lr_decay=0.8)
+    assert hist[-1] < 0.8 * hist[0]
+    test_specs = [synth.river_spec(seed=int(s)) for s in rng.integers(1 << 62, size=64)]
+    hb = kps.Batch([kps.Game(s) for s in test_specs])
+    r = warmstart.compare(m, hb, kps.F32, 1e-3, kappa=0.02, t0=0, block=25, max_iters=2000)
+    assert r["cold"]["max_expl"] < 1e-3 and r["warm"]["max_expl"] < 1e-3
+    assert r["warm"]["iterations"] < r["cold"]["iterations"], r
