@@ -217,6 +217,14 @@ kps_status kps_batch_shape_get(kps_batch *batch, kps_dtype dt, kps_batch_shape *
  * (out of range), KPS_ENOTSUP (warp count the games do not fit). */
 kps_status kps_batch_shape_set(kps_batch *batch, kps_dtype dt, const kps_batch_shape *shape);
 
+/* Splits items 0..n-1 (games, in order) into `parts` contiguous ranges
+ * [bounds[k], bounds[k+1]) whose weight sums (e.g. H * (n1 + n2) bytes per
+ * game) are as even as a prefix split allows: cut k falls where the prefix
+ * sum is closest to k/parts of the total.  bounds has parts + 1 entries.
+ * Host only; used to shard a batch of games over GPUs, one rank each (the
+ * games need no communication; only per-game scalars are gathered). */
+kps_status kps_partition(const int64_t *weights, int32_t n, int32_t parts, int32_t *bounds);
+
 /* ---- First-order solver ---------------------------------------------------
  * Regret matching plus with alternating updates and linearly weighted
  * averages on every game of a batch, the gradients A y and -A^T x coming

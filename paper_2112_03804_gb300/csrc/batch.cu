@@ -395,4 +395,25 @@ kps_status kps_batch_shape_set(kps_batch *b, kps_dtype dt, const kps_batch_shape
     return KPS_OK;
 }
 
+kps_status kps_partition(const int64_t *weights, int32_t n, int32_t parts, int32_t *bounds) {
+    if (!bounds || n < 0 || parts < 1 || (n > 0 && !weights)) return fail(KPS_EINVAL, "bad argument");
+    long long total = 0;
+    for (int i = 0; i < n; ++i) {
+        if (weights[i] < 0) return fail(KPS_EINVAL, "negative weight");
+        total += weights[i];
+    }
+    bounds[0] = 0;
+    long long cum = 0;
+    int i = 0;
+    for (int k = 1; k < parts; ++k) {
+        // cut where the prefix sum comes closest to k/parts of the total
+        const double target = (double)total * k / parts;
+        while (i < n && (double)(cum + weights[i]) <= target) cum += weights[i++];
+        if (i < n && (double)(cum + weights[i]) - target < target - (double)cum) cum += weights[i++];
+        bounds[k] = i;
+    }
+    bounds[parts] = n;
+    return KPS_OK;
+}
+
 }  // extern "C"

@@ -67,7 +67,7 @@ EXPORTED = ["kps_sparsify", "kps_game_destroy", "kps_game_info", "kps_game_hands
             "kps_matvec_A", "kps_matvec_AT", "kps_matvec_A_host", "kps_matvec_AT_host",
             "kps_matvec_A_static_scratch",
             "kps_batch_create", "kps_batch_destroy", "kps_batch_offsets", "kps_batch_matvec_A",
-            "kps_batch_matvec_AT", "kps_batch_tune", "kps_batch_shape_get", "kps_batch_shape_set",
+            "kps_batch_matvec_AT", "kps_batch_tune", "kps_batch_shape_get", "kps_batch_shape_set", "kps_partition",
             "kps_solver_create", "kps_solver_destroy", "kps_solver_reset", "kps_solver_warm_start",
             "kps_solver_step",
             "kps_solver_iterations", "kps_solver_average", "kps_solver_strategy", "kps_solver_exploitability",
@@ -106,6 +106,7 @@ def lib():
         L.kps_batch_tune.argtypes = [P, C.c_int, P, C.POINTER(BatchShape)]
         L.kps_batch_shape_get.argtypes = [P, C.c_int, C.POINTER(BatchShape)]
         L.kps_batch_shape_set.argtypes = [P, C.c_int, C.POINTER(BatchShape)]
+        L.kps_partition.argtypes = [P, C.c_int32, C.c_int32, P]
         L.kps_solver_create.argtypes = [P, C.c_int, C.POINTER(C.c_void_p)]
         L.kps_solver_destroy.argtypes = [P]
         L.kps_solver_reset.argtypes = [P, P, P, P]
@@ -349,6 +350,14 @@ class Batch:
     def set_shape(self, dtype: int, warps: int, grid: int, schedule: int):
         sh = BatchShape(warps, grid, schedule, 0.0)
         _check(lib().kps_batch_shape_set(self._h, dtype, C.byref(sh)))
+
+
+def partition(weights, parts: int) -> np.ndarray:
+    """Contiguous ranges of items balanced by weight (``kps_partition``)."""
+    w = np.ascontiguousarray(weights, dtype=np.int64)
+    bounds = np.zeros(parts + 1, dtype=np.int32)
+    _check(lib().kps_partition(w.ctypes.data if len(w) else None, len(w), parts, bounds.ctypes.data))
+    return bounds
 
 
 class Solver:
