@@ -156,15 +156,30 @@ kps_status tiles_for(kps_game *g, int nw, cudaStream_t stream, const kps_game::T
         std::vector<int2> host(tl.size());
         for (size_t i = 0; i < tl.size(); ++i) host[i] = make_int2(tl[i].first, tl[i].second);
         t.host = host;
-        cudaError_t e = cudaMalloc(&t.dev, std::max<size_t>(1, host.size()) * sizeof(int2));
+        std::vector<std::pair<int, int>> work;
+        std::vector<uint32_t> trip;
+        if (g->host.max_tie <= kps::kTile) kps::tie_work(g->host, tl, work, trip);
+        else work.assign(tl.size(), std::make_pair(0, 0));
+        // one allocation: tiles, tie work, tie entries
+        const size_t n = host.size();
+        const size_t bytes = (2 * n + 1) * sizeof(int2) + std::max<size_t>(1, trip.size()) * sizeof(uint32_t);
+        std::vector<unsigned char> blob(bytes, 0);
+        std::vector<int2> w2(n);
+        for (size_t i = 0; i < n; ++i) w2[i] = make_int2(work[i].first, work[i].second);
+        if (n) {
+            std::memcpy(blob.data(), host.data(), n * sizeof(int2));
+            std::memcpy(blob.data() + n * sizeof(int2), w2.data(), n * sizeof(int2));
+        }
+        if (!trip.empty()) std::memcpy(blob.data() + 2 * n * sizeof(int2), trip.data(), trip.size() * sizeof(uint32_t));
+        cudaError_t e = cudaMalloc(&t.dev, bytes);
         if (e != cudaSuccess) return fail(KPS_ENOMEM, "tile table");
-        if (!host.empty()) {
-            e = cudaMemcpyAsync(t.dev, host.data(), host.size() * sizeof(int2), cudaMemcpyHostToDevice, stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-            if (e != cudaSuccess) {
-                cudaFree(t.dev);
-                return cuda_fail(e, "uploading the tile table");
-            }
+        t.tie_work = t.dev + n;
+        t.tie_trip = reinterpret_cast<uint32_t *>(t.dev + 2 * n);
+        e = cudaMemcpyAsync(t.dev, blob.data(), bytes, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) {
+            cudaFree(t.dev);
+            return cuda_fail(e, "uploading the tile table");
         }
         it = g->tiles.emplace(nw, std::move(t)).first;
     }
@@ -270,6 +285,8 @@ kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int stor
     p.lam_in = sp.lam_in;
     p.lam_out = sp.lam_out;
     p.tiles = tiles->dev;
+    p.tie_work = tiles->tie_work;
+    p.tie_trip = tiles->tie_trip;
     p.nw = nw;
     for (int i = 0; i <= nw; ++i) p.tchunk[i] = tiles->tchunk[i];
     (void)dir;

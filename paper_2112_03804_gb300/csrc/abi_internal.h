@@ -46,7 +46,9 @@ struct kps_game {
     size_t stage_in_bytes = 0, stage_out_bytes = 0;
     // tie-aligned tile lists on the device, per warp count
     struct Tiles {
-        int2 *dev = nullptr;
+        int2 *dev = nullptr;          // tile list, then tie work, then tie entries (one allocation)
+        int2 *tie_work = nullptr;
+        uint32_t *tie_trip = nullptr;
         std::vector<int2> host;
         std::vector<int> tchunk;
     };

@@ -102,6 +102,8 @@ kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t str
         p.lam_in = dir == 0 ? l2 : l1;
         p.lam_out = dir == 0 ? l1 : l2;
         p.tiles = t->dev;
+        p.tie_work = t->tie_work;
+        p.tie_trip = t->tie_trip;
         p.nw = nw;
         for (int k = 0; k <= nw; ++k) p.tchunk[k] = t->tchunk[k];
         nc = std::max(nc, p.nc);

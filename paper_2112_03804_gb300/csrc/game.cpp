@@ -347,6 +347,29 @@ std::vector<std::pair<int, int>> tie_tiles(const HostGame &g, int parts, int til
     return tiles;
 }
 
+void tie_work(const HostGame &g, const std::vector<std::pair<int, int>> &tiles, std::vector<std::pair<int, int>> &work,
+              std::vector<uint32_t> &trip) {
+    work.assign(tiles.size(), std::make_pair(0, 0));
+    trip.clear();
+    for (size_t t = 0; t < tiles.size(); ++t) {
+        const int s0 = tiles[t].first, len = tiles[t].second;
+        const int first = (int)trip.size();
+        for (int q = s0; q < s0 + len; ++q) {
+            if (g.group_hi[q] == g.group_lo[q]) continue;
+            const int qa = g.hand_slots[2 * q], qb = g.hand_slots[2 * q + 1];
+            for (int r = g.group_lo[q]; r <= g.group_hi[q]; ++r) {
+                if (r == q) continue;
+                const int ra = g.hand_slots[2 * r], rb = g.hand_slots[2 * r + 1];
+                bool share = qa == ra;
+                if (g.k == 2) share = share || qa == rb || qb == ra || qb == rb;
+                if (share) continue;
+                trip.push_back((uint32_t)(q - s0) | ((uint32_t)(r - s0) << 5) | ((uint32_t)(r > q) << 10));
+            }
+        }
+        work[t] = std::make_pair(first, (int)trip.size() - first);
+    }
+}
+
 // Sizes of Technique B, counted from the structure of its factors:
 //   Ahat = -(Lambda1 Hx Lambda2) (x) F,  U = [Lambda1 (x) I | lambda1 (x) I],
 //   M = diag(D (x) I, I),  V = [(Lambda2 Y^T) (x) S^T | lambda2 (x) F^T],

@@ -93,4 +93,11 @@ std::vector<int> chunk_bounds(const HostGame &g, int parts);
 std::vector<std::pair<int, int>> tie_tiles(const HostGame &g, int parts, int tile,
                                            std::vector<int> &tchunk);
 
+// Tie work of a tile list: for every tile, the ordered pairs (q, r), q != r,
+// of compatible hands (no shared card) in one tie group, packed as
+// q | r << 5 | (r > q) << 10 with q, r offsets in the tile (groups never
+// straddle a tile).  work[t] = (first entry, count).
+void tie_work(const HostGame &g, const std::vector<std::pair<int, int>> &tiles, std::vector<std::pair<int, int>> &work,
+              std::vector<uint32_t> &trip);
+
 }  // namespace kps

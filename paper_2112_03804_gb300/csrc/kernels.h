@@ -62,6 +62,12 @@ struct FastParams {
     const int2 *tiles;           // (start, length) of every tile, chunk after chunk
     int nw;
     int tchunk[kMaxWarps + 1];   // chunk k owns tiles [tchunk[k], tchunk[k+1])
+    // Tie work of every tile (tensor-memory kernels): tie_work[t] = (first,
+    // count) of its entries in tie_trip, one per ordered pair (q, r) of
+    // compatible hands of one tie group: q | r << 5 | (r > q) << 10, with q,
+    // r offsets in the tile.
+    const int2 *tie_work;
+    const uint32_t *tie_trip;
 };
 
 size_t fast_smem_bytes(int storage, int nc, int nw);

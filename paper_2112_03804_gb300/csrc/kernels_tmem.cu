@@ -129,6 +129,7 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
     float2 *R = reinterpret_cast<float2 *>(mine);            // [card][32]: {v running, w total}
     float2 *stage = R + (size_t)nc * 32;                     // [hand][kPitch]: lambda_in * {x_f, x_s}
     float *ptile = reinterpret_cast<float *>(stage + 32 * kPitch);   // [hand][kPitch]
+    const float *st1v = reinterpret_cast<const float *>(stage);      // single-width stage
     const S *vin = static_cast<const S *>(p.vin);
     S *vout = static_cast<S *>(p.vout);
     const float *lam_in = static_cast<const float *>(p.lam_in);
@@ -177,85 +178,143 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
     if (tb < te) fetch(tb);
     for (int t = tb; t < te; ++t) {
         const int2 tl = p.tiles[t];
-        const int t0 = tl.x, len = tl.y;
+        const int t0 = tl.x;
         const float lin = lin_n;
         const uint32_t hreg = h_n;
+        float r[32];
+        if constexpr (KIND == kKindFS) {
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) stage[lane * kPitch + jj] = make_float2(lin * xf[jj], lin * xs[jj]);
-        __syncwarp();
-        if (t + 1 < te) fetch(t + 1);
-        for (int i = 0; i < len;) {
-            const uint32_t h1 = __shfl_sync(kFull, hreg, i);
-            const uint32_t h2 = __shfl_sync(kFull, hreg, min(i + 1, 31));
-            const int a1 = h1 & 63, b1 = (h1 >> 6) & 63;
-            const float2 x1 = stage[i * kPitch + lane];
-            const float u1 = HF ? fco * x1.x : 0.f, v1 = HS ? sco * x1.y : 0.f, w1 = u1 - v1;
-            if ((h1 & (1u << 15)) && i + 1 < len) {
-                // the next hand shares no card: both hands' loads are independent
-                const int a2 = h2 & 63, b2 = (h2 >> 6) & 63;
-                const float2 x2 = stage[(i + 1) * kPitch + lane];
-                const float u2 = HF ? fco * x2.x : 0.f, v2 = HS ? sco * x2.y : 0.f, w2 = u2 - v2;
-                const float2 ra1 = R[a1 * 32 + lane], ra2 = R[a2 * 32 + lane];
-                float2 rb1 = make_float2(0.f, 0.f), rb2 = make_float2(0.f, 0.f);
-                if (K2 == 2) {
-                    rb1 = R[b1 * 32 + lane];
-                    rb2 = R[b2 * 32 + lane];
+            for (int jj = 0; jj < 32; ++jj) stage[lane * kPitch + jj] = make_float2(lin * xf[jj], lin * xs[jj]);
+            __syncwarp();
+            if (t + 1 < te) fetch(t + 1);
+            // Two hands per step, the whole 32-hand tile unrolled: hands past the
+            // tile's end have zero input and add nothing.  Each half tile's inputs
+            // and hand records are read into registers before its scan (so no
+            // staged value waits behind a per-card store); all four per-card
+            // loads of a pair are issued together; when the second hand holds a
+            // card of the first, its loaded sums get the first hand's update in
+            // registers, and its store (the later one) leaves the combined value.
+            const float2 *st_l = stage + lane;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float2 xh[16];
+                uint32_t hh[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    xh[k] = st_l[(16 * half + k) * kPitch];
+                    hh[k] = __shfl_sync(kFull, hreg, 16 * half + k);
                 }
-                const float g1 = Gv + v1;
-                ptile[i * kPitch + lane] = (K2 == 2 ? w1 : 0.f) + (HS ? 2.f * (Gv - ra1.x - rb1.x) : 0.f);
-                ptile[(i + 1) * kPitch + lane] = (K2 == 2 ? w2 : 0.f) + (HS ? 2.f * (g1 - ra2.x - rb2.x) : 0.f);
-                R[a1 * 32 + lane] = make_float2(ra1.x + v1, ra1.y + w1);
-                R[a2 * 32 + lane] = make_float2(ra2.x + v2, ra2.y + w2);
-                if (K2 == 2) {
-                    R[b1 * 32 + lane] = make_float2(rb1.x + v1, rb1.y + w1);
-                    R[b2 * 32 + lane] = make_float2(rb2.x + v2, rb2.y + w2);
+#pragma unroll
+                for (int k = 0; k < 16; k += 2) {
+                    const int i = 16 * half + k;
+                    const uint32_t h1 = hh[k], h2 = hh[k + 1];
+                    const int a1 = h1 & 63, b1 = (h1 >> 6) & 63, a2 = h2 & 63, b2 = (h2 >> 6) & 63;
+                    const float2 x1 = xh[k], x2 = xh[k + 1];
+                    const float u1 = HF ? fco * x1.x : 0.f, v1 = HS ? sco * x1.y : 0.f, w1 = u1 - v1;
+                    const float u2 = HF ? fco * x2.x : 0.f, v2 = HS ? sco * x2.y : 0.f, w2 = u2 - v2;
+                    float2 ra1 = R[a1 * 32 + lane], ra2 = R[a2 * 32 + lane];
+                    float2 rb1 = make_float2(0.f, 0.f), rb2 = make_float2(0.f, 0.f);
+                    if (K2 == 2) {
+                        rb1 = R[b1 * 32 + lane];
+                        rb2 = R[b2 * 32 + lane];
+                        const bool sa = a2 == a1 || a2 == b1, sb = b2 == a1 || b2 == b1;
+                        ra2.x += sa ? v1 : 0.f;
+                        ra2.y += sa ? w1 : 0.f;
+                        rb2.x += sb ? v1 : 0.f;
+                        rb2.y += sb ? w1 : 0.f;
+                    } else {
+                        const bool sa = a2 == a1;
+                        ra2.x += sa ? v1 : 0.f;
+                        ra2.y += sa ? w1 : 0.f;
+                    }
+                    const float g1 = Gv + v1;
+                    r[i] = (K2 == 2 ? w1 : 0.f) + (HS ? 2.f * (Gv - ra1.x - rb1.x) : 0.f);
+                    r[i + 1] = (K2 == 2 ? w2 : 0.f) + (HS ? 2.f * (g1 - ra2.x - rb2.x) : 0.f);
+                    R[a1 * 32 + lane] = make_float2(ra1.x + v1, ra1.y + w1);
+                    if (K2 == 2) R[b1 * 32 + lane] = make_float2(rb1.x + v1, rb1.y + w1);
+                    R[a2 * 32 + lane] = make_float2(ra2.x + v2, ra2.y + w2);
+                    if (K2 == 2) R[b2 * 32 + lane] = make_float2(rb2.x + v2, rb2.y + w2);
+                    Gv = g1 + v2;
+                    Gw = (Gw + w1) + w2;
                 }
-                Gv = g1 + v2;
-                Gw = (Gw + w1) + w2;
-                i += 2;
-            } else {
-                const float2 ra1 = R[a1 * 32 + lane];
-                const float2 rb1 = K2 == 2 ? R[b1 * 32 + lane] : make_float2(0.f, 0.f);
-                ptile[i * kPitch + lane] = (K2 == 2 ? w1 : 0.f) + (HS ? 2.f * (Gv - ra1.x - rb1.x) : 0.f);
-                R[a1 * 32 + lane] = make_float2(ra1.x + v1, ra1.y + w1);
-                if (K2 == 2) R[b1 * 32 + lane] = make_float2(rb1.x + v1, rb1.y + w1);
-                Gv += v1;
-                Gw += w1;
-                i += 1;
+            }
+        } else {
+            // One running value per card (the fold total of fold-only columns,
+            // the showdown mass of showdown-only ones, whose fold total is its
+            // negative) and one staged input per hand: half the shared-memory
+            // traffic of columns with both terminals.
+            float *R1 = reinterpret_cast<float *>(mine);
+            float *st1 = reinterpret_cast<float *>(stage);
+            const float cof = HF ? fco : sco;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) st1[lane * kPitch + jj] = lin * (HF ? xf[jj] : xs[jj]);
+            __syncwarp();
+            if (t + 1 < te) fetch(t + 1);
+            const float *sl = st1 + lane;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float xh[16];
+                uint32_t hh[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    xh[k] = sl[(16 * half + k) * kPitch];
+                    hh[k] = __shfl_sync(kFull, hreg, 16 * half + k);
+                }
+#pragma unroll
+                for (int k = 0; k < 16; k += 2) {
+                    const int i = 16 * half + k;
+                    const uint32_t h1 = hh[k], h2 = hh[k + 1];
+                    const int a1 = h1 & 63, b1 = (h1 >> 6) & 63, a2 = h2 & 63, b2 = (h2 >> 6) & 63;
+                    const float c1 = cof * xh[k], c2 = cof * xh[k + 1];
+                    float ra1 = R1[a1 * 32 + lane], ra2 = R1[a2 * 32 + lane], rb1 = 0.f, rb2 = 0.f;
+                    if (K2 == 2) {
+                        rb1 = R1[b1 * 32 + lane];
+                        rb2 = R1[b2 * 32 + lane];
+                        ra2 += (a2 == a1 || a2 == b1) ? c1 : 0.f;
+                        rb2 += (b2 == a1 || b2 == b1) ? c1 : 0.f;
+                    } else {
+                        ra2 += a2 == a1 ? c1 : 0.f;
+                    }
+                    if (HS) {
+                        // w = -v for a showdown-only column
+                        const float g1 = Gv + c1;
+                        r[i] = (K2 == 2 ? -c1 : 0.f) + 2.f * (Gv - ra1 - rb1);
+                        r[i + 1] = (K2 == 2 ? -c2 : 0.f) + 2.f * (g1 - ra2 - rb2);
+                        Gv = g1 + c2;
+                    } else {
+                        r[i] = K2 == 2 ? c1 : 0.f;
+                        r[i + 1] = K2 == 2 ? c2 : 0.f;
+                        Gw = (Gw + c1) + c2;
+                    }
+                    R1[a1 * 32 + lane] = ra1 + c1;
+                    if (K2 == 2) R1[b1 * 32 + lane] = rb1 + c1;
+                    R1[a2 * 32 + lane] = ra2 + c2;
+                    if (K2 == 2) R1[b2 * 32 + lane] = rb2 + c2;
+                }
             }
         }
         // Tie groups (never split across a tile): the scan counted earlier
         // members as weaker; the exact equal-strength term adds the later
-        // compatible members and removes the earlier ones.
+        // compatible members and removes the earlier ones.  The tile's
+        // compatible tied pairs come from a table; their terms are summed per
+        // hand in the (idle) partial tile, then added to the registers.
         if (HS) {
-            uint32_t last = __ballot_sync(kFull, lane < len && (hreg & (1u << 13)) != 0u);
-            while (last) {
-                const int i = __ffs(last) - 1;
-                last &= last - 1;
-                const uint32_t hi = __shfl_sync(kFull, hreg, i);
-                const int g0 = i - (int)(hi >> 16);
-                for (int q = g0; q <= i; ++q) {
-                    const uint32_t hq = __shfl_sync(kFull, hreg, q);
-                    float corr = 0.f;
-                    for (int r = g0; r <= i; ++r) {
-                        const uint32_t hr = __shfl_sync(kFull, hreg, r);
-                        if (r == q) continue;
-                        const int qa = hq & 63, qb = (hq >> 6) & 63, ra = hr & 63, rb = (hr >> 6) & 63;
-                        bool share = qa == ra;
-                        if (K2 == 2) share = share || qa == rb || qb == ra || qb == rb;
-                        if (share) continue;
-                        const float vr = sco * stage[r * kPitch + lane].y;
-                        corr += r > q ? vr : -vr;
-                    }
-                    ptile[q * kPitch + lane] += corr;
+            const int2 tw = p.tie_work[t];
+            if (tw.y > 0) {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) ptile[k * kPitch + lane] = 0.f;
+                for (int e = 0; e < tw.y; ++e) {
+                    const uint32_t tr = __ldg(&p.tie_trip[tw.x + e]);
+                    const int q = tr & 31, rr = (tr >> 5) & 31;
+                    const float vr = sco * (KIND == kKindFS ? stage[rr * kPitch + lane].y : st1v[rr * kPitch + lane]);
+                    ptile[q * kPitch + lane] += (tr >> 10) & 1u ? vr : -vr;
                 }
+#pragma unroll
+                for (int k = 0; k < 32; ++k) r[k] += ptile[k * kPitch + lane];
             }
         }
-        __syncwarp();
-        // the tile's partial results to tensor memory (lane = column)
-        float r[32];
-#pragma unroll
-        for (int k = 0; k < 32; ++k) r[k] = ptile[k * kPitch + lane];
+        // the tile's partial results to tensor memory (lane = column); the
+        // columns past the tile's end are rewritten by the next tile
         tm_st32(treg + (uint32_t)(t0 - cstart), r);
         __syncwarp();
     }
@@ -273,9 +332,16 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         for (int k = 0; k < kMaxWarps; ++k) {
             tot[k] = run[k] = 0.f;
             if (k < nw) {
-                const float2 s2 = reinterpret_cast<const float2 *>(wbase + (size_t)k * tm_warp_floats(nc))[c * 32 + lane];
-                run[k] = HS ? s2.x : 0.f;
-                tot[k] = HF ? s2.y : -s2.x;
+                const float *Rk = wbase + (size_t)k * tm_warp_floats(nc);
+                if (KIND == kKindFS) {
+                    const float2 s2 = reinterpret_cast<const float2 *>(Rk)[c * 32 + lane];
+                    run[k] = s2.x;
+                    tot[k] = s2.y;
+                } else {
+                    const float s1 = Rk[c * 32 + lane];
+                    run[k] = HS ? s1 : 0.f;
+                    tot[k] = HF ? s1 : -s1;
+                }
             }
         }
         float pw = 0.f;
