@@ -99,11 +99,14 @@ __device__ __forceinline__ void tm_ld32(uint32_t taddr, float *r) {
         : "r"(taddr));
 }
 
-// Shared memory: header then, per warp, state [nc][32] float2,
-// stage [32][kPitch] float2 and a [32][kPitch] float tile.
-__host__ __device__ inline size_t tm_header_bytes(int nw) {
+// Shared memory: header (columns, coefficients, per-warp sums, the tensor-
+// memory slot, per-warp tile descriptors) then, per warp, state [nc][32]
+// float2, stage [32][kPitch] float2 and a [32][kPitch] float tile.
+constexpr int kTlCache = 16;       // tile descriptors of a chunk kept in shared memory
+__host__ __device__ inline size_t tm_tls_offset(int nw) {
     return (32 * sizeof(Col) + (2 * 32 + (size_t)nw * 3 * 32) * sizeof(float) + 16 + 15) & ~(size_t)15;
 }
+__host__ __device__ inline size_t tm_header_bytes(int nw) { return tm_tls_offset(nw) + (size_t)nw * kTlCache * 8; }
 __host__ __device__ inline size_t tm_warp_floats(int nc) { return 2 * (size_t)nc * 32 + 3 * 32 * kPitch; }
 
 struct Cta {
@@ -137,6 +140,7 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
     const long long istride = (long long)p.n_in * hs, ostride = (long long)p.n_out * hs;
     const float fco = fco_s[lane], sco = sco_s[lane];
     const Col c0i = ci[0];
+    int2 *tls = reinterpret_cast<int2 *>(smem + tm_tls_offset(nw)) + warp * kTlCache;
     // this warp's tensor-memory lanes (= its 32 columns) and column region
     const uint32_t treg = cta.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * kRegion);
 
@@ -149,6 +153,7 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
     float xf[32], xs[32];
     float lin_n = 0.f;
     uint32_t h_n = 0u;
+    int2 tw_n = make_int2(0, 0);
     // next tile's inputs, lane = hand, one register per column
     auto fetch = [&](int t) {
         const int2 tl = p.tiles[t];
@@ -156,6 +161,7 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         const bool pin = lane < tl.y;
         lin_n = pin ? lam_in[pos] : 0.f;
         h_n = pin ? __ldg(&p.hinfo[pos]) : 0u;
+        if (HS) tw_n = p.tie_work[t];
         if (uni) {
             const S *fb = vin + c0i.in_off + pos + c0i.foff;
             const S *sb = vin + c0i.in_off + pos + c0i.soff;
@@ -181,6 +187,8 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         const int t0 = tl.x;
         const float lin = lin_n;
         const uint32_t hreg = h_n;
+        const int2 tw = tw_n;
+        if (lane == 0 && t - tb < kTlCache) tls[t - tb] = tl;
         float r[32];
         if constexpr (KIND == kKindFS) {
 #pragma unroll
@@ -299,7 +307,6 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         // compatible tied pairs come from a table; their terms are summed per
         // hand in the (idle) partial tile, then added to the registers.
         if (HS) {
-            const int2 tw = p.tie_work[t];
             if (tw.y > 0) {
 #pragma unroll
                 for (int k = 0; k < 32; ++k) ptile[k * kPitch + lane] = 0.f;
@@ -372,33 +379,48 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
     // write it out with coalesced stores (lane = hand)
     const float *Z = mine + 2 * (size_t)nc * 32 + lane;
     const float base = sums[(warp * 3 + 2) * 32 + lane];
+    // the next tile's descriptor (shared memory for the first kTlCache tiles
+    // of the chunk), hand records and output weights are loaded while the
+    // current tile is finished
+    int2 tl_n = make_int2(0, 0);
+    uint32_t hq_n = 0u;
+    float lo_n = 0.f;
+    auto pre3 = [&](int t) {
+        tl_n = t - tb < kTlCache ? tls[t - tb] : p.tiles[t];
+        const int pos = tl_n.x + lane;
+        const bool pin = lane < tl_n.y;
+        hq_n = pin ? __ldg(&p.hinfo[pos]) : 0u;
+        lo_n = pin ? lam_out[pos] : 0.f;
+    };
+    if (tb < te) pre3(tb);
     for (int t = tb; t < te; ++t) {
-        const int2 tl = p.tiles[t];
+        const int2 tl = tl_n;
+        const uint32_t hq = hq_n;
+        const float lo = lo_n;
         const int t0 = tl.x, len = tl.y;
         const int pos = t0 + lane;
         const bool pin = lane < len;
-        const uint32_t hq = pin ? __ldg(&p.hinfo[pos]) : 0u;
-        const float lo = pin ? lam_out[pos] : 0.f;
         float r[32];
         tm_ld32(treg + (uint32_t)(t0 - cstart), r);
+        if (t + 1 < te) pre3(t + 1);
         tm_wait_ld();
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
             const uint32_t h = __shfl_sync(kFull, hq, k);
-            const float l = __shfl_sync(kFull, lo, k);
             float val = r[k] + base - Z[(h & 63) * 32];
             if (K2 == 2) val -= Z[((h >> 6) & 63) * 32];
-            ptile[k * kPitch + lane] = l * val;
+            ptile[k * kPitch + lane] = val;
         }
         __syncwarp();
+        // lane = hand: the hand's output weight, then coalesced stores
         if (pin) {
             if (uni) {
                 S *dst = vout + c0i.out_off + pos;
-                for (int jj = 0; jj < nvalid; ++jj) dst[jj * ostride] = Num<S>::conv(ptile[lane * kPitch + jj]);
+                for (int jj = 0; jj < nvalid; ++jj) dst[jj * ostride] = Num<S>::conv(lo * ptile[lane * kPitch + jj]);
             } else {
                 for (int jj = 0; jj < 32; ++jj) {
                     const long long o = ci[jj].out_off;
-                    if (o >= 0) vout[o + pos] = Num<S>::conv(ptile[lane * kPitch + jj]);
+                    if (o >= 0) vout[o + pos] = Num<S>::conv(lo * ptile[lane * kPitch + jj]);
                 }
             }
         }
