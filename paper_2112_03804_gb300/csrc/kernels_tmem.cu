@@ -403,12 +403,20 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         float r[32];
         tm_ld32(treg + (uint32_t)(t0 - cstart), r);
         if (t + 1 < te) pre3(t + 1);
-        tm_wait_ld();
+        // every hand's per-card terms first (no shared-memory load waits
+        // behind a store of the partial tile), then the tile
+        float za[32], zb[32];
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
             const uint32_t h = __shfl_sync(kFull, hq, k);
-            float val = r[k] + base - Z[(h & 63) * 32];
-            if (K2 == 2) val -= Z[((h >> 6) & 63) * 32];
+            za[k] = Z[(h & 63) * 32];
+            zb[k] = K2 == 2 ? Z[((h >> 6) & 63) * 32] : 0.f;
+        }
+        tm_wait_ld();
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            float val = r[k] + base - za[k];
+            if (K2 == 2) val -= zb[k];
             ptile[k * kPitch + lane] = val;
         }
         __syncwarp();
