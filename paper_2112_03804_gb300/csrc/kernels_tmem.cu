@@ -78,24 +78,19 @@ __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;"); }
 __device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;"); }
 
-// 32 consecutive tensor-memory columns of this warp's lanes <-> r[0..31]
-__device__ __forceinline__ void tm_st32(uint32_t taddr, const float *r) {
+// 16 consecutive tensor-memory columns of this warp's lanes <-> r[0..15]
+__device__ __forceinline__ void tm_st16(uint32_t taddr, const float *r) {
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
         "f"(r[0]), "f"(r[1]), "f"(r[2]), "f"(r[3]), "f"(r[4]), "f"(r[5]), "f"(r[6]), "f"(r[7]), "f"(r[8]), "f"(r[9]),
-        "f"(r[10]), "f"(r[11]), "f"(r[12]), "f"(r[13]), "f"(r[14]), "f"(r[15]), "f"(r[16]), "f"(r[17]), "f"(r[18]),
-        "f"(r[19]), "f"(r[20]), "f"(r[21]), "f"(r[22]), "f"(r[23]), "f"(r[24]), "f"(r[25]), "f"(r[26]), "f"(r[27]),
-        "f"(r[28]), "f"(r[29]), "f"(r[30]), "f"(r[31]));
+        "f"(r[10]), "f"(r[11]), "f"(r[12]), "f"(r[13]), "f"(r[14]), "f"(r[15]));
 }
-__device__ __forceinline__ void tm_ld32(uint32_t taddr, float *r) {
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, float *r) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
-        "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]), "=f"(r[8]),
-          "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15]), "=f"(r[16]),
-          "=f"(r[17]), "=f"(r[18]), "=f"(r[19]), "=f"(r[20]), "=f"(r[21]), "=f"(r[22]), "=f"(r[23]), "=f"(r[24]),
-          "=f"(r[25]), "=f"(r[26]), "=f"(r[27]), "=f"(r[28]), "=f"(r[29]), "=f"(r[30]), "=f"(r[31])
+          "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15])
         : "r"(taddr));
 }
 
@@ -189,37 +184,59 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         const uint32_t hreg = h_n;
         const int2 tw = tw_n;
         if (lane == 0 && t - tb < kTlCache) tls[t - tb] = tl;
-        float r[32];
+        // stage the tile (lane = hand), then prefetch the next one
+        float *st1w = reinterpret_cast<float *>(stage);
         if constexpr (KIND == kKindFS) {
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) stage[lane * kPitch + jj] = make_float2(lin * xf[jj], lin * xs[jj]);
-            __syncwarp();
-            if (t + 1 < te) fetch(t + 1);
-            // Two hands per step, the whole 32-hand tile unrolled: hands past the
-            // tile's end have zero input and add nothing.  Each half tile's inputs
-            // and hand records are read into registers before its scan (so no
-            // staged value waits behind a per-card store); all four per-card
-            // loads of a pair are issued together; when the second hand holds a
-            // card of the first, its loaded sums get the first hand's update in
-            // registers, and its store (the later one) leaves the combined value.
-            const float2 *st_l = stage + lane;
+        } else {
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
+            for (int jj = 0; jj < 32; ++jj) st1w[lane * kPitch + jj] = lin * (HF ? xf[jj] : xs[jj]);
+        }
+        __syncwarp();
+        if (t + 1 < te) fetch(t + 1);
+        // Tie groups (never split across a tile): the scan counts earlier
+        // members as weaker; the exact equal-strength term adds the later
+        // compatible members and removes the earlier ones.  The tile's
+        // compatible tied pairs come from a table; their terms (inputs only)
+        // are summed per hand in the idle partial tile and added after the
+        // scan of each half.
+        const bool ties = HS && tw.y > 0;
+        if (ties) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) ptile[k * kPitch + lane] = 0.f;
+            for (int e = 0; e < tw.y; ++e) {
+                const uint32_t tr = __ldg(&p.tie_trip[tw.x + e]);
+                const int q = tr & 31, rr = (tr >> 5) & 31;
+                const float vr = sco * (KIND == kKindFS ? stage[rr * kPitch + lane].y : st1v[rr * kPitch + lane]);
+                ptile[q * kPitch + lane] += (tr >> 10) & 1u ? vr : -vr;
+            }
+        }
+        // The scan, one half tile (16 hands, 8 steps of two hands) at a
+        // time.  Hands past the tile's end have zero input and add nothing.
+        // The half's inputs and hand records are read into registers first
+        // (no staged value waits behind a per-card store); all four per-card
+        // loads of a step are issued together; when the second hand holds a
+        // card of the first, its loaded sums get the first hand's update in
+        // registers, and its store (the later one) leaves the combined value.
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            float r[16];
+            uint32_t hh[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) hh[k] = __shfl_sync(kFull, hreg, 16 * half + k);
+            if constexpr (KIND == kKindFS) {
                 float2 xh[16];
-                uint32_t hh[16];
+                const float2 *st_l = stage + lane + 16 * half * kPitch;
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    xh[k] = st_l[(16 * half + k) * kPitch];
-                    hh[k] = __shfl_sync(kFull, hreg, 16 * half + k);
-                }
+                for (int k = 0; k < 16; ++k) xh[k] = st_l[k * kPitch];
 #pragma unroll
                 for (int k = 0; k < 16; k += 2) {
-                    const int i = 16 * half + k;
                     const uint32_t h1 = hh[k], h2 = hh[k + 1];
                     const int a1 = h1 & 63, b1 = (h1 >> 6) & 63, a2 = h2 & 63, b2 = (h2 >> 6) & 63;
                     const float2 x1 = xh[k], x2 = xh[k + 1];
-                    const float u1 = HF ? fco * x1.x : 0.f, v1 = HS ? sco * x1.y : 0.f, w1 = u1 - v1;
-                    const float u2 = HF ? fco * x2.x : 0.f, v2 = HS ? sco * x2.y : 0.f, w2 = u2 - v2;
+                    const float u1 = fco * x1.x, v1 = sco * x1.y, w1 = u1 - v1;
+                    const float u2 = fco * x2.x, v2 = sco * x2.y, w2 = u2 - v2;
                     float2 ra1 = R[a1 * 32 + lane], ra2 = R[a2 * 32 + lane];
                     float2 rb1 = make_float2(0.f, 0.f), rb2 = make_float2(0.f, 0.f);
                     if (K2 == 2) {
@@ -236,8 +253,8 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
                         ra2.y += sa ? w1 : 0.f;
                     }
                     const float g1 = Gv + v1;
-                    r[i] = (K2 == 2 ? w1 : 0.f) + (HS ? 2.f * (Gv - ra1.x - rb1.x) : 0.f);
-                    r[i + 1] = (K2 == 2 ? w2 : 0.f) + (HS ? 2.f * (g1 - ra2.x - rb2.x) : 0.f);
+                    r[k] = (K2 == 2 ? w1 : 0.f) + 2.f * (Gv - ra1.x - rb1.x);
+                    r[k + 1] = (K2 == 2 ? w2 : 0.f) + 2.f * (g1 - ra2.x - rb2.x);
                     R[a1 * 32 + lane] = make_float2(ra1.x + v1, ra1.y + w1);
                     if (K2 == 2) R[b1 * 32 + lane] = make_float2(rb1.x + v1, rb1.y + w1);
                     R[a2 * 32 + lane] = make_float2(ra2.x + v2, ra2.y + w2);
@@ -245,32 +262,18 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
                     Gv = g1 + v2;
                     Gw = (Gw + w1) + w2;
                 }
-            }
-        } else {
-            // One running value per card (the fold total of fold-only columns,
-            // the showdown mass of showdown-only ones, whose fold total is its
-            // negative) and one staged input per hand: half the shared-memory
-            // traffic of columns with both terminals.
-            float *R1 = reinterpret_cast<float *>(mine);
-            float *st1 = reinterpret_cast<float *>(stage);
-            const float cof = HF ? fco : sco;
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) st1[lane * kPitch + jj] = lin * (HF ? xf[jj] : xs[jj]);
-            __syncwarp();
-            if (t + 1 < te) fetch(t + 1);
-            const float *sl = st1 + lane;
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
+            } else {
+                // One running value per card (the fold total of fold-only
+                // columns, the showdown mass of showdown-only ones, whose fold
+                // total is its negative): half the shared-memory traffic.
+                float *R1 = reinterpret_cast<float *>(mine);
+                const float cof = HF ? fco : sco;
                 float xh[16];
-                uint32_t hh[16];
+                const float *sl = st1v + lane + 16 * half * kPitch;
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    xh[k] = sl[(16 * half + k) * kPitch];
-                    hh[k] = __shfl_sync(kFull, hreg, 16 * half + k);
-                }
+                for (int k = 0; k < 16; ++k) xh[k] = sl[k * kPitch];
 #pragma unroll
                 for (int k = 0; k < 16; k += 2) {
-                    const int i = 16 * half + k;
                     const uint32_t h1 = hh[k], h2 = hh[k + 1];
                     const int a1 = h1 & 63, b1 = (h1 >> 6) & 63, a2 = h2 & 63, b2 = (h2 >> 6) & 63;
                     const float c1 = cof * xh[k], c2 = cof * xh[k + 1];
@@ -286,12 +289,12 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
                     if (HS) {
                         // w = -v for a showdown-only column
                         const float g1 = Gv + c1;
-                        r[i] = (K2 == 2 ? -c1 : 0.f) + 2.f * (Gv - ra1 - rb1);
-                        r[i + 1] = (K2 == 2 ? -c2 : 0.f) + 2.f * (g1 - ra2 - rb2);
+                        r[k] = (K2 == 2 ? -c1 : 0.f) + 2.f * (Gv - ra1 - rb1);
+                        r[k + 1] = (K2 == 2 ? -c2 : 0.f) + 2.f * (g1 - ra2 - rb2);
                         Gv = g1 + c2;
                     } else {
-                        r[i] = K2 == 2 ? c1 : 0.f;
-                        r[i + 1] = K2 == 2 ? c2 : 0.f;
+                        r[k] = K2 == 2 ? c1 : 0.f;
+                        r[k + 1] = K2 == 2 ? c2 : 0.f;
                         Gw = (Gw + c1) + c2;
                     }
                     R1[a1 * 32 + lane] = ra1 + c1;
@@ -300,29 +303,14 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
                     if (K2 == 2) R1[b2 * 32 + lane] = rb2 + c2;
                 }
             }
-        }
-        // Tie groups (never split across a tile): the scan counted earlier
-        // members as weaker; the exact equal-strength term adds the later
-        // compatible members and removes the earlier ones.  The tile's
-        // compatible tied pairs come from a table; their terms are summed per
-        // hand in the (idle) partial tile, then added to the registers.
-        if (HS) {
-            if (tw.y > 0) {
+            if (ties) {
 #pragma unroll
-                for (int k = 0; k < 32; ++k) ptile[k * kPitch + lane] = 0.f;
-                for (int e = 0; e < tw.y; ++e) {
-                    const uint32_t tr = __ldg(&p.tie_trip[tw.x + e]);
-                    const int q = tr & 31, rr = (tr >> 5) & 31;
-                    const float vr = sco * (KIND == kKindFS ? stage[rr * kPitch + lane].y : st1v[rr * kPitch + lane]);
-                    ptile[q * kPitch + lane] += (tr >> 10) & 1u ? vr : -vr;
-                }
-#pragma unroll
-                for (int k = 0; k < 32; ++k) r[k] += ptile[k * kPitch + lane];
+                for (int k = 0; k < 16; ++k) r[k] += ptile[(16 * half + k) * kPitch + lane];
             }
+            // the half's partial results to tensor memory (lane = column);
+            // columns past the tile's end are rewritten by the next tile
+            tm_st16(treg + (uint32_t)(t0 - cstart + 16 * half), r);
         }
-        // the tile's partial results to tensor memory (lane = column); the
-        // columns past the tile's end are rewritten by the next tile
-        tm_st32(treg + (uint32_t)(t0 - cstart), r);
         __syncwarp();
     }
     tm_wait_st();
@@ -400,24 +388,27 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         const int t0 = tl.x, len = tl.y;
         const int pos = t0 + lane;
         const bool pin = lane < len;
-        float r[32];
-        tm_ld32(treg + (uint32_t)(t0 - cstart), r);
         if (t + 1 < te) pre3(t + 1);
-        // every hand's per-card terms first (no shared-memory load waits
-        // behind a store of the partial tile), then the tile
-        float za[32], zb[32];
+        // per half tile: partial results from tensor memory, every hand's
+        // per-card terms (loaded before any store of the partial tile), the
+        // finished values into the partial tile
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            float r[16], za[16], zb[16];
+            tm_ld16(treg + (uint32_t)(t0 - cstart + 16 * half), r);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            const uint32_t h = __shfl_sync(kFull, hq, k);
-            za[k] = Z[(h & 63) * 32];
-            zb[k] = K2 == 2 ? Z[((h >> 6) & 63) * 32] : 0.f;
-        }
-        tm_wait_ld();
+            for (int k = 0; k < 16; ++k) {
+                const uint32_t h = __shfl_sync(kFull, hq, 16 * half + k);
+                za[k] = Z[(h & 63) * 32];
+                zb[k] = K2 == 2 ? Z[((h >> 6) & 63) * 32] : 0.f;
+            }
+            tm_wait_ld();
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            float val = r[k] + base - za[k];
-            if (K2 == 2) val -= zb[k];
-            ptile[k * kPitch + lane] = val;
+            for (int k = 0; k < 16; ++k) {
+                float val = r[k] + base - za[k];
+                if (K2 == 2) val -= zb[k];
+                ptile[(16 * half + k) * kPitch + lane] = val;
+            }
         }
         __syncwarp();
         // lane = hand: the hand's output weight, then coalesced stores
