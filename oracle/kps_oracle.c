@@ -946,6 +946,124 @@ static void uniform_beh(const orc_game *g, int p, double *beh)
     }
 }
 
+/* DCFR's regret step for player p, bottom-up like bottom_up: with the
+ * instantaneous regret q - v added, a cumulative regret is multiplied by
+ * dpos when positive and by dneg otherwise. */
+static void bottom_up_dcfr(const orc_game *g, int p, const double *gv, const double *beh, double *regret,
+                           double dpos, double dneg)
+{
+    int H = g->H, n = g->n[p];
+    double *cv = (double *)calloc((size_t)n * H, sizeof(double));
+    double *q = (double *)malloc((size_t)MAXA * H * sizeof(double));
+    for (int i = g->np[p] - 1; i >= 0; i--) {
+        const onode *nd = &g->nodes[g->pn_tree[p][i]];
+        int s0 = nd->seq[0], na = nd->nact;
+        for (int a = 0; a < na; a++)
+            for (int h = 0; h < H; h++)
+                q[a * H + h] = gv[(size_t)(s0 + a) * H + h] + cv[(size_t)(s0 + a) * H + h];
+        int par = nd->last_seq[p];
+        for (int h = 0; h < H; h++) {
+            double v = 0.0;
+            for (int a = 0; a < na; a++) v += beh[(size_t)(s0 + a) * H + h] * q[a * H + h];
+            for (int a = 0; a < na; a++) {
+                double r = regret[(size_t)(s0 + a) * H + h] + q[a * H + h] - v;
+                regret[(size_t)(s0 + a) * H + h] = r * (r > 0.0 ? dpos : dneg);
+            }
+            if (par >= 0) cv[(size_t)par * H + h] += v;
+        }
+    }
+    free(cv);
+    free(q);
+}
+
+/* Regret matching on the positive parts of possibly negative regrets. */
+static void regret_match_pos(const orc_game *g, int p, const double *regret, double *beh, double theta)
+{
+    int H = g->H;
+    for (int i = 0; i < g->np[p]; i++) {
+        const onode *nd = &g->nodes[g->pn_tree[p][i]];
+        int s0 = nd->seq[0], na = nd->nact;
+        for (int h = 0; h < H; h++) {
+            double s = 0.0;
+            for (int a = 0; a < na; a++) {
+                double r = regret[(size_t)(s0 + a) * H + h];
+                s += r > 0.0 ? r : 0.0;
+            }
+            for (int a = 0; a < na; a++) {
+                double r = regret[(size_t)(s0 + a) * H + h];
+                beh[(size_t)(s0 + a) * H + h] = s > theta ? (r > 0.0 ? r : 0.0) / s : 1.0 / na;
+            }
+        }
+    }
+}
+
+double orc_dcfr(const orc_game *g, int iters, double alpha, double beta, double gamma,
+                double *avg_beh1, double *avg_beh2, double *trace, int trace_every)
+{
+    int H = g->H, n1 = g->n[0], n2 = g->n[1];
+    size_t N1 = (size_t)n1 * H, N2 = (size_t)n2 * H;
+    double *b1 = (double *)malloc(N1 * sizeof(double)), *b2 = (double *)malloc(N2 * sizeof(double));
+    double *x = (double *)malloc(N1 * sizeof(double)), *y = (double *)malloc(N2 * sizeof(double));
+    double *R1 = (double *)calloc(N1, sizeof(double)), *R2 = (double *)calloc(N2, sizeof(double));
+    double *xs = (double *)calloc(N1, sizeof(double)), *ys = (double *)calloc(N2, sizeof(double));
+    double *g1 = (double *)malloc(N1 * sizeof(double)), *g2 = (double *)malloc(N2 * sizeof(double));
+    double *xa = (double *)malloc(N1 * sizeof(double)), *ya = (double *)malloc(N2 * sizeof(double));
+    uniform_beh(g, 0, b1);
+    uniform_beh(g, 1, b2);
+    orc_seqform(g, 0, b1, x);
+    orc_seqform(g, 1, b2, y);
+    const double th1 = orc_regret_floor(g, 0, ORC_REGRET_EPS), th2 = orc_regret_floor(g, 1, ORC_REGRET_EPS);
+    double wsum = 0.0, expl = 0.0;
+    for (int t = 1; t <= iters; t++) {
+        const double ta = pow((double)t, alpha), tb = pow((double)t, beta), wt = pow((double)t, gamma);
+        const double dpos = ta / (ta + 1.0), dneg = tb / (tb + 1.0);
+        for (size_t i = 0; i < N1; i++) xs[i] += wt * x[i];
+        matvec_one(g, y, g1);
+        bottom_up_dcfr(g, 0, g1, b1, R1, dpos, dneg);
+        regret_match_pos(g, 0, R1, b1, th1);
+        orc_seqform(g, 0, b1, x);
+        for (size_t i = 0; i < N2; i++) ys[i] += wt * y[i];
+        matvec_t_one(g, x, g2);
+        for (size_t i = 0; i < N2; i++) g2[i] = -g2[i];
+        bottom_up_dcfr(g, 1, g2, b2, R2, dpos, dneg);
+        regret_match_pos(g, 1, R2, b2, th2);
+        orc_seqform(g, 1, b2, y);
+        wsum += wt;
+        if (trace) {
+            trace[t - 1] = 0.0;
+            if (trace_every > 0 && t % trace_every == 0) {
+                for (size_t i = 0; i < N1; i++) xa[i] = xs[i] / wsum;
+                for (size_t i = 0; i < N2; i++) ya[i] = ys[i] / wsum;
+                trace[t - 1] = orc_exploitability(g, xa, ya, NULL, NULL);
+            }
+        }
+    }
+    for (size_t i = 0; i < N1; i++) xa[i] = wsum > 0 ? xs[i] / wsum : x[i];
+    for (size_t i = 0; i < N2; i++) ya[i] = wsum > 0 ? ys[i] / wsum : y[i];
+    expl = orc_exploitability(g, xa, ya, NULL, NULL);
+    for (int p = 0; p < 2; p++) {
+        double *dst = p == 0 ? avg_beh1 : avg_beh2;
+        double *src = p == 0 ? xa : ya;
+        if (!dst) continue;
+        for (int s = 0; s < g->n[p]; s++) {
+            int par = g->seq_parent[p][s];
+            for (int h = 0; h < H; h++) {
+                double den = par < 0 ? 1.0 : src[(size_t)par * H + h];
+                dst[(size_t)s * H + h] = den > 0.0 ? src[(size_t)s * H + h] / den : -1.0;
+            }
+        }
+        for (int i = 0; i < g->np[p]; i++) {
+            const onode *nd = &g->nodes[g->pn_tree[p][i]];
+            for (int h = 0; h < H; h++)
+                if (dst[(size_t)nd->seq[0] * H + h] < 0.0)
+                    for (int a = 0; a < nd->nact; a++) dst[(size_t)nd->seq[a] * H + h] = 1.0 / nd->nact;
+        }
+    }
+    free(b1); free(b2); free(x); free(y); free(R1); free(R2); free(xs); free(ys);
+    free(g1); free(g2); free(xa); free(ya);
+    return expl;
+}
+
 double orc_exploitability(const orc_game *g, const double *x, const double *y,
                           double *br1, double *br2)
 {

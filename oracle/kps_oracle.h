@@ -143,6 +143,15 @@ double orc_rmplus_warm(const orc_game *g, int iters, const double *beh1_0, const
                        double kappa, int t0, double *avg_beh1, double *avg_beh2, double *trace,
                        int trace_every);
 
+/* Discounted CFR (the solver the paper runs, Sec. 5; Brown & Sandholm's
+ * DCFR): alternating updates from uniform strategies; on iteration t the
+ * instantaneous regret q - v is added and a cumulative regret is multiplied
+ * by t^alpha / (t^alpha + 1) when positive, t^beta / (t^beta + 1) otherwise;
+ * regret matching on the positive parts (uniform at or below the noise
+ * floor); iteration t's strategy enters the average with weight t^gamma. */
+double orc_dcfr(const orc_game *g, int iters, double alpha, double beta, double gamma,
+                double *avg_beh1, double *avg_beh2, double *trace, int trace_every);
+
 /* Best-response values: br1 = max_x x^T A y, br2 = max_y -x^T A y for
  * sequence-form x [n1][H], y [n2][H].  Returns (br1 + br2)/2/pot0. */
 double orc_exploitability(const orc_game *g, const double *x, const double *y,

@@ -65,6 +65,8 @@ def lib():
         L.orc_regret_floor.restype = C.c_double
         L.orc_rmplus_warm.argtypes = [P, C.c_int, P, P, C.c_double, C.c_int, P, P, P, C.c_int]
         L.orc_rmplus_warm.restype = C.c_double
+        L.orc_dcfr.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, P, P, P, C.c_int]
+        L.orc_dcfr.restype = C.c_double
         L.orc_beta.argtypes = [P]
         L.orc_pot0.restype = C.c_double
         L.orc_pot0.argtypes = [P]
@@ -240,6 +242,14 @@ class OracleGame:
         b2 = None if beh2 is None else np.ascontiguousarray(beh2, dtype=np.float64)
         e = lib().orc_rmplus_warm(self._g, iters, _p(b1), _p(b2), kappa, t0, _p(avg1), _p(avg2), _p(trace),
                                   trace_every)
+        return e, avg1, avg2, trace[:iters]
+
+    def dcfr(self, iters: int, alpha: float = 1.5, beta: float = 0.0, gamma: float = 2.0, trace_every: int = 0):
+        """Discounted CFR from uniform strategies (see orc_dcfr)."""
+        avg1 = np.zeros((self.n1, self.H))
+        avg2 = np.zeros((self.n2, self.H))
+        trace = np.zeros(max(iters, 1))
+        e = lib().orc_dcfr(self._g, iters, alpha, beta, gamma, _p(avg1), _p(avg2), _p(trace), trace_every)
         return e, avg1, avg2, trace[:iters]
 
     def exploitability(self, x: np.ndarray, y: np.ndarray):

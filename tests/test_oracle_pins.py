@@ -275,3 +275,27 @@ def test_kuhn_equilibrium_is_a_fixed_point_of_warm_rmplus():
     e1, c1, c2, _ = g.rmplus_warm(7, b1, b2, kappa=0.0, t0=0)
     e2, d1, d2, _ = g.rmplus(7, b1, b2)
     assert e1 == e2 and np.array_equal(c1, d1) and np.array_equal(c2, d2)
+
+
+def test_dcfr_two_iterations_equal_rmplus_with_linear_weights():
+    """After one iteration DCFR's regrets are (q - v)/2 (both discount
+    factors are 1/2 at t = 1), whose positive parts point the same way as
+    RM+'s max(0, q - v): the second iteration plays the same strategies, so
+    with gamma = 1 the averages after two iterations are RM+'s exactly."""
+    for spec in (synth.kuhn_spec(), synth.micro_spec(seed=3, ranks=4, suits=2, nboard=2)):
+        g = OracleGame(spec)
+        e1, a1, b1, _ = g.dcfr(2, alpha=1.5, beta=0.0, gamma=1.0)
+        e2, a2, b2, _ = g.rmplus(2)
+        assert np.array_equal(a1, a2) and np.array_equal(b1, b2) and e1 == e2
+
+
+def test_dcfr_solves_kuhn():
+    """Kuhn poker: DCFR(1.5, 0, 2) reaches the closed-form value -1/18 and a
+    small exploitability, decreasing along the run."""
+    g = _kuhn()
+    expl, avg1, avg2, tr = g.dcfr(2000, trace_every=500)
+    x, y = g.seqform(0, avg1), g.seqform(1, avg2)
+    assert g.value(x, y) == pytest.approx(-1.0 / 18.0, abs=2e-4)
+    assert 0.0 <= expl < 2e-4
+    pts = tr[499::500]
+    assert np.all(np.diff(pts) <= 1e-12)
