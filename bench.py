@@ -341,10 +341,12 @@ def measure_batch(ngames: int, steps: int, warmup: int, rank: int = 0):
             "l2": "inputs larger than L2" if alg > 2.6e8 else "inputs smaller than L2"}
 
 
-def measure_solver(target: float = 1e-3, block: int = 25, max_iters: int = 4000):
+def measure_solver(target: float = 1e-3, block: int = 10, max_iters: int = 4000):
     """RM+ on the tiny Kronecker game (6 one-card hands) until the FP64
-    exploitability of the averages is below `target` of the pot, per storage
-    type; error against the FP64-storage run at every checkpoint."""
+    exploitability of the averages is below `target` of the pot (checked
+    every `block` iterations), per storage type; error against the
+    FP64-storage run at every checkpoint; Discounted CFR (1.5, 0, 2) in FP32
+    and BF16 storage beside it."""
     import torch
     from paper_2112_03804_gb300 import kps, synth
     spec = synth.tiny_spec()
@@ -353,8 +355,11 @@ def measure_solver(target: float = 1e-3, block: int = 25, max_iters: int = 4000)
     res = {}
     traces = {}
     names = {kps.F64: "f64", kps.F32: "f32", kps.BF16: "bf16", kps.F16: "f16"}
-    for dt in (kps.F64, kps.F32, kps.BF16, kps.F16):
+    runs = [(dt, 0) for dt in (kps.F64, kps.F32, kps.BF16, kps.F16)] + [(kps.F32, 1), (kps.BF16, 1)]
+    for dt, method in runs:
         s = kps.Solver(b, dt)
+        if method == 1:
+            s.set_method(1, 1.5, 0.0, 2.0)
         e = torch.zeros(1, dtype=torch.float64, device="cuda")
         s.step(block)          # capture the graph outside the timed run
         s.reset()
@@ -375,14 +380,15 @@ def measure_solver(target: float = 1e-3, block: int = 25, max_iters: int = 4000)
         ev1.record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        traces[dt] = tr
-        res[names[dt]] = {"iters_to_target": it if tr[-1] < target else None, "final_expl": tr[-1],
-                          "wall_ms": 1e3 * wall, "gpu_ms": ev0.elapsed_time(ev1)}
+        key = names[dt] + ("_dcfr" if method else "")
+        traces[key] = tr
+        res[key] = {"iters_to_target": it if tr[-1] < target else None, "final_expl": tr[-1],
+                    "wall_ms": 1e3 * wall, "gpu_ms": ev0.elapsed_time(ev1)}
         s.close()
-    ref = traces[kps.F64]
-    for dt in (kps.F32, kps.BF16, kps.F16):
-        n = min(len(ref), len(traces[dt]))
-        res[names[dt]]["max_abs_err_vs_f64"] = float(np.max(np.abs(np.array(traces[dt][:n]) - np.array(ref[:n]))))
+    ref = traces["f64"]
+    for key in ("f32", "bf16", "f16"):
+        n = min(len(ref), len(traces[key]))
+        res[key]["max_abs_err_vs_f64"] = float(np.max(np.abs(np.array(traces[key][:n]) - np.array(ref[:n]))))
     return {"game": "tiny Kronecker game: 3 ranks x 2 suits, one card each (6 hands), 7+7 sequences",
             "target_expl_pot": target, "check_every": block, "by_storage": res}
 

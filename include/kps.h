@@ -259,6 +259,14 @@ kps_status kps_solver_reset(kps_solver *solver, const float *beh1, const float *
  * beh2 NULL). */
 kps_status kps_solver_warm_start(kps_solver *solver, const float *beh1, const float *beh2, double kappa,
                                  int32_t t0, void *stream);
+/* Selects the regret update: method 0 = RM+ (the default), method 1 =
+ * Discounted CFR, the solver the paper runs (Sec. 5): on iteration t the
+ * instantaneous regret is added, a cumulative regret is multiplied by
+ * t^alpha/(t^alpha+1) when positive and t^beta/(t^beta+1) otherwise,
+ * regret matching uses positive parts, iteration t enters the average with
+ * weight t^gamma (1.5, 0, 2 are the usual values).  Takes effect at the next
+ * reset / warm start.  Errors: KPS_EINVAL. */
+kps_status kps_solver_set_method(kps_solver *solver, int32_t method, double alpha, double beta, double gamma);
 /* Runs `iters` iterations as one CUDA graph (captured on first use of each
  * count), asynchronous on `stream`. */
 kps_status kps_solver_step(kps_solver *solver, int32_t iters, void *stream);

@@ -38,6 +38,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -99,13 +100,20 @@ __device__ __forceinline__ Where locate(const SolverGame *games, const int *bloc
 // at most the noise floor theta.
 template <typename C>
 __device__ __forceinline__ void regret_match(const C *r, int na, C *b, C theta) {
+    // positive parts (RM+ regrets are never negative; DCFR's may be)
     C sum = C(0);
 #pragma unroll
     for (int a = 0; a < kMaxActions; ++a)
-        if (a < na) sum += r[a];
+        if (a < na) sum += r[a] > C(0) ? r[a] : C(0);
 #pragma unroll
     for (int a = 0; a < kMaxActions; ++a)
-        if (a < na) b[a] = sum > theta ? r[a] / sum : C(1) / C(na);
+        if (a < na) b[a] = sum > theta ? (r[a] > C(0) ? r[a] : C(0)) / sum : C(1) / C(na);
+}
+
+// Weight of iteration t in the average: t (RM+) or t^gamma (DCFR, from the
+// host-computed table).
+__device__ __forceinline__ double avg_weight(long long t, int method, const double *dtab) {
+    return method == 0 ? (double)t : dtab[3 * t + 2];
 }
 
 template <typename S, typename C>
@@ -122,8 +130,11 @@ struct UpdateArgs {
     const float *beh0;       // initial behavioural strategy
     const long long *iter;   // completed iterations
     const long long *init_iter;  // the iteration that plays beh0 (0 = none)
+    const double *wsum;      // sum of the average weights so far
     C kappa;                 // warm start: regrets kappa * V_p * beh0
     C w0;                    // warm start: weight of the initial strategy in the average
+    int method;              // 0 RM+, 1 DCFR
+    const double *dtab;      // DCFR: per iteration t, {t^a/(t^a+1), t^b/(t^b+1), t^g} at 3t
 };
 
 // One RM+ half-iteration of one player (see the file comment).
@@ -138,12 +149,19 @@ __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S,
     const long long base = G.off[p] + w.h;
     const long long t = *u.iter + 1;
     const bool init = t == *u.init_iter;
+    const C wt = C(avg_weight(t, u.method, u.dtab));
+    // DCFR: positive cumulative regrets times t^a / (t^a + 1), others t^b / (t^b + 1)
+    C dpos = C(1), dneg = C(0);
+    if (u.method == 1) {
+        dpos = C(u.dtab[3 * t]);
+        dneg = C(u.dtab[3 * t + 1]);
+    }
     const int4 *nodes = u.nodes + G.node_off[p];
     const int nn = G.nnodes[p];
     const C theta = C(G.theta[p]);
     for (int s = 0; s < n; ++s) {
         const long long i = base + (long long)s * hs;
-        u.xsum[i] += C(t) * C(Cv<S>::ld(u.x + i));
+        u.xsum[i] += wt * C(Cv<S>::ld(u.x + i));
         buf[s * kThreads + tid] = C(0);
     }
     // bottom-up: values and regrets
@@ -173,7 +191,8 @@ __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S,
         for (int a = 0; a < kMaxActions; ++a)
             if (a < na) {
                 const C rn = r[a] + q[a] - v;
-                u.regret[base + (long long)(s0 + a) * hs] = rn > C(0) ? rn : C(0);
+                u.regret[base + (long long)(s0 + a) * hs] =
+                    u.method == 0 ? (rn > C(0) ? rn : C(0)) : rn * (rn > C(0) ? dpos : dneg);
             }
         if (par >= 0) buf[par * kThreads + tid] += v;
     }
@@ -226,7 +245,11 @@ __global__ void __launch_bounds__(kThreads) seqform_kernel(const UpdateArgs<S, C
     }
 }
 
-__global__ void bump_kernel(long long *iter) { *iter += 1; }
+__global__ void bump_kernel(long long *iter, double *wsum, int method, const double *dtab) {
+    const long long t = *iter + 1;
+    *wsum += avg_weight(t, method, dtab);
+    *iter = t;
+}
 
 // FP64 averages: sequence form xsum / sum_t t (the current strategy before
 // any iteration), or behavioural (x[sigma] / x[parent], uniform where the
@@ -238,11 +261,10 @@ __global__ void __launch_bounds__(kThreads) average_kernel(const UpdateArgs<S, C
     if (w.h >= G.H) return;
     const int p = u.player, hs = G.hs;
     const long long base = G.off[p] + w.h;
-    const long long t = *u.iter;
-    const double wsum = 0.5 * (double)t * (double)(t + 1);
+    const double wsum = *u.wsum;
     auto avg = [&](int s) -> double {
         const long long i = base + (long long)s * hs;
-        return t > 0 ? (double)u.xsum[i] / wsum : (double)Cv<S>::ld(u.x + i);
+        return wsum > 0.0 ? (double)u.xsum[i] / wsum : (double)Cv<S>::ld(u.x + i);
     };
     const int4 *nodes = u.nodes + G.node_off[p];
     for (int k = 0; k < G.nnodes[p]; ++k) {
@@ -336,8 +358,13 @@ struct kps_solver {
     double *partial[2] = {nullptr, nullptr};
     long long *iter = nullptr;      // completed iterations (device)
     long long *init_iter = nullptr; // iteration that plays the initial strategy (device)
+    double *wsum = nullptr;         // sum of the average weights (device)
     int has_beh = 0;
     double kappa = 0.0, w0 = 0.0;
+    int method = 0;                 // 0 RM+, 1 DCFR
+    double alpha = 1.5, beta = 0.0, gamma = 2.0;
+    double *dtab = nullptr;         // DCFR factors per iteration (device), 3 per t
+    long long dtab_cap = 0;         // iterations covered
     long long iters_host = 0;
     cudaStream_t cap = nullptr;     // capture stream
     std::map<int, cudaGraphExec_t> graphs;
@@ -364,8 +391,11 @@ UpdateArgs<S, C> make_args(kps_solver *s, int p) {
     u.beh0 = s->beh0[p];
     u.iter = s->iter;
     u.init_iter = s->init_iter;
+    u.wsum = s->wsum;
     u.kappa = C(s->kappa);
     u.w0 = C(s->w0);
+    u.method = s->method;
+    u.dtab = s->dtab;
     return u;
 }
 
@@ -427,7 +457,7 @@ kps_status one_iteration(kps_solver *s, cudaStream_t st) {
     if (r != KPS_OK) return r;
     e = KPS_DISPATCH(s->dt, update_t, s, 1, st);
     if (e != cudaSuccess) return cuda_fail(e, "player-2 update");
-    bump_kernel<<<1, 1, 0, st>>>(s->iter);
+    bump_kernel<<<1, 1, 0, st>>>(s->iter, s->wsum, s->method, s->dtab);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "iteration counter");
     return KPS_OK;
@@ -435,9 +465,40 @@ kps_status one_iteration(kps_solver *s, cudaStream_t st) {
 
 void free_solver(kps_solver *s) {
     for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    if (s->dtab) cudaFree(s->dtab);
     for (void *p : s->allocs) cudaFree(p);
     if (s->cap) cudaStreamDestroy(s->cap);
     delete s;
+}
+
+// DCFR factors for every iteration up to `last` (host std::pow, the same
+// values on every run); a reallocated table invalidates captured graphs.
+kps_status ensure_dtab(kps_solver *s, long long last, cudaStream_t st) {
+    if (s->method != 1 || last < s->dtab_cap) return KPS_OK;
+    long long cap = std::max<long long>(1024, s->dtab_cap);
+    while (cap <= last) cap *= 2;
+    std::vector<double> h(3 * (size_t)cap, 0.0);
+    for (long long t = 1; t < cap; ++t) {
+        const double ta = std::pow((double)t, s->alpha), tb = std::pow((double)t, s->beta);
+        h[3 * t] = ta / (ta + 1.0);
+        h[3 * t + 1] = tb / (tb + 1.0);
+        h[3 * t + 2] = std::pow((double)t, s->gamma);
+    }
+    double *d = nullptr;
+    if (cudaMalloc(&d, h.size() * sizeof(double)) != cudaSuccess) return fail(KPS_ENOMEM, "DCFR table");
+    cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "uploading the DCFR table");
+    }
+    (void)st;
+    cudaDeviceSynchronize();   // work using the old table has finished
+    if (s->dtab) cudaFree(s->dtab);
+    s->dtab = d;
+    s->dtab_cap = cap;
+    for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    s->graphs.clear();
+    return KPS_OK;
 }
 
 }  // namespace
@@ -512,7 +573,7 @@ kps_status kps_solver_create(kps_batch *b, kps_dtype dt, kps_solver **out) {
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
     const size_t o_g = 0, o_bg = al(sizeof(SolverGame) * ng), o_gb = al(o_bg + 4 * block_game.size()),
                  o_nd = al(o_gb + 4 * (size_t)ng), o_it = al(o_nd + sizeof(int4) * std::max<size_t>(1, nodes.size())),
-                 total = al(o_it + 16);
+                 total = al(o_it + 24);
     std::vector<unsigned char> host(total, 0);
     std::memcpy(host.data() + o_g, games.data(), sizeof(SolverGame) * ng);
     std::memcpy(host.data() + o_bg, block_game.data(), 4 * block_game.size());
@@ -533,6 +594,7 @@ kps_status kps_solver_create(kps_batch *b, kps_dtype dt, kps_solver **out) {
     s->nodes = reinterpret_cast<int4 *>(bl + o_nd);
     s->iter = reinterpret_cast<long long *>(bl + o_it);
     s->init_iter = reinterpret_cast<long long *>(bl + o_it + 8);
+    s->wsum = reinterpret_cast<double *>(bl + o_it + 16);
     const size_t es = elem_size(dt);
     for (int p = 0; p < 2; ++p) {
         const size_t len = (size_t)b->off[p].back();
@@ -584,7 +646,13 @@ kps_status kps_solver_warm_start(kps_solver *s, const float *beh1, const float *
     const size_t es = elem_size(s->dt);
     s->has_beh = beh1 ? 1 : 0;
     s->kappa = kappa;
-    s->w0 = 0.5 * (double)t0 * (double)(t0 + 1);
+    double w0 = 0.0;
+    for (int k = 1; k <= t0; ++k) w0 += s->method == 0 ? (double)k : std::pow((double)k, s->gamma);
+    {
+        kps_status r0 = ensure_dtab(s, (long long)t0 + 1, st);
+        if (r0 != KPS_OK) return r0;
+    }
+    s->w0 = w0;
     const long long iter0 = t0, init_iter = beh1 ? (long long)t0 + 1 : 0;
     cudaError_t e = cudaSuccess;
     for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
@@ -599,6 +667,7 @@ kps_status kps_solver_warm_start(kps_solver *s, const float *beh1, const float *
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->iter, &iter0, 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->init_iter, &init_iter, 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->wsum, &s->w0, 8, cudaMemcpyHostToDevice, st);
     // the pageable copies above are staged before they return
     for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = KPS_DISPATCH(s->dt, seqform_t, s, p, st);
     if (e != cudaSuccess) return cuda_fail(e, "starting the solver");
@@ -610,11 +679,36 @@ kps_status kps_solver_reset(kps_solver *s, const float *beh1, const float *beh2,
     return kps_solver_warm_start(s, beh1, beh2, 0.0, 0, stream_ptr);
 }
 
+kps_status kps_solver_set_method(kps_solver *s, int32_t method, double alpha, double beta, double gamma) {
+    if (!s) return fail(KPS_EINVAL, "solver is NULL");
+    if (method != 0 && method != 1) return fail(KPS_EINVAL, "method must be 0 (RM+) or 1 (DCFR)");
+    if (method == 1 && !(std::isfinite(alpha) && std::isfinite(beta) && std::isfinite(gamma) && gamma >= 0.0))
+        return fail(KPS_EINVAL, "DCFR needs finite alpha, beta and gamma >= 0");
+    s->method = method;
+    if (method == 1) {
+        s->alpha = alpha;
+        s->beta = beta;
+        s->gamma = gamma;
+    }
+    if (s->dtab) {
+        cudaDeviceSynchronize();
+        cudaFree(s->dtab);
+    }
+    s->dtab = nullptr;
+    s->dtab_cap = 0;
+    // captured iteration graphs hold the old parameters
+    for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    s->graphs.clear();
+    return KPS_OK;
+}
+
 kps_status kps_solver_step(kps_solver *s, int32_t iters, void *stream_ptr) {
     if (!s) return fail(KPS_EINVAL, "solver is NULL");
     if (iters < 0) return fail(KPS_EINVAL, "iters must be >= 0");
     if (iters == 0) return KPS_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream_ptr);
+    kps_status r0 = ensure_dtab(s, s->iters_host + iters, st);
+    if (r0 != KPS_OK) return r0;
     auto it = s->graphs.find(iters);
     if (it == s->graphs.end()) {
         cudaGraph_t graph = nullptr;

@@ -69,7 +69,7 @@ EXPORTED = ["kps_sparsify", "kps_game_destroy", "kps_game_info", "kps_game_hands
             "kps_batch_create", "kps_batch_destroy", "kps_batch_offsets", "kps_batch_matvec_A",
             "kps_batch_matvec_AT", "kps_batch_tune", "kps_batch_shape_get", "kps_batch_shape_set", "kps_partition",
             "kps_solver_create", "kps_solver_destroy", "kps_solver_reset", "kps_solver_warm_start",
-            "kps_solver_step",
+            "kps_solver_set_method", "kps_solver_step",
             "kps_solver_iterations", "kps_solver_average", "kps_solver_strategy", "kps_solver_exploitability",
             "kps_warm_num_queries", "kps_warm_features", "kps_warm_targets", "kps_warm_scatter",
             "kps_warm_predict",
@@ -116,6 +116,7 @@ def lib():
         L.kps_solver_exploitability.argtypes = [P, P, P, P, P]
         L.kps_solver_strategy.argtypes = [P, P, P, P]
         L.kps_solver_warm_start.argtypes = [P, P, P, C.c_double, C.c_int32, P]
+        L.kps_solver_set_method.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_double]
         L.kps_warm_num_queries.argtypes = [P, C.POINTER(C.c_int64)]
         L.kps_warm_features.argtypes = [P, P, C.c_int64, C.c_int32, P, P, P]
         L.kps_warm_targets.argtypes = [P, P, P, P, P, P, C.c_int64, C.c_int32, P, P, P]
@@ -385,6 +386,10 @@ class Solver:
 
     def warm_start(self, beh1, beh2, kappa: float, t0: int, stream=None):
         _check(lib().kps_solver_warm_start(self._h, _ptr(beh1), _ptr(beh2), float(kappa), int(t0), _stream(stream)))
+
+    def set_method(self, method: int, alpha: float = 1.5, beta: float = 0.0, gamma: float = 2.0):
+        """0 = RM+, 1 = Discounted CFR (takes effect at the next reset)."""
+        _check(lib().kps_solver_set_method(self._h, int(method), float(alpha), float(beta), float(gamma)))
 
     def step(self, iters: int, stream=None):
         _check(lib().kps_solver_step(self._h, int(iters), _stream(stream)))

@@ -182,3 +182,34 @@ def test_mixed_precision_reaches_1e3_pot(dt):
     bound = {kps.F32: 1e-5, kps.BF16: 2.0 ** -6, kps.F16: 2.0 ** -8}[dt]
     assert np.max(err) <= bound, (np.max(err), trace, ref)
     assert min(trace) < 1e-3
+
+
+@pytest.mark.parametrize("name,mk", SOLVER_SPECS, ids=[c[0] for c in SOLVER_SPECS])
+def test_fp64_dcfr_matches_oracle(name, mk):
+    """Discounted CFR (alpha 1.5, beta 0, gamma 2) in FP64 storage equals
+    the oracle's DCFR: exploitability and sequence-form averages to 1e-9,
+    the solver bar (60 iterations of regret dynamics amplify the products'
+    rounding differences, ~1e-16, to ~1e-10 here).  With t^2 weights some
+    sequences end with a tiny average reach; behavioural strategies there
+    are ratios of tiny numbers, so they are compared through the sequence
+    form."""
+    specs = mk()
+    games, b, s = _setup(specs, kps.F64)
+    s.set_method(1, 1.5, 0.0, 2.0)
+    s.reset()
+    orders = [library_order(sp["strength"]) for sp in specs]
+    s.step(25)
+    s.step(35)
+    e, _, _ = _expl(s, len(specs))
+    x = torch.zeros(int(b.offsets(0)[-1]), dtype=torch.float64, device="cuda")
+    y = torch.zeros(int(b.offsets(1)[-1]), dtype=torch.float64, device="cuda")
+    s.average(x, y, behavioural=False)
+    torch.cuda.synchronize()
+    sx = _split(b, games, orders, 0, x.cpu().numpy())
+    sy = _split(b, games, orders, 1, y.cpu().numpy())
+    for i, sp in enumerate(specs):
+        og = OracleGame(sp)
+        e_or, a1, a2, _ = og.dcfr(60, 1.5, 0.0, 2.0)
+        assert abs(e[i] - e_or) <= 1e-9 * max(1.0, abs(e_or)), (i, e[i], e_or)
+        assert np.max(np.abs(sx[i] - og.seqform(0, a1))) <= 1e-9
+        assert np.max(np.abs(sy[i] - og.seqform(1, a2))) <= 1e-9
