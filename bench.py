@@ -430,13 +430,18 @@ def measure_warmstart(train_games: int = 20480, per_game: int = 64, heldout: int
     torch.cuda.empty_cache()
     hb = batch(5555, heldout)
     res = {}
-    for name, dt in (("f32", kps.F32), ("bf16", kps.BF16)):
-        res[name] = W.compare(mlp, hb, dt, 1e-3, kappa, t0, block=25, max_iters=2000)
-    return {"train_games": train_games, "train_rows": rows, "train_solve_seconds": solve_s,
-            "train_solve_iterations": iters, "train_seconds": train_s, "epochs": epochs,
-            "loss_first_last": [hist[0], hist[-1]], "heldout_games": heldout, "kappa": kappa, "t0": t0,
-            "cold_f32": res["f32"]["cold"], "warm_f32": res["f32"]["warm"], "warm_bf16": res["bf16"]["warm"],
-            "cold_bf16": res["bf16"]["cold"], "total_seconds": time.perf_counter() - t_start}
+    for method in (0, 1):
+        for name, dt in (("f32", kps.F32), ("bf16", kps.BF16)):
+            r = W.compare(mlp, hb, dt, 1e-3, kappa, t0, block=25, max_iters=2000, method=method)
+            tag = ("dcfr_" if method else "") + name
+            res["cold_" + tag] = r["cold"]
+            res["warm_" + tag] = r["warm"]
+    out = {"train_games": train_games, "train_rows": rows, "train_solve_seconds": solve_s,
+           "train_solve_iterations": iters, "train_seconds": train_s, "epochs": epochs,
+           "loss_first_last": [hist[0], hist[-1]], "heldout_games": heldout, "kappa": kappa, "t0": t0}
+    out.update(res)
+    out["total_seconds"] = time.perf_counter() - t_start
+    return out
 
 
 def _e2e(g, y, x, oy, ox, stream, args, world):

@@ -30,13 +30,15 @@ def _torch():
 
 
 def solve(batch: "kps.Batch", dtype: int, target: float, block: int = 25, max_iters: int = 2000,
-          solver: "kps.Solver" = None, start=None, stream=None):
-    """Runs RM+ until max over games of the exploitability < target.
-    `start` = (beh1, beh2, kappa, t0) for a warm start.  Returns (solver,
-    iterations run, exploitability per game [numpy], wall seconds)."""
+          solver: "kps.Solver" = None, start=None, stream=None, method: int = 0):
+    """Runs RM+ (method 0) or Discounted CFR (method 1) until max over games
+    of the exploitability < target.  `start` = (beh1, beh2, kappa, t0) for a
+    warm start.  Returns (solver, iterations run, exploitability per game
+    [numpy], wall seconds)."""
     torch = _torch()
     ng = len(batch.games)
     s = solver or kps.Solver(batch, dtype)
+    s.set_method(method)
     e = torch.zeros(ng, dtype=torch.float64, device="cuda")
     s.step(block, stream)            # capture the iteration graph outside the timed run
     torch.cuda.synchronize()
@@ -146,19 +148,19 @@ def predict_unfused(mlp: "kps.MLP", batch: "kps.Batch", chunk: int = 1 << 16):
 
 
 def compare(mlp: "kps.MLP", batch: "kps.Batch", dtype: int, target: float, kappa: float, t0: int,
-            block: int = 25, max_iters: int = 2000):
+            block: int = 25, max_iters: int = 2000, method: int = 0):
     """Cold start vs warm start from the network on one batch."""
     torch = _torch()
-    s_cold, it_cold, e_cold, sec_cold = solve(batch, dtype, target, block, max_iters)
+    s_cold, it_cold, e_cold, sec_cold = solve(batch, dtype, target, block, max_iters, method=method)
     torch.cuda.synchronize()
     t_inf = time.perf_counter()
     beh = predict(mlp, batch)
     torch.cuda.synchronize()
     sec_inf = time.perf_counter() - t_inf
     _, it_warm, e_warm, sec_warm = solve(batch, dtype, target, block, max_iters, solver=s_cold,
-                                         start=(beh[0], beh[1], kappa, t0))
+                                         start=(beh[0], beh[1], kappa, t0), method=method)
     return {"games": len(batch.games), "target": target, "check_every": block,
             "cold": {"iterations": it_cold, "seconds": sec_cold, "max_expl": float(e_cold.max())},
             "warm": {"iterations": it_warm, "seconds": sec_warm + sec_inf, "solve_seconds": sec_warm,
                      "inference_seconds": sec_inf, "max_expl": float(e_warm.max())},
-            "kappa": kappa, "t0": t0}
+            "kappa": kappa, "t0": t0, "method": "dcfr" if method else "rm+"}
