@@ -135,18 +135,29 @@ struct UpdateArgs {
     C w0;                    // warm start: weight of the initial strategy in the average
     int method;              // 0 RM+, 1 DCFR
     const double *dtab;      // DCFR: per iteration t, {t^a/(t^a+1), t^b/(t^b+1), t^g} at 3t
+    int nmax;                // largest sequence count (shared-memory rows)
 };
 
-// One RM+ half-iteration of one player (see the file comment).
+// One half-iteration of one player (see the file comment).  Everything the
+// thread reads is loaded first, with independent loads, into shared memory
+// ([sequence][thread]: values, then regrets); the bottom-up and top-down
+// walks run in shared memory (child values are added into the parent's
+// value slot, which the walk reads after all children; the slots then take
+// the new sequence form), and regrets and strategy are written back last.
 template <typename S, typename C>
 __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S, C> u) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
     const Where w = locate(u.games, u.block_game);
     const SolverGame &G = u.games[w.game];
     if (w.h >= G.H) return;
-    const int p = u.player, n = G.n[p], hs = G.hs, tid = threadIdx.x;
+    const int p = u.player, n = G.n[p], hs = G.hs;
+    C *qv = reinterpret_cast<C *>(smem_raw) + threadIdx.x;      // [s * kThreads]
+    C *rg = qv + (size_t)u.nmax * kThreads;
     const long long base = G.off[p] + w.h;
+    const S *__restrict__ gp = u.g + base;
+    C *__restrict__ Rp = u.regret + base;
+    S *__restrict__ xp = u.x + base;
+    C *__restrict__ xsp = u.xsum + base;
     const long long t = *u.iter + 1;
     const bool init = t == *u.init_iter;
     const C wt = C(avg_weight(t, u.method, u.dtab));
@@ -159,10 +170,13 @@ __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S,
     const int4 *nodes = u.nodes + G.node_off[p];
     const int nn = G.nnodes[p];
     const C theta = C(G.theta[p]);
+    // values, regrets, and the strategy played added to the average
+#pragma unroll 4
     for (int s = 0; s < n; ++s) {
-        const long long i = base + (long long)s * hs;
-        u.xsum[i] += wt * C(Cv<S>::ld(u.x + i));
-        buf[s * kThreads + tid] = C(0);
+        const long long i = (long long)s * hs;
+        qv[s * kThreads] = u.sign * C(Cv<S>::ld(gp + i));
+        rg[s * kThreads] = Rp[i];
+        xsp[i] += wt * C(Cv<S>::ld(xp + i));
     }
     // bottom-up: values and regrets
     for (int k = nn - 1; k >= 0; --k) {
@@ -172,9 +186,8 @@ __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S,
 #pragma unroll
         for (int a = 0; a < kMaxActions; ++a)
             if (a < na) {
-                const long long i = base + (long long)(s0 + a) * hs;
-                r[a] = u.regret[i];
-                q[a] = u.sign * C(Cv<S>::ld(u.g + i)) + buf[(s0 + a) * kThreads + tid];
+                r[a] = rg[(s0 + a) * kThreads];
+                q[a] = qv[(s0 + a) * kThreads];
             }
         if (init) {
 #pragma unroll
@@ -191,10 +204,9 @@ __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S,
         for (int a = 0; a < kMaxActions; ++a)
             if (a < na) {
                 const C rn = r[a] + q[a] - v;
-                u.regret[base + (long long)(s0 + a) * hs] =
-                    u.method == 0 ? (rn > C(0) ? rn : C(0)) : rn * (rn > C(0) ? dpos : dneg);
+                rg[(s0 + a) * kThreads] = u.method == 0 ? (rn > C(0) ? rn : C(0)) : rn * (rn > C(0) ? dpos : dneg);
             }
-        if (par >= 0) buf[par * kThreads + tid] += v;
+        if (par >= 0) qv[par * kThreads] += v;
     }
     // top-down: next behavioural strategy and its sequence form
     for (int k = 0; k < nn; ++k) {
@@ -203,16 +215,19 @@ __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S,
         C r[kMaxActions], b[kMaxActions];
 #pragma unroll
         for (int a = 0; a < kMaxActions; ++a)
-            if (a < na) r[a] = u.regret[base + (long long)(s0 + a) * hs];
+            if (a < na) r[a] = rg[(s0 + a) * kThreads];
         regret_match<C>(r, na, b, theta);
-        const C xp = par >= 0 ? buf[par * kThreads + tid] : C(1);
+        const C xpar = par >= 0 ? qv[par * kThreads] : C(1);
 #pragma unroll
         for (int a = 0; a < kMaxActions; ++a)
-            if (a < na) {
-                const C xv = xp * b[a];
-                buf[(s0 + a) * kThreads + tid] = xv;
-                u.x[base + (long long)(s0 + a) * hs] = Cv<S>::st(xv);
-            }
+            if (a < na) qv[(s0 + a) * kThreads] = xpar * b[a];
+    }
+    // regrets and strategy back
+#pragma unroll 4
+    for (int s = 0; s < n; ++s) {
+        const long long i = (long long)s * hs;
+        Rp[i] = rg[s * kThreads];
+        xp[i] = Cv<S>::st(qv[s * kThreads]);
     }
 }
 
@@ -286,32 +301,36 @@ struct BrArgs {
     const int4 *nodes;
     int player;
     double sign;
-    double *g;          // FP64 values, player layout (accumulated in place)
+    const double *g;    // FP64 values, player layout
     double *partial;    // [blocks]
 };
 
 // Best response value of every hand: bottom-up max over the player's
-// actions; the sum over the block's hands goes to partial[block].
+// actions on the values loaded into shared memory ([sequence][thread]; a
+// child's value is added into its parent's slot, read after all children);
+// the sum over the block's hands goes to partial[block].
 __global__ void __launch_bounds__(kThreads) best_response_kernel(const BrArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kThreads];
     const Where w = locate(a.games, a.block_game);
     const SolverGame &G = a.games[w.game];
     double root = 0.0;
     if (w.h < G.H) {
-        const int p = a.player, hs = G.hs;
-        const long long base = G.off[p] + w.h;
+        const int p = a.player, hs = G.hs, n = G.n[p];
+        const double *__restrict__ gp = a.g + G.off[p] + w.h;
+        double *qv = reinterpret_cast<double *>(smem_raw) + threadIdx.x;
+#pragma unroll 4
+        for (int s = 0; s < n; ++s) qv[s * kThreads] = a.sign * gp[(long long)s * hs];
         const int4 *nodes = a.nodes + G.node_off[p];
-        // child values are added into the parent's value entry: the parent's
-        // node comes earlier in pre-order, so it is read after all of them
         for (int k = G.nnodes[p] - 1; k >= 0; --k) {
             const int4 nd = nodes[k];
             const int s0 = nd.x, na = nd.y, par = nd.z;
             double v = -1e300;
             for (int q = 0; q < na; ++q) {
-                const double val = a.sign * a.g[base + (long long)(s0 + q) * hs];
+                const double val = qv[(s0 + q) * kThreads];
                 v = val > v ? val : v;
             }
-            if (par >= 0) a.g[base + (long long)par * hs] += a.sign * v;
+            if (par >= 0) qv[par * kThreads] += v;
             else root += v;
         }
     }
@@ -396,6 +415,7 @@ UpdateArgs<S, C> make_args(kps_solver *s, int p) {
     u.w0 = C(s->w0);
     u.method = s->method;
     u.dtab = s->dtab;
+    u.nmax = s->nmax;
     return u;
 }
 
@@ -422,7 +442,7 @@ cudaError_t launch_node_kernel(kps_solver *s, K kernel, const UpdateArgs<S, C> &
 
 template <typename S, typename C>
 cudaError_t update_t(kps_solver *s, int p, cudaStream_t st) {
-    const size_t smem = (size_t)s->nmax * kThreads * sizeof(C);
+    const size_t smem = 2 * (size_t)s->nmax * kThreads * sizeof(C);
     return launch_node_kernel(s, rm_update_kernel<S, C>, make_args<S, C>(s, p), smem, st);
 }
 
@@ -566,7 +586,7 @@ kps_status kps_solver_create(kps_batch *b, kps_dtype dt, kps_solver **out) {
     }
     s->nblocks = (int)block_game.size();
     const size_t csz = compute_size(dt);
-    if ((size_t)s->nmax * kThreads * csz > (size_t)kps::max_dyn_smem()) {
+    if (2 * (size_t)s->nmax * kThreads * std::max<size_t>(csz, 8) > (size_t)kps::max_dyn_smem()) {
         free_solver(s);
         return fail(KPS_ENOTSUP, "too many sequences per player for the solver's shared memory");
     }
@@ -784,7 +804,10 @@ kps_status kps_solver_exploitability(kps_solver *s, double *expl, double *br1, d
         a.sign = p == 0 ? 1.0 : -1.0;
         a.g = s->g64[p];
         a.partial = s->partial[p];
-        best_response_kernel<<<s->nblocks, kThreads, 0, st>>>(a);
+        const size_t smem = (size_t)s->nmax * kThreads * sizeof(double);
+        cudaError_t e0 = smem_limit(reinterpret_cast<const void *>(best_response_kernel), smem);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "best response");
+        best_response_kernel<<<s->nblocks, kThreads, smem, st>>>(a);
     }
     const int ng = (int)s->batch->games.size();
     expl_kernel<<<(ng + 127) / 128, 128, 0, st>>>(s->games, ng, s->game_blocks, s->partial[0], s->partial[1], expl, br1,
