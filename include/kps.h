@@ -285,6 +285,11 @@ kps_status kps_solver_strategy(kps_solver *solver, void *x, void *y, void *strea
  * and the best-response values BR1, BR2 (may be NULL).  FP64 products and
  * best responses.  Asynchronous on `stream`. */
 kps_status kps_solver_exploitability(kps_solver *solver, double *expl, double *br1, double *br2, void *stream);
+/* The same quantity estimated cheaply for stopping tests: averages and
+ * products in FP32 (tensor-memory kernels), best-response sums in FP64.
+ * Differs from kps_solver_exploitability by the FP32 rounding of the
+ * products (about 1e-6 of the values); confirm a stop with the FP64 call. */
+kps_status kps_solver_exploitability_estimate(kps_solver *solver, double *expl, void *stream);
 
 /* ---- Learned warm start ----------------------------------------------------
  * Not in the paper.  A 3-layer perceptron (BF16 weights, FP32 master copy,

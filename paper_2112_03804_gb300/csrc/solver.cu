@@ -269,8 +269,8 @@ __global__ void bump_kernel(long long *iter, double *wsum, int method, const dou
 // FP64 averages: sequence form xsum / sum_t t (the current strategy before
 // any iteration), or behavioural (x[sigma] / x[parent], uniform where the
 // parent is never reached).
-template <typename S, typename C>
-__global__ void __launch_bounds__(kThreads) average_kernel(const UpdateArgs<S, C> u, double *out, int behavioural) {
+template <typename S, typename C, typename O>
+__global__ void __launch_bounds__(kThreads) average_kernel(const UpdateArgs<S, C> u, O *out, int behavioural) {
     const Where w = locate(u.games, u.block_game);
     const SolverGame &G = u.games[w.game];
     if (w.h >= G.H) return;
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) average_kernel(const UpdateArgs<S, C
             const double xa = avg(s0 + a);
             double v = xa;
             if (behavioural) v = xp > 0.0 ? xa / xp : 1.0 / na;
-            out[base + (long long)(s0 + a) * hs] = v;
+            out[base + (long long)(s0 + a) * hs] = O(v);
         }
     }
 }
@@ -301,7 +301,7 @@ struct BrArgs {
     const int4 *nodes;
     int player;
     double sign;
-    const double *g;    // FP64 values, player layout
+    const void *g;      // values (FP64, or FP32 for the estimate), player layout
     double *partial;    // [blocks]
 };
 
@@ -309,6 +309,7 @@ struct BrArgs {
 // actions on the values loaded into shared memory ([sequence][thread]; a
 // child's value is added into its parent's slot, read after all children);
 // the sum over the block's hands goes to partial[block].
+template <typename V>
 __global__ void __launch_bounds__(kThreads) best_response_kernel(const BrArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kThreads];
@@ -317,10 +318,10 @@ __global__ void __launch_bounds__(kThreads) best_response_kernel(const BrArgs a)
     double root = 0.0;
     if (w.h < G.H) {
         const int p = a.player, hs = G.hs, n = G.n[p];
-        const double *__restrict__ gp = a.g + G.off[p] + w.h;
+        const V *__restrict__ gp = static_cast<const V *>(a.g) + G.off[p] + w.h;
         double *qv = reinterpret_cast<double *>(smem_raw) + threadIdx.x;
 #pragma unroll 4
-        for (int s = 0; s < n; ++s) qv[s * kThreads] = a.sign * gp[(long long)s * hs];
+        for (int s = 0; s < n; ++s) qv[s * kThreads] = a.sign * (double)gp[(long long)s * hs];
         const int4 *nodes = a.nodes + G.node_off[p];
         for (int k = G.nnodes[p] - 1; k >= 0; --k) {
             const int4 nd = nodes[k];
@@ -457,7 +458,13 @@ cudaError_t seqform_t(kps_solver *s, int p, cudaStream_t st) {
 
 template <typename S, typename C>
 cudaError_t average_t(kps_solver *s, int p, double *out, int behavioural, cudaStream_t st) {
-    average_kernel<S, C><<<s->nblocks, kThreads, 0, st>>>(make_args<S, C>(s, p), out, behavioural);
+    average_kernel<S, C, double><<<s->nblocks, kThreads, 0, st>>>(make_args<S, C>(s, p), out, behavioural);
+    return cudaGetLastError();
+}
+
+template <typename S, typename C>
+cudaError_t average32_t(kps_solver *s, int p, float *out, cudaStream_t st) {
+    average_kernel<S, C, float><<<s->nblocks, kThreads, 0, st>>>(make_args<S, C>(s, p), out, 0);
     return cudaGetLastError();
 }
 
@@ -785,16 +792,28 @@ kps_status kps_solver_strategy(kps_solver *s, void *x, void *y, void *stream_ptr
     return KPS_OK;
 }
 
-kps_status kps_solver_exploitability(kps_solver *s, double *expl, double *br1, double *br2, void *stream_ptr) {
+}  // extern "C"
+
+namespace {
+
+// Averages, products of the averages (FP64, or FP32 for the estimate),
+// best responses (FP64 sums), exploitability per game.
+kps_status exploitability_impl(kps_solver *s, bool f32, double *expl, double *br1, double *br2, cudaStream_t st) {
     if (!s || !expl) return fail(KPS_EINVAL, "bad argument");
-    cudaStream_t st = static_cast<cudaStream_t>(stream_ptr);
     for (int p = 0; p < 2; ++p) {
-        cudaError_t e = KPS_DISPATCH(s->dt, average_t, s, p, s->xa[p], 0, st);
+        cudaError_t e = f32 ? KPS_DISPATCH(s->dt, average32_t, s, p, reinterpret_cast<float *>(s->xa[p]), st)
+                            : KPS_DISPATCH(s->dt, average_t, s, p, s->xa[p], 0, st);
         if (e != cudaSuccess) return cuda_fail(e, "averaging");
     }
-    kps_status r = batch_matvec(s->batch, 0, s->xa[1], s->g64[0], KPS_F64, st);
-    if (r == KPS_OK) r = batch_matvec(s->batch, 1, s->xa[0], s->g64[1], KPS_F64, st);
+    const kps_dtype pd = f32 ? KPS_F32 : KPS_F64;
+    kps_status r = batch_matvec(s->batch, 0, s->xa[1], s->g64[0], pd, st);
+    if (r == KPS_OK) r = batch_matvec(s->batch, 1, s->xa[0], s->g64[1], pd, st);
     if (r != KPS_OK) return r;
+    const size_t smem = (size_t)s->nmax * kThreads * sizeof(double);
+    const void *kern = f32 ? reinterpret_cast<const void *>(best_response_kernel<float>)
+                           : reinterpret_cast<const void *>(best_response_kernel<double>);
+    cudaError_t e = smem_limit(kern, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "best response");
     for (int p = 0; p < 2; ++p) {
         BrArgs a;
         a.games = s->games;
@@ -804,17 +823,27 @@ kps_status kps_solver_exploitability(kps_solver *s, double *expl, double *br1, d
         a.sign = p == 0 ? 1.0 : -1.0;
         a.g = s->g64[p];
         a.partial = s->partial[p];
-        const size_t smem = (size_t)s->nmax * kThreads * sizeof(double);
-        cudaError_t e0 = smem_limit(reinterpret_cast<const void *>(best_response_kernel), smem);
-        if (e0 != cudaSuccess) return cuda_fail(e0, "best response");
-        best_response_kernel<<<s->nblocks, kThreads, smem, st>>>(a);
+        if (f32) best_response_kernel<float><<<s->nblocks, kThreads, smem, st>>>(a);
+        else best_response_kernel<double><<<s->nblocks, kThreads, smem, st>>>(a);
     }
     const int ng = (int)s->batch->games.size();
     expl_kernel<<<(ng + 127) / 128, 128, 0, st>>>(s->games, ng, s->game_blocks, s->partial[0], s->partial[1], expl, br1,
                                                   br2);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "best response");
     return KPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kps_status kps_solver_exploitability(kps_solver *s, double *expl, double *br1, double *br2, void *stream_ptr) {
+    return exploitability_impl(s, false, expl, br1, br2, static_cast<cudaStream_t>(stream_ptr));
+}
+
+kps_status kps_solver_exploitability_estimate(kps_solver *s, double *expl, void *stream_ptr) {
+    return exploitability_impl(s, true, expl, nullptr, nullptr, static_cast<cudaStream_t>(stream_ptr));
 }
 
 }  // extern "C"

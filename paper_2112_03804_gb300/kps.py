@@ -71,6 +71,7 @@ EXPORTED = ["kps_sparsify", "kps_game_destroy", "kps_game_info", "kps_game_hands
             "kps_solver_create", "kps_solver_destroy", "kps_solver_reset", "kps_solver_warm_start",
             "kps_solver_set_method", "kps_solver_step",
             "kps_solver_iterations", "kps_solver_average", "kps_solver_strategy", "kps_solver_exploitability",
+            "kps_solver_exploitability_estimate",
             "kps_warm_num_queries", "kps_warm_features", "kps_warm_targets", "kps_warm_scatter",
             "kps_warm_predict",
             "kps_mlp_create", "kps_mlp_destroy", "kps_mlp_num_params", "kps_mlp_get", "kps_mlp_set",
@@ -115,6 +116,7 @@ def lib():
         L.kps_solver_average.argtypes = [P, C.c_int32, P, P, P]
         L.kps_solver_exploitability.argtypes = [P, P, P, P, P]
         L.kps_solver_strategy.argtypes = [P, P, P, P]
+        L.kps_solver_exploitability_estimate.argtypes = [P, P, P]
         L.kps_solver_warm_start.argtypes = [P, P, P, C.c_double, C.c_int32, P]
         L.kps_solver_set_method.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_double]
         L.kps_warm_num_queries.argtypes = [P, C.POINTER(C.c_int64)]
@@ -404,6 +406,9 @@ class Solver:
 
     def strategy(self, x, y, stream=None):
         _check(lib().kps_solver_strategy(self._h, _ptr(x), _ptr(y), _stream(stream)))
+
+    def exploitability_estimate(self, expl, stream=None):
+        _check(lib().kps_solver_exploitability_estimate(self._h, _ptr(expl), _stream(stream)))
 
     def exploitability(self, expl, br1=None, br2=None, stream=None):
         _check(lib().kps_solver_exploitability(self._h, _ptr(expl), _ptr(br1), _ptr(br2), _stream(stream)))

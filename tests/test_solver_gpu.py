@@ -213,3 +213,18 @@ def test_fp64_dcfr_matches_oracle(name, mk):
         assert abs(e[i] - e_or) <= 1e-9 * max(1.0, abs(e_or)), (i, e[i], e_or)
         assert np.max(np.abs(sx[i] - og.seqform(0, a1))) <= 1e-9
         assert np.max(np.abs(sy[i] - og.seqform(1, a2))) <= 1e-9
+
+
+def test_exploitability_estimate_close_to_fp64():
+    """The FP32 estimate used for stopping tests differs from the FP64
+    exploitability only by the FP32 rounding of the products: within 1e-5
+    of the pot on river games (values are at most a few pots)."""
+    specs = [synth.river_spec(seed=sd) for sd in (5, 6, 7)]
+    games, b, s = _setup(specs, kps.F32)
+    s.step(40)
+    e64, _, _ = _expl(s, 3)
+    e = torch.zeros(3, dtype=torch.float64, device="cuda")
+    s.exploitability_estimate(e)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(e.cpu().numpy() - e64)) <= 1e-5
+    assert np.all(e64 > 0)
