@@ -179,7 +179,7 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
     if (tb < te) fetch(tb);
     for (int t = tb; t < te; ++t) {
         const int2 tl = p.tiles[t];
-        const int t0 = tl.x;
+        const int t0 = tl.x, len = tl.y;
         const float lin = lin_n;
         const uint32_t hreg = h_n;
         const int2 tw = tw_n;
@@ -221,6 +221,7 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         // registers, and its store (the later one) leaves the combined value.
 #pragma unroll 1
         for (int half = 0; half < 2; ++half) {
+            if (16 * half >= len) break;   // a short tile's second half is all padding
             float r[16];
             uint32_t hh[16];
 #pragma unroll
@@ -394,6 +395,7 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         // finished values into the partial tile
 #pragma unroll 1
         for (int half = 0; half < 2; ++half) {
+            if (16 * half >= len) break;
             float r[16], za[16], zb[16];
             tm_ld16(treg + (uint32_t)(t0 - cstart + 16 * half), r);
 #pragma unroll
