@@ -188,13 +188,41 @@ kps_status tiles_for(kps_game *g, int nw, cudaStream_t stream, const kps_game::T
 }
 
 bool tmem_chunks_fit(const kps_game::Tiles &t, int nw) {
-    const auto &tc = t.tchunk;
     for (int k = 0; k < nw; ++k) {
-        if (tc[k] == tc[k + 1]) continue;
-        const int2 a = t.host[tc[k]], b = t.host[tc[k + 1] - 1];
-        if (b.x + b.y - a.x > kps::kTmemChunk) return false;
+        const int a = t.tchunk[k];
+        auto at = [&](int i) { return std::make_pair(t.host[a + i].x, t.host[a + i].y); };
+        if (!kps::tmem_chunk_fits(t.tchunk[k + 1] - a, at)) return false;
     }
     return true;
+}
+
+bool tmem_split_fits(const kps::HostGame &h, int nw) {
+    std::vector<int> tchunk;
+    const std::vector<std::pair<int, int>> tl = kps::tie_tiles(h, nw, kps::kTile, tchunk);
+    for (int k = 0; k < nw; ++k) {
+        const int a = tchunk[k];
+        if (!kps::tmem_chunk_fits(tchunk[k + 1] - a, [&](int i) { return tl[a + i]; })) return false;
+    }
+    return true;
+}
+
+int tmem_warps(kps_game *g, int nc) {
+    const kps::HostGame &h = g->host;
+    if (const char *env = std::getenv("KPS_WARPS")) {
+        const int w = std::atoi(env);
+        if (w >= 1 && w <= kps::kMaxWarps && tmem_split_fits(h, w)) return w;
+    }
+    if (g->tmem_nw != 0) return g->tmem_nw;
+    int nw = std::min(kps::kMaxWarps, (h.H + kps::kTile - 1) / kps::kTile);
+    const int smem_max = kps::max_dyn_smem();
+    if (nw > 4 && 2 * (kps::tmem_smem_bytes(nc, 4) + 1024) <= (size_t)smem_max + 1024 && tmem_split_fits(h, 4)) {
+        nw = 4;
+    } else {
+        while (nw <= kps::kMaxWarps && !tmem_split_fits(h, nw)) ++nw;
+        if (nw > kps::kMaxWarps) nw = -1;
+    }
+    g->tmem_nw = nw;
+    return nw;
 }
 
 // Warps per CTA of the fast path: two CTAs of 4 warps per SM when they fit
@@ -236,13 +264,8 @@ kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int stor
     }
     int nw;
     if (path == kTmem) {
-        // enough warps that every chunk fits a warp's tensor-memory region
-        nw = std::max((h.H + 199) / 200, std::min(kps::kMaxWarps, (h.H + kps::kTile - 1) / kps::kTile));
-        if (const char *env = std::getenv("KPS_WARPS")) {
-            const int w = std::atoi(env);
-            if (w >= 1 && w <= kps::kMaxWarps && (long long)w * kps::kTmemChunk >= (long long)h.H + 64) nw = w;
-        }
-        if (nw > kps::kMaxWarps || kps::tmem_smem_bytes(sp.nc, nw) > (size_t)kps::max_dyn_smem()) path = kScalar;
+        nw = tmem_warps(g, sp.nc);
+        if (nw < 1 || kps::tmem_smem_bytes(sp.nc, nw) > (size_t)kps::max_dyn_smem()) path = kScalar;
     }
     const bool vec = path == kVec;
     if (path != kTmem) nw = fast_warps(storage, sp.nc, h.H, vec);

@@ -53,6 +53,8 @@ struct kps_game {
         std::vector<int> tchunk;
     };
     std::map<int, Tiles> tiles;
+    // warps per CTA of the tensor-memory path (0 = not chosen yet)
+    int tmem_nw = 0;
     // FP32 partial results for half-precision outputs
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -67,8 +69,17 @@ kps_status upload(kps_game *g, cudaStream_t stream);
 // uploaded on first use; synchronises `stream` then).
 kps_status tiles_for(kps_game *g, int nw, cudaStream_t stream, const kps_game::Tiles **out);
 
-// Does every warp's chunk of the `nw`-warp tile list span at most
-// kps::kTmemChunk hands?
+// Do the chunks of the `nw`-warp tile list fit the tensor-memory layout
+// (kps::tmem_chunk_fits)?  The first form checks an uploaded list, the
+// second builds the list on the host.
 bool tmem_chunks_fit(const kps_game::Tiles &t, int nw);
+bool tmem_split_fits(const kps::HostGame &h, int nw);
+
+// Warps per CTA of the tensor-memory path for a game with `nc` cards left:
+// four (two CTAs per SM, whose phases overlap) when the four-way split fits
+// and two CTAs fit an SM's shared memory, else the fewest warps from one
+// per 32 hands (at most kMaxWarps) whose split fits; -1 if none does.
+// KPS_WARPS overrides the choice when that split fits.  Cached per game.
+int tmem_warps(kps_game *g, int nc);
 
 }  // namespace kps_abi

@@ -41,21 +41,13 @@ int sm_count() {
     return n > 0 ? n : 1;
 }
 
-// Smallest warp count whose tile lists give every game's chunks at most
-// kTmemChunk hands (tensor-memory path); 0 if none does.  Host only.
+// Smallest warp count whose tile lists fit every game's chunks into the
+// tensor-memory layout; 0 if none does.  Host only.
 int tmem_min_warps(kps_batch *b) {
     for (int nw = 1; nw <= kps::kMaxWarps; ++nw) {
         bool ok = true;
         for (kps_game *g : b->games) {
-            if ((long long)nw * kps::kTmemChunk < g->host.H) { ok = false; break; }
-            std::vector<int> tchunk;
-            const std::vector<std::pair<int, int>> tl = kps::tie_tiles(g->host, nw, kps::kTile, tchunk);
-            for (int k = 0; k < nw && ok; ++k) {
-                if (tchunk[k] == tchunk[k + 1]) continue;
-                const auto &a = tl[tchunk[k]], &z = tl[tchunk[k + 1] - 1];
-                ok = z.first + z.second - a.first <= kps::kTmemChunk;
-            }
-            if (!ok) break;
+            if (!kps_abi::tmem_split_fits(g->host, nw)) { ok = false; break; }
         }
         if (ok) return nw;
     }
@@ -174,6 +166,13 @@ kps_status batch_default_shape(kps_batch *b, kps_dtype dt, cudaStream_t stream, 
         const int lo = tmem_min_warps(b);
         if (lo == 0) return fail(KPS_ENOTSUP, "hand chunk too long for tensor memory");
         s.nw = std::max(lo, std::min(kps::kMaxWarps, (maxH + kps::kTile - 1) / kps::kTile));
+        // two CTAs of four warps per SM (their phases overlap) when every
+        // game's four-way split fits
+        if (s.nw > 4 && kps::tmem_multi_ctas_per_sm(storage, b->k, maxnc, 4) >= 2) {
+            bool fit = true;
+            for (kps_game *g : b->games) fit = fit && kps_abi::tmem_split_fits(g->host, 4);
+            if (fit) s.nw = 4;
+        }
         s.per_sm = std::max(1, kps::tmem_multi_ctas_per_sm(storage, b->k, maxnc, s.nw));
     }
     s.grid = sm_count() * s.per_sm;

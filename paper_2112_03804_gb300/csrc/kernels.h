@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <utility>
 
 namespace kps {
 
@@ -88,9 +89,24 @@ cudaError_t launch_vec_scan(const FastParams &p, int storage, int cards_per_hand
 namespace kps {
 
 // Tensor-memory path (FP32 arithmetic; FP32/BF16/FP16 storage): partial
-// results stay in tensor memory.  Every warp's chunk must span at most
-// kTmemChunk hands.  `scratch` is unused.
-constexpr int kTmemChunk = 224;
+// results stay on chip.  A warp owns kTmemRegion tensor-memory columns (one
+// per hand, written 16 hands at a time from a tile's offset in the chunk)
+// for every tile of its chunk but the last, whose partial results stay in
+// shared memory.  `scratch` is unused.
+constexpr int kTmemRegion = 256;
+
+// Does a chunk fit?  `tile(i)` gives the (start, length) of its i-th of n
+// tiles.
+template <typename TileAt>
+inline bool tmem_chunk_fits(int n, TileAt tile) {
+    if (n <= 1) return true;
+    const int cs = tile(0).first;
+    for (int i = 0; i + 1 < n; ++i) {
+        const auto t = tile(i);
+        if (t.first - cs + (t.second + 15) / 16 * 16 > kTmemRegion) return false;
+    }
+    return true;
+}
 size_t tmem_smem_bytes(int nc, int nw);
 cudaError_t launch_tmem_scan(const FastParams &p, int storage, int cards_per_hand, cudaStream_t stream);
 

@@ -36,7 +36,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPitch = 33;         // row pitch of [hand][column] tiles
-constexpr int kRegion = 256;       // tensor-memory columns owned by one warp
+constexpr int kRegion = kTmemRegion;   // tensor-memory columns owned by one warp
 
 template <typename S> struct Num;
 template <> struct Num<float> {
@@ -76,7 +76,13 @@ __device__ __forceinline__ void tm_dealloc(uint32_t taddr, uint32_t ncols) {
 __device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;"); }
 __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;"); }
-__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;"); }
+// waits for this thread's tensor-memory loads; names the 16 destination
+// registers so that no use of them is scheduled before the data arrive
+__device__ __forceinline__ void tm_wait_ld16(float *r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(r[0]), "+f"(r[1]), "+f"(r[2]), "+f"(r[3]), "+f"(r[4]), "+f"(r[5]), "+f"(r[6]), "+f"(r[7]),
+                   "+f"(r[8]), "+f"(r[9]), "+f"(r[10]), "+f"(r[11]), "+f"(r[12]), "+f"(r[13]), "+f"(r[14]), "+f"(r[15])::"memory");
+}
 
 // 16 consecutive tensor-memory columns of this warp's lanes <-> r[0..15]
 __device__ __forceinline__ void tm_st16(uint32_t taddr, const float *r) {
@@ -308,9 +314,16 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
 #pragma unroll
                 for (int k = 0; k < 16; ++k) r[k] += ptile[(16 * half + k) * kPitch + lane];
             }
-            // the half's partial results to tensor memory (lane = column);
-            // columns past the tile's end are rewritten by the next tile
-            tm_st16(treg + (uint32_t)(t0 - cstart + 16 * half), r);
+            // the half's partial results to tensor memory (lane = column;
+            // columns past the tile's end are rewritten by the next tile),
+            // the last tile's to the partial tile, where the finishing pass
+            // takes them first
+            if (t + 1 < te) {
+                tm_st16(treg + (uint32_t)(t0 - cstart + 16 * half), r);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) ptile[(16 * half + k) * kPitch + lane] = r[k];
+            }
         }
         __syncwarp();
     }
@@ -364,8 +377,9 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
     }
     __syncthreads();
 
-    // ---- phase 3: finish each tile from tensor memory (lane = column), then
-    // write it out with coalesced stores (lane = hand)
+    // ---- phase 3: finish each tile from tensor memory (the last tile from
+    // the partial tile, first; lane = column), then write it out with
+    // coalesced stores (lane = hand)
     const float *Z = mine + 2 * (size_t)nc * 32 + lane;
     const float base = sums[(warp * 3 + 2) * 32 + lane];
     // the next tile's descriptor (shared memory for the first kTlCache tiles
@@ -381,15 +395,16 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         hq_n = pin ? __ldg(&p.hinfo[pos]) : 0u;
         lo_n = pin ? lam_out[pos] : 0.f;
     };
-    if (tb < te) pre3(tb);
-    for (int t = tb; t < te; ++t) {
+    const int nt = te - tb;
+    if (nt > 0) pre3(te - 1);
+    for (int i = 0; i < nt; ++i) {
         const int2 tl = tl_n;
         const uint32_t hq = hq_n;
         const float lo = lo_n;
         const int t0 = tl.x, len = tl.y;
         const int pos = t0 + lane;
         const bool pin = lane < len;
-        if (t + 1 < te) pre3(t + 1);
+        if (i + 1 < nt) pre3(tb + i);
         // per half tile: partial results from tensor memory, every hand's
         // per-card terms (loaded before any store of the partial tile), the
         // finished values into the partial tile
@@ -397,14 +412,19 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         for (int half = 0; half < 2; ++half) {
             if (16 * half >= len) break;
             float r[16], za[16], zb[16];
-            tm_ld16(treg + (uint32_t)(t0 - cstart + 16 * half), r);
+            if (i > 0) {
+                tm_ld16(treg + (uint32_t)(t0 - cstart + 16 * half), r);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) r[k] = ptile[(16 * half + k) * kPitch + lane];
+            }
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 const uint32_t h = __shfl_sync(kFull, hq, 16 * half + k);
                 za[k] = Z[(h & 63) * 32];
                 zb[k] = K2 == 2 ? Z[((h >> 6) & 63) * 32] : 0.f;
             }
-            tm_wait_ld();
+            tm_wait_ld16(r);
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 float val = r[k] + base - za[k];

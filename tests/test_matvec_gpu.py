@@ -178,7 +178,7 @@ def river_ties():
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
-@pytest.mark.parametrize("warps", ["1", "3", "6", "8"])
+@pytest.mark.parametrize("warps", ["1", "3", "4", "6", "8"])
 @pytest.mark.parametrize("transpose", [False, True])
 def test_river_many_ties_warp_counts(river_ties, warps, transpose, kernel, monkeypatch):
     """Tie groups inside tiles, several hand chunks per CTA, each kernel path
