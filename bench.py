@@ -44,8 +44,9 @@ def _args():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--workload", default="matvec", choices=["matvec", "batch", "solver", "warmstart"],
-                    help="matvec: the headline line; batch / solver: print only that measurement")
+    ap.add_argument("--workload", default="matvec", choices=["matvec", "batch", "solver", "warmstart", "factors"],
+                    help="matvec: the headline line; batch / solver / warmstart / factors: print only that "
+                         "measurement")
     ap.add_argument("--games", type=int, default=4096, help="games of the batched workload")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the batched and solver measurements in the headline line")
@@ -341,6 +342,51 @@ def measure_batch(ngames: int, steps: int, warmup: int, rank: int = 0):
             "l2": "inputs larger than L2" if alg > 2.6e8 else "inputs smaller than L2"}
 
 
+def measure_factors(batch: int = BATCH, steps: int = 3, warmup: int = 2):
+    """The three routes to A*y on the headline workload (river game, FP32):
+    the fused kernel, Technique B's explicit factors with this library's
+    sparse kernels, and the same factors with cuSPARSE (SpMM + SpSM), the
+    paper's GPU route (Sec. 4).  Times per launch from CUDA events."""
+    import torch
+    from paper_2112_03804_gb300 import kps
+    spec = _workload()
+    g = kps.Game(spec)
+    inf = g.info()
+    H, hs, n1, n2 = inf["H"], inf["hs"], inf["n1"], inf["n2"]
+    tb = kps.TechniqueB(g)
+    sz = tb.sizes()
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    y = torch.rand((batch, n2, hs), device="cuda", generator=gen)
+    y[..., H:] = 0
+    routes = {"fused": lambda o: kps.matvec_A(g, y, o, batch),
+              "own_sparse": lambda o: tb.matvec(y, o, batch, backend=0),
+              "cusparse": lambda o: tb.matvec(y, o, batch, backend=1)}
+    ms, outs = {}, {}
+    for name, fn in routes.items():
+        o = torch.empty((batch, n1, hs), device="cuda")
+        for _ in range(warmup):
+            fn(o)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn(o)
+        e1.record()
+        torch.cuda.synchronize()
+        ms[name] = e0.elapsed_time(e1) / steps
+        outs[name] = o
+    ref = outs["fused"].double()
+    scale = float(ref.abs().max())
+    diff = {k: float((outs[k].double() - ref).abs().max()) / scale for k in ("own_sparse", "cusparse")}
+    total = sz["nnz_Ahat"] + sz["nnz_U"] + sz["nnz_M"] + sz["nnz_V"]
+    return {"workload": WORKLOAD + ", A*y", "vectors": batch,
+            "factor_nnz": {"Ahat": sz["nnz_Ahat"], "U": sz["nnz_U"], "M": sz["nnz_M"], "V": sz["nnz_V"],
+                           "total": total, "explicit_A": inf["nnz_A"]},
+            "ms_per_launch": ms, "matvecs_per_s": {k: batch / (v / 1e3) for k, v in ms.items()},
+            "fused_speedup": {k: ms[k] / ms["fused"] for k in ("own_sparse", "cusparse")},
+            "max_normwise_diff_vs_fused": diff}
+
+
 def measure_solver(target: float = 1e-3, block: int = 10, max_iters: int = 4000):
     """RM+ on the tiny Kronecker game (6 one-card hands) until the FP64
     exploitability of the averages is below `target` of the pot (checked
@@ -496,7 +542,8 @@ def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec):
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_seconds)
     if not args.no_secondary:
-        for key, fn in (("batched", lambda: measure_batch(args.games, 10, 3)), ("solver", measure_solver)):
+        for key, fn in (("batched", lambda: measure_batch(args.games, 10, 3)), ("solver", measure_solver),
+                        ("technique_b", measure_factors)):
             try:
                 line[key] = fn()
             except Exception as exc:   # reported, never silently dropped
@@ -520,6 +567,10 @@ def main():
         import torch
         torch.cuda.set_device(_dist()[2])
         print(json.dumps(measure_solver()), flush=True)
+    elif args.workload == "factors":
+        import torch
+        torch.cuda.set_device(_dist()[2])
+        print(json.dumps(measure_factors(steps=args.steps, warmup=args.warmup)), flush=True)
     else:
         run_ours(args)
 

@@ -385,6 +385,62 @@ kps_status kps_mlp_adam(kps_mlp *mlp, float lr, float beta1, float beta2, float 
 kps_status kps_matvec_A_static_scratch(kps_game *game, const void *y, void *out, int32_t batch,
                                        kps_dtype dt, void *stream);
 
+/* ---- Technique B's explicit factors (Sec. 4) ----------------------------
+ * The paper's own route to A*y: A = Ahat + U M^-1 V^T (Technique B
+ * proposition, before the postprocessing step), the four factors
+ * materialised as sparse matrices and applied with sparse products and a
+ * triangular solve.  The library's kps_matvec_A computes the same product
+ * without materialising anything; these calls exist to compare the two.
+ *
+ * Layout of the factors (the vector layout above; hands in library order):
+ *   rows of A (and of Ahat, U)    s1 * hs + h1       R = n1 * hs
+ *   columns of A (and of V^T)     s2 * hs + h2       C = n2 * hs
+ *   inner dimension (U, M, V^T)   s1 * hs + h  for the I (x) D block,
+ *                                 n1 * hs + s1 for the identity block,
+ *                                 m = n1 * hs + n1
+ *   Ahat = -F (x) (Lambda1 Hx Lambda2)
+ *   U    = [I (x) Lambda1 | I (x) lambda1]
+ *   M    = diag(I (x) D, I), D lower bidiagonal with 1 on the diagonal and
+ *          -1 below it (stored with its unit diagonal; rows of padding
+ *          hands hold the diagonal alone)
+ *   V^T  = [S (x) (Y Lambda2) ; F (x) lambda2^T],  Y = D W
+ * with F, S the fold and showdown payoff matrices of the skeleton, W the
+ * win/lose sign with zeros on card overlaps, Hx the card-overlap indicator
+ * and lambda = mu / sqrt(beta) (the paper's hand-major D (x) I and
+ * (Lambda2 Y^T) (x) S^T in this sequence-major order).
+ *
+ * kps_tb_create builds the factors on the host (no GPU needed); *out
+ * receives a new object that refers to `game` (which must outlive it).
+ * Errors: KPS_EINVAL (NULL), KPS_ENOMEM, KPS_ENOTSUP (a factor with more
+ * than 2^31 nonzeros). */
+typedef struct kps_tb kps_tb;
+kps_status kps_tb_create(const kps_game *game, kps_tb **out);
+kps_status kps_tb_destroy(kps_tb *tb);
+
+/* sizes[0..6] = R, C, m, nnz(Ahat), nnz(U), nnz(M), nnz(V).  nnz(M)
+ * excludes the diagonal of padding rows, so the four nonzero counts equal
+ * kps_info's Technique B counts before postprocessing. */
+kps_status kps_tb_sizes(const kps_tb *tb, int64_t *sizes);
+
+/* Host copy of one factor in CSR (columns ascending within a row, FP64
+ * values): which = 0 Ahat, 1 U, 2 M, 3 V^T.  shape[0..2] = rows, columns,
+ * stored nonzeros; rowptr[rows + 1], col[nnz], val[nnz] (caller-owned; any
+ * of the four pointers may be NULL to skip it). */
+kps_status kps_tb_export(const kps_tb *tb, int which, int64_t *shape, int32_t *rowptr, int32_t *col, double *val);
+
+/* out = (Ahat + U M^-1 V^T) y on the GPU for `batch` player-2 vectors y
+ * (device, [batch][n2][hs]) into player-1 vectors out (device,
+ * [batch][n1][hs]); dt = KPS_F32 or KPS_F64 (values and arithmetic).
+ * backend 0: this library's kernels (a CSR times dense-matrix product and,
+ *   for M^-1, prefix sums over the hands of each player-1 sequence);
+ * backend 1: cuSPARSE (SpMM for V^T, Ahat and U; SpSM for M).
+ * The factors are uploaded on the first call; a workspace of
+ * 2 * batch * m values is kept between calls.  Errors: KPS_EINVAL,
+ * KPS_ENOTSUP (other dtypes), KPS_ENOMEM, KPS_ECUDA (CUDA or cuSPARSE
+ * failure, with the library's message). */
+kps_status kps_tb_matvec(kps_tb *tb, const void *y, void *out, int32_t batch, kps_dtype dt, int32_t backend,
+                         void *stream);
+
 /* Thread-local description of the last failure ("" if none). */
 const char *kps_last_error(void);
 

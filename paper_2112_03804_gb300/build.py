@@ -23,7 +23,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
               "-I" + INCLUDE] + ARCH
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-I" + INCLUDE]
 
-SOURCES = ["game.cpp", "abi.cu", "kernels.cu", "kernels_fast.cu", "kernels_vec.cu", "kernels_tmem.cu", "batch.cu", "solver.cu", "mlp.cu", "warm.cu"]
+SOURCES = ["game.cpp", "abi.cu", "kernels.cu", "kernels_fast.cu", "kernels_vec.cu", "kernels_tmem.cu", "batch.cu", "solver.cu", "mlp.cu", "warm.cu", "tb.cu"]
 
 
 def _nvcc() -> str:
@@ -69,7 +69,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + ".tmp"
         subprocess.check_call([nvcc, "-shared", "-o", tmp] + objs + ARCH +
-                              ["-L" + _cuda_lib_dir(nvcc), "-lcudart"])
+                              ["-L" + _cuda_lib_dir(nvcc), "-lcudart", "-lcusparse"])
         os.replace(tmp, LIB)
     return LIB
 

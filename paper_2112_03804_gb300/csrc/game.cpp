@@ -480,4 +480,142 @@ void technique_b_counts(HostGame &g) {
     g.counts_done = true;
 }
 
+namespace {
+
+// Appends row r of a CSR under construction from (column, value) pairs:
+// sorted by column, equal columns summed, zeros dropped.
+void csr_push_row(Csr &c, std::vector<std::pair<int, double>> &e) {
+    std::sort(e.begin(), e.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+    for (size_t i = 0; i < e.size();) {
+        size_t j = i;
+        double v = 0.0;
+        for (; j < e.size() && e[j].first == e[i].first; ++j) v += e[j].second;
+        if (v != 0.0) {
+            c.col.push_back(e[i].first);
+            c.val.push_back(v);
+        }
+        i = j;
+    }
+    c.rowptr.push_back((int)c.col.size());
+    e.clear();
+}
+
+}  // namespace
+
+void technique_b_factors(const HostGame &g, TechniqueB &f) {
+    const int H = g.H, hs = g.hs, n1 = g.n[0], n2 = g.n[1], N = g.ncards, k = g.k;
+    const int R = n1 * hs, C = n2 * hs, m = n1 * hs + n1;
+    auto share = [&](int x, int y) {
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j)
+                if (g.hand_slots[2 * x + i] == g.hand_slots[2 * y + j]) return true;
+        return false;
+    };
+    std::vector<std::vector<int>> by_card(N + 1);
+    for (int p = 0; p < H; ++p)
+        for (int j = 0; j < k; ++j) by_card[g.hand_slots[2 * p + j]].push_back(p);
+    // W[i][j]: +1 if hand i beats a compatible hand j, -1 if it loses, 0 for
+    // ties and card overlaps (library order is the strength order).
+    auto wval = [&](int i, int j) -> int {
+        if (i < 0 || share(i, j)) return 0;
+        return (g.strength[i] > g.strength[j]) - (g.strength[i] < g.strength[j]);
+    };
+    // Y = D W row by row.  Row i differs from row i-1 only in the columns of
+    // strength between theirs (positions group_lo[i-1] .. group_hi[i]) and
+    // in the hands sharing a card with i or i-1; row 0 is W's first row.
+    std::vector<std::vector<std::pair<int, int>>> Y(H);
+    std::vector<int> mark(H, -1), cand;
+    for (int i = 0; i < H; ++i) {
+        cand.clear();
+        auto visit = [&](int j) {
+            if (mark[j] != i) {
+                mark[j] = i;
+                cand.push_back(j);
+            }
+        };
+        for (int j = i > 0 ? g.group_lo[i - 1] : 0; j <= g.group_hi[i]; ++j) visit(j);
+        if (i == 0)
+            for (int j = 0; j < H; ++j) visit(j);
+        for (int side = 0; side < 2; ++side) {
+            const int h = i - side;
+            if (h < 0) continue;
+            for (int j = 0; j < k; ++j)
+                for (int q : by_card[g.hand_slots[2 * h + j]]) visit(q);
+        }
+        std::sort(cand.begin(), cand.end());
+        for (int j : cand) {
+            if (g.mu2[j] == 0.0) continue;
+            const int y = wval(i, j) - wval(i - 1, j);
+            if (y != 0) Y[i].emplace_back(j, y);
+        }
+    }
+    const PairCsr &pc = g.csr_A;          // terminals by player-1 sequence
+    std::vector<std::pair<int, double>> e;
+    auto start = [](Csr &c, int rows, int cols) {
+        c = Csr();
+        c.rows = rows;
+        c.cols = cols;
+        c.rowptr.push_back(0);
+    };
+    // Ahat: card-overlapping pairs of every fold terminal
+    start(f.ahat, R, C);
+    for (int s1 = 0; s1 < n1; ++s1)
+        for (int h1 = 0; h1 < hs; ++h1) {
+            if (h1 < H && g.lam1[h1] != 0.0)
+                for (int t = pc.rowptr[s1]; t < pc.rowptr[s1 + 1]; ++t) {
+                    if (pc.kind[t] != 0) continue;
+                    for (int j = 0; j < k; ++j)
+                        for (int h2 : by_card[g.hand_slots[2 * h1 + j]]) {
+                            // a hand sharing both cards with h1 is h1 itself:
+                            // list it once
+                            if (j == 1 && h2 == h1) continue;
+                            if (g.lam2[h2] != 0.0)
+                                e.emplace_back(pc.col[t] * hs + h2, -pc.coef[t] * g.lam1[h1] * g.lam2[h2]);
+                        }
+                }
+            csr_push_row(f.ahat, e);
+        }
+    // U = [I (x) Lambda1 | I (x) lambda1]
+    start(f.u, R, m);
+    for (int s1 = 0; s1 < n1; ++s1)
+        for (int h1 = 0; h1 < hs; ++h1) {
+            if (h1 < H && g.lam1[h1] != 0.0) {
+                e.emplace_back(s1 * hs + h1, g.lam1[h1]);
+                e.emplace_back(n1 * hs + s1, g.lam1[h1]);
+            }
+            csr_push_row(f.u, e);
+        }
+    // M = diag(I (x) D, I)
+    start(f.m, m, m);
+    for (int s1 = 0; s1 < n1; ++s1)
+        for (int h = 0; h < hs; ++h) {
+            if (h > 0 && h < H) e.emplace_back(s1 * hs + h - 1, -1.0);
+            e.emplace_back(s1 * hs + h, 1.0);
+            csr_push_row(f.m, e);
+        }
+    for (int s1 = 0; s1 < n1; ++s1) {
+        e.emplace_back(n1 * hs + s1, 1.0);
+        csr_push_row(f.m, e);
+    }
+    // V^T = [S (x) (Y Lambda2) ; F (x) lambda2^T]
+    start(f.vt, m, C);
+    for (int s1 = 0; s1 < n1; ++s1)
+        for (int h = 0; h < hs; ++h) {
+            if (h < H)
+                for (int t = pc.rowptr[s1]; t < pc.rowptr[s1 + 1]; ++t) {
+                    if (pc.kind[t] != 1) continue;
+                    for (const auto &yj : Y[h]) e.emplace_back(pc.col[t] * hs + yj.first, pc.coef[t] * yj.second * g.lam2[yj.first]);
+                }
+            csr_push_row(f.vt, e);
+        }
+    for (int s1 = 0; s1 < n1; ++s1) {
+        for (int t = pc.rowptr[s1]; t < pc.rowptr[s1 + 1]; ++t) {
+            if (pc.kind[t] != 0) continue;
+            for (int h2 = 0; h2 < H; ++h2)
+                if (g.lam2[h2] != 0.0) e.emplace_back(pc.col[t] * hs + h2, pc.coef[t] * g.lam2[h2]);
+        }
+        csr_push_row(f.vt, e);
+    }
+}
+
 }  // namespace kps

@@ -83,6 +83,30 @@ std::string build_game(const kps_game_spec *spec, HostGame &g, kps_status *code)
 // Technique B sizes (Sec. 4) from the structure of the factors.
 void technique_b_counts(HostGame &g);
 
+// A sparse matrix in CSR form (FP64 values, columns ascending in a row).
+struct Csr {
+    int rows = 0, cols = 0;
+    std::vector<int> rowptr, col;
+    std::vector<double> val;
+};
+
+// Technique B factors (Sec. 4), A = Ahat + U M^-1 V^T, before the
+// postprocessing step, in the vector layout: rows of A are s1 * hs + h1,
+// columns s2 * hs + h2 (library hand order, padding rows and columns
+// empty).  The inner dimension lists one entry per (player-1 sequence,
+// hand), s1 * hs + h (the I (x) D block; the paper's D (x) I in its
+// hand-major order), then one per player-1 sequence, n1 * hs + s1.
+//   Ahat = -F (x) (Lambda1 Hx Lambda2)
+//   U    = [I (x) Lambda1 | I (x) lambda1]
+//   M    = diag(I (x) D, I), D lower bidiagonal (1, -1), stored with its
+//          unit diagonal (padding rows: the diagonal alone)
+//   V^T  = [S (x) (Y Lambda2) ; F (x) lambda2^T],  Y = D W
+// with lambda in the rank-one blocks (the chance deal of Sec. 3).
+struct TechniqueB {
+    Csr ahat, u, m, vt;
+};
+void technique_b_factors(const HostGame &g, TechniqueB &f);
+
 // Split [0, H) into `parts` contiguous chunks whose boundaries fall on tie
 // group boundaries.  Returns parts+1 offsets (some chunks may be empty).
 std::vector<int> chunk_bounds(const HostGame &g, int parts);

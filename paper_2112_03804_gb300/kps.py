@@ -76,6 +76,7 @@ EXPORTED = ["kps_sparsify", "kps_game_destroy", "kps_game_info", "kps_game_hands
             "kps_warm_predict",
             "kps_mlp_create", "kps_mlp_destroy", "kps_mlp_num_params", "kps_mlp_get", "kps_mlp_set",
             "kps_mlp_forward", "kps_mlp_gradients", "kps_mlp_adam",
+            "kps_tb_create", "kps_tb_destroy", "kps_tb_sizes", "kps_tb_export", "kps_tb_matvec",
             "kps_last_error", "kps_version"]
 
 _lib = None
@@ -132,6 +133,11 @@ def lib():
         L.kps_mlp_forward.argtypes = [P, P, C.c_int32, P, P, P]
         L.kps_mlp_gradients.argtypes = [P, P, C.c_int32, P, P, P, C.c_float, P, P]
         L.kps_mlp_adam.argtypes = [P, C.c_float, C.c_float, C.c_float, C.c_float, P]
+        L.kps_tb_create.argtypes = [P, C.POINTER(C.c_void_p)]
+        L.kps_tb_destroy.argtypes = [P]
+        L.kps_tb_sizes.argtypes = [P, P]
+        L.kps_tb_export.argtypes = [P, C.c_int, P, P, P, P]
+        L.kps_tb_matvec.argtypes = [P, P, P, C.c_int32, C.c_int, C.c_int32, P]
         for name in EXPORTED:
             if name not in ("kps_last_error", "kps_version"):
                 getattr(L, name).restype = C.c_int
@@ -291,6 +297,53 @@ def matvec_A_host(game: Game, y, out, batch: int, dtype: int, stream=None):
 
 def matvec_AT_host(game: Game, x, out, batch: int, dtype: int, stream=None):
     _check(lib().kps_matvec_AT_host(game._h, _ptr(x), _ptr(out), int(batch), dtype, _stream(stream)))
+
+
+class TechniqueB:
+    """Technique B's explicit factors of a game's A (Sec. 4), built on the
+    host: A = Ahat + U M^-1 V^T.  `sizes()` gives R, C, m and the nonzero
+    counts; `export(which)` a factor as (shape, rowptr, col, val) numpy
+    arrays (0 Ahat, 1 U, 2 M, 3 V^T); `matvec` the GPU product with this
+    library's kernels (backend 0) or cuSPARSE (backend 1)."""
+
+    AHAT, U, M, VT = 0, 1, 2, 3
+
+    def __init__(self, game: Game):
+        self._game = game           # the factors refer to the game's tables
+        h = C.c_void_p()
+        _check(lib().kps_tb_create(game._h, C.byref(h)))
+        self._h = h.value
+
+    def sizes(self) -> dict:
+        a = np.zeros(7, dtype=np.int64)
+        _check(lib().kps_tb_sizes(self._h, _ptr(a)))
+        return dict(zip(("R", "C", "m", "nnz_Ahat", "nnz_U", "nnz_M", "nnz_V"), (int(x) for x in a)))
+
+    def export(self, which: int):
+        shape = np.zeros(3, dtype=np.int64)
+        _check(lib().kps_tb_export(self._h, which, _ptr(shape), None, None, None))
+        rows, cols, nnz = (int(x) for x in shape)
+        rowptr = np.zeros(rows + 1, dtype=np.int32)
+        col = np.zeros(max(nnz, 1), dtype=np.int32)
+        val = np.zeros(max(nnz, 1), dtype=np.float64)
+        _check(lib().kps_tb_export(self._h, which, None, _ptr(rowptr), _ptr(col), _ptr(val)))
+        return (rows, cols), rowptr, col[:nnz], val[:nnz]
+
+    def matvec(self, y, out, batch: int, backend: int = 0, dtype=None, stream=None):
+        """out[b] = (Ahat + U M^-1 V^T) y[b]; y [batch][n2][hs], out [batch][n1][hs] on the device."""
+        _check(lib().kps_tb_matvec(self._h, _ptr(y), _ptr(out), int(batch), _dtype_code(y, dtype), int(backend),
+                                   _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kps_tb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 STATIC_SCRATCH_FLOATS = 4194304
