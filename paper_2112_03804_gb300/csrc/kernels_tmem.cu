@@ -164,13 +164,17 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         h_n = pin ? __ldg(&p.hinfo[pos]) : 0u;
         if (HS) tw_n = p.tie_work[t];
         if (uni) {
-            const S *fb = vin + c0i.in_off + pos + c0i.foff;
-            const S *sb = vin + c0i.in_off + pos + c0i.soff;
+            // lanes past the tile's end read its last hand (their staged
+            // value is lin = 0 times a finite input)
+            const int pc = min(pos, tl.x + tl.y - 1);
+            const S *fb = vin + c0i.in_off + pc + (HF ? c0i.foff : 0);
+            const S *sb = vin + c0i.in_off + pc + (HS ? c0i.soff : 0);
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
-                const bool ok = pin && jj < nvalid;
-                xf[jj] = (HF && ok && c0i.foff >= 0) ? Num<S>::load(fb + jj * istride) : 0.f;
-                xs[jj] = (HS && ok && c0i.soff >= 0) ? Num<S>::load(sb + jj * istride) : 0.f;
+                xf[jj] = (HF && jj < nvalid) ? Num<S>::load(fb) : 0.f;
+                xs[jj] = (HS && jj < nvalid) ? Num<S>::load(sb) : 0.f;
+                fb += istride;
+                sb += istride;
             }
         } else {
 #pragma unroll
@@ -437,7 +441,15 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         if (pin) {
             if (uni) {
                 S *dst = vout + c0i.out_off + pos;
-                for (int jj = 0; jj < nvalid; ++jj) dst[jj * ostride] = Num<S>::conv(lo * ptile[lane * kPitch + jj]);
+                if (nvalid == 32) {
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) {
+                        *dst = Num<S>::conv(lo * ptile[lane * kPitch + jj]);
+                        dst += ostride;
+                    }
+                } else {
+                    for (int jj = 0; jj < nvalid; ++jj) dst[jj * ostride] = Num<S>::conv(lo * ptile[lane * kPitch + jj]);
+                }
             } else {
                 for (int jj = 0; jj < 32; ++jj) {
                     const long long o = ci[jj].out_off;
