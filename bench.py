@@ -44,9 +44,9 @@ def _args():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--workload", default="matvec", choices=["matvec", "batch", "solver", "warmstart", "factors"],
-                    help="matvec: the headline line; batch / solver / warmstart / factors: print only that "
-                         "measurement")
+    ap.add_argument("--workload", default="matvec", choices=["matvec", "batch", "solver", "warmstart", "factors", "libratus"],
+                    help="matvec: the headline line; batch / solver / warmstart / factors / libratus: print "
+                         "only that measurement")
     ap.add_argument("--games", type=int, default=4096, help="games of the batched workload")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the batched and solver measurements in the headline line")
@@ -387,6 +387,41 @@ def measure_factors(batch: int = BATCH, steps: int = 3, warmup: int = 2):
             "max_normwise_diff_vs_fused": diff}
 
 
+def measure_libratus(batch: int = BATCH, steps: int = 5, warmup: int = 3):
+    """The large-tree stress shape: the fused products on a 1081-hand river
+    game with the Libratus betting menus (247 + 247 sequences, 329
+    terminals), FP32, `batch` vectors per launch, inputs resident in HBM."""
+    import torch
+    from paper_2112_03804_gb300 import kps, synth
+    g = kps.Game(synth.libratus_spec(seed=2))
+    inf = g.info()
+    H, hs, n1, n2 = inf["H"], inf["hs"], inf["n1"], inf["n2"]
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    y = torch.rand((batch, n2, hs), device="cuda", generator=gen)
+    x = torch.rand((batch, n1, hs), device="cuda", generator=gen)
+    oa = torch.empty((batch, n1, hs), device="cuda")
+    ot = torch.empty((batch, n2, hs), device="cuda")
+    ms = {}
+    for name, fn, i, o in (("A", kps.matvec_A, y, oa), ("AT", kps.matvec_AT, x, ot)):
+        for _ in range(warmup):
+            fn(g, i, o, batch)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn(g, i, o, batch)
+        e1.record()
+        torch.cuda.synchronize()
+        ms[name] = e0.elapsed_time(e1) / steps
+    alg = 4.0 * H * (n1 + n2) * batch
+    peak, peak_kind = _peaks()
+    gbs = alg / (statistics.mean(ms.values()) / 1e3) / 1e9
+    return {"workload": f"river endgame with the Libratus betting menus, {H} hands, {n1}+{n2} sequences, "
+                        f"{inf['T']} terminals, batch {batch}, fp32",
+            "ms_per_launch": ms, "matvecs_per_s": 2 * batch / (sum(ms.values()) / 1e3),
+            "alg_bytes_per_launch": alg, "achieved_gbs": gbs, "frac_of_peak": gbs / peak, "peak_source": peak_kind}
+
+
 def measure_solver(target: float = 1e-3, block: int = 10, max_iters: int = 4000):
     """RM+ on the tiny Kronecker game (6 one-card hands) until the FP64
     exploitability of the averages is below `target` of the pot (checked
@@ -543,7 +578,7 @@ def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec):
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_seconds)
     if not args.no_secondary:
         for key, fn in (("batched", lambda: measure_batch(args.games, 10, 3)), ("solver", measure_solver),
-                        ("technique_b", measure_factors)):
+                        ("technique_b", measure_factors), ("libratus", measure_libratus)):
             try:
                 line[key] = fn()
             except Exception as exc:   # reported, never silently dropped
@@ -567,6 +602,10 @@ def main():
         import torch
         torch.cuda.set_device(_dist()[2])
         print(json.dumps(measure_solver()), flush=True)
+    elif args.workload == "libratus":
+        import torch
+        torch.cuda.set_device(_dist()[2])
+        print(json.dumps(measure_libratus()), flush=True)
     elif args.workload == "factors":
         import torch
         torch.cuda.set_device(_dist()[2])

@@ -70,6 +70,22 @@ typedef enum {
 
 #define KPS_MAX_BETS 8
 #define KPS_MAX_BOARD 8
+#define KPS_SITUATIONS 5
+
+/* Optional betting menu: the bet/raise pot fractions of each player in
+ * each situation of the round (the shape of the Libratus abstraction the
+ * paper's experiments use, appendix "Libratus' betting abstraction"):
+ *   situation 0: first action of the round,
+ *             1: after a check,
+ *             2: facing the first bet,
+ *             3: facing one raise,
+ *             4: facing two or more raises.
+ * nbet[p][s] fractions bet_frac[p][s][0..nbet-1] (> 0, finite) for player p
+ * (0 = player 1).  Fractions are applied as the spec's bet_frac are. */
+typedef struct {
+    int32_t nbet[2][KPS_SITUATIONS];
+    double bet_frac[2][KPS_SITUATIONS][KPS_MAX_BETS];
+} kps_bet_menu;
 
 /* River endgame (Sec. 3): board B, stacks, initial pot contributions,
  * beliefs mu1, mu2 and a fixed betting abstraction (appendix "Betting
@@ -82,6 +98,8 @@ typedef enum {
  *     all-in amount and merges with the all-in action;
  *   - raise_cap limits the aggressive actions of the round (bets, raises
  *     and all-ins counted together; < 0 = no cap);
+ *   - with a menu (kps_bet_menu), the fractions of the acting player in the
+ *     current situation replace bet_frac;
  *   - a call, or a check after a check, ends the round in a showdown.
  * The payoff of player 1 is +c2 when player 2 folds, -c1 when player 1
  * folds, and gamma(h1,h2) * min(c1,c2) at a showdown. */
@@ -98,6 +116,7 @@ typedef struct {
     int32_t allow_allin;
     const double *mu1, *mu2;            /* beliefs per CANONICAL hand; NULL = 1 */
     const int32_t *strength;            /* per CANONICAL hand, higher wins     */
+    const kps_bet_menu *menu;           /* NULL = bet_frac in every situation  */
 } kps_game_spec;
 
 typedef struct {

@@ -98,6 +98,20 @@ static double dmin(double a, double b) { return a < b ? a : b; }
 static int list_actions(const orc_game *g, const onode *nd, int *code, double *amt)
 {
     int p = nd->player, o = 1 - p, na = 0;
+    /* the bet sizes on offer: one list, or the menu entry of this player in
+     * this situation (how many bets and raises came before, and whether the
+     * opponent just checked) */
+    int nbet = g->sp.nbet;
+    const double *frac = g->sp.bet_frac;
+    if (g->sp.use_menu) {
+        int k;
+        if (nd->naggr == 0) k = nd->prev_check ? 1 : 0;
+        else if (nd->naggr == 1) k = 2;
+        else if (nd->naggr == 2) k = 3;
+        else k = 4;
+        nbet = g->sp.menu_nbet[p][k];
+        frac = g->sp.menu_frac[p][k];
+    }
     double maxp = g->sp.contrib0[p] + g->sp.stack[p];
     double maxo = g->sp.contrib0[o] + g->sp.stack[o];
     double eff = dmin(maxp, maxo);
@@ -110,8 +124,8 @@ static int list_actions(const orc_game *g, const onode *nd, int *code, double *a
         if (can_aggr && eff > nd->c[o]) {
             double matched = nd->c[o];
             double pot_after = 2.0 * matched;
-            for (int i = 0; i < g->sp.nbet; i++) {
-                double a = matched + g->sp.bet_frac[i] * pot_after;
+            for (int i = 0; i < nbet; i++) {
+                double a = matched + frac[i] * pot_after;
                 aggr[nag++] = a >= eff ? eff : a;
             }
             if (g->sp.allow_allin) aggr[nag++] = eff;
@@ -120,8 +134,8 @@ static int list_actions(const orc_game *g, const onode *nd, int *code, double *a
         code[na] = ACT_CHECKCALL; amt[na] = nd->c[p]; na++;
         if (can_aggr && eff > nd->c[p]) {
             double pot = nd->c[0] + nd->c[1];
-            for (int i = 0; i < g->sp.nbet; i++) {
-                double a = nd->c[p] + g->sp.bet_frac[i] * pot;
+            for (int i = 0; i < nbet; i++) {
+                double a = nd->c[p] + frac[i] * pot;
                 aggr[nag++] = a >= eff ? eff : a;
             }
             if (g->sp.allow_allin) aggr[nag++] = eff;
@@ -227,6 +241,10 @@ orc_game *orc_build(const orc_spec *sp)
 {
     if (!sp || sp->cards_per_hand < 1 || sp->cards_per_hand > 2) return NULL;
     if (sp->ranks < 1 || sp->suits < 1 || sp->nbet < 0 || sp->nbet > ORC_MAX_BETS) return NULL;
+    if (sp->use_menu)
+        for (int p = 0; p < 2; p++)
+            for (int k = 0; k < 5; k++)
+                if (sp->menu_nbet[p][k] < 0 || sp->menu_nbet[p][k] > ORC_MAX_BETS) return NULL;
     if (sp->nboard < 0 || sp->nboard > ORC_MAX_BOARD) return NULL;
     if (!sp->strength) return NULL;
     int ncard = sp->ranks * sp->suits;

@@ -44,6 +44,14 @@ typedef struct {
     int allow_allin;           /* explicit all-in action                      */
     const double *mu1, *mu2;   /* beliefs per canonical hand; NULL = uniform  */
     const int *strength;       /* per canonical hand, higher = stronger       */
+    /* Optional per-player menu (appendix "Libratus' betting abstraction"):
+     * when use_menu, player p in situation k bets the fractions
+     * menu_frac[p][k][0..menu_nbet[p][k]-1] instead of bet_frac.  Situations:
+     * 0 first action of the round, 1 after a check, 2 facing the first bet,
+     * 3 facing one raise, 4 facing two or more raises. */
+    int use_menu;
+    int menu_nbet[2][5];
+    double menu_frac[2][5][ORC_MAX_BETS];
 } orc_spec;
 
 typedef struct orc_game orc_game;

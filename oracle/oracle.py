@@ -44,7 +44,9 @@ class _Spec(C.Structure):
                 ("nbet", C.c_int), ("bet_frac", C.c_double * MAX_BETS),
                 ("raise_cap", C.c_int), ("allow_allin", C.c_int),
                 ("mu1", C.POINTER(C.c_double)), ("mu2", C.POINTER(C.c_double)),
-                ("strength", C.POINTER(C.c_int))]
+                ("strength", C.POINTER(C.c_int)),
+                ("use_menu", C.c_int), ("menu_nbet", (C.c_int * 5) * 2),
+                ("menu_frac", ((C.c_double * MAX_BETS) * 5) * 2)]
 
 
 _lib = None
@@ -105,7 +107,10 @@ class OracleGame:
 
     spec keys: ranks, suits, cards_per_hand, board (list of card ids),
     stack (2), contrib0 (2), bet_frac (list), raise_cap (int, <0 none),
-    allow_allin (bool), strength (per canonical hand), mu1/mu2 (optional).
+    allow_allin (bool), strength (per canonical hand), mu1/mu2 (optional),
+    menu (optional: menu[player][situation] = list of fractions, situations
+    first action / after a check / facing the first bet / facing one raise /
+    facing two or more raises).
     """
 
     def __init__(self, spec: dict):
@@ -125,6 +130,14 @@ class OracleGame:
             s.bet_frac[i] = float(f)
         s.raise_cap = int(spec.get("raise_cap", -1))
         s.allow_allin = 1 if spec.get("allow_allin", False) else 0
+        if spec.get("menu") is not None:
+            s.use_menu = 1
+            for p in range(2):
+                for k in range(5):
+                    fr = list(spec["menu"][p][k])
+                    s.menu_nbet[p][k] = len(fr)
+                    for i, f in enumerate(fr):
+                        s.menu_frac[p][k][i] = float(f)
         self._strength = np.ascontiguousarray(spec["strength"], dtype=np.int32)
         self._mu1 = None if spec.get("mu1") is None else np.ascontiguousarray(spec["mu1"], dtype=np.float64)
         self._mu2 = None if spec.get("mu2") is None else np.ascontiguousarray(spec["mu2"], dtype=np.float64)

@@ -40,7 +40,13 @@ struct Choice {
 };
 
 // Actions of a decision node, in the library's action order.
-int legal_actions(const kps_game_spec &s, const Pending &nd, Choice *out) {
+// Situation of the acting player for the betting menu (kps_bet_menu).
+int situation(const Pending &nd) {
+    if (nd.aggressive == 0) return nd.after_check ? 1 : 0;
+    return std::min(nd.aggressive + 1, KPS_SITUATIONS - 1);
+}
+
+int legal_actions(const kps_game_spec &s, const kps_bet_menu *menu, const Pending &nd, Choice *out) {
     const int me = nd.who, opp = 1 - nd.who;
     const double my_max = s.contrib0[me] + s.stack[me];
     const double opp_max = s.contrib0[opp] + s.stack[opp];
@@ -58,10 +64,13 @@ int legal_actions(const kps_game_spec &s, const Pending &nd, Choice *out) {
     int nr = 0;
     const double level = facing ? nd.c[opp] : nd.c[me];
     if (may_raise && all_in > level) {
-        for (int i = 0; i < s.nbet; ++i) {
+        const int sit = situation(nd);
+        const int nbet = menu ? menu->nbet[me][sit] : s.nbet;
+        const double *frac = menu ? menu->bet_frac[me][sit] : s.bet_frac;
+        for (int i = 0; i < nbet; ++i) {
             // match the opponent, then add the fraction of the matched pot
-            double target = facing ? nd.c[opp] + s.bet_frac[i] * (2.0 * nd.c[opp])
-                                   : nd.c[me] + s.bet_frac[i] * (nd.c[me] + nd.c[opp]);
+            double target = facing ? nd.c[opp] + frac[i] * (2.0 * nd.c[opp])
+                                   : nd.c[me] + frac[i] * (nd.c[me] + nd.c[opp]);
             raise_to[nr++] = target >= all_in ? all_in : target;
         }
         if (s.allow_allin) raise_to[nr++] = all_in;
@@ -90,6 +99,15 @@ std::string validate(const kps_game_spec *s, kps_status *code) {
     for (int i = 0; i < s->nbet; ++i)
         if (!(s->bet_frac[i] > 0.0) || !std::isfinite(s->bet_frac[i]))
             return "bet fractions must be positive and finite";
+    if (s->menu)
+        for (int p = 0; p < 2; ++p)
+            for (int k = 0; k < KPS_SITUATIONS; ++k) {
+                const int n = s->menu->nbet[p][k];
+                if (n < 0 || n > KPS_MAX_BETS) return "menu nbet out of range";
+                for (int i = 0; i < n; ++i)
+                    if (!(s->menu->bet_frac[p][k][i] > 0.0) || !std::isfinite(s->menu->bet_frac[p][k][i]))
+                        return "menu bet fractions must be positive and finite";
+            }
     const int deck = s->ranks * s->suits;
     if (deck > 63) {
         *code = KPS_ENOTSUP;
@@ -130,7 +148,7 @@ std::string build_tree(HostGame &g) {
             continue;
         }
         const int me = nd.who;
-        const int na = legal_actions(s, nd, acts);
+        const int na = legal_actions(s, g.has_menu ? &g.menu : nullptr, nd, acts);
         const int node_id = g.nodes[me]++;
         g.nodes_nact[me].push_back(na);
         const int first = g.n[me];
@@ -299,6 +317,11 @@ std::string build_game(const kps_game_spec *spec, HostGame &g, kps_status *code)
     g.spec = *spec;
     g.spec.mu1 = g.spec.mu2 = nullptr;
     g.spec.strength = nullptr;
+    g.spec.menu = nullptr;
+    if (spec->menu) {
+        g.menu = *spec->menu;
+        g.has_menu = true;
+    }
     g.pot0 = spec->contrib0[0] + spec->contrib0[1];
     *code = KPS_EINVAL;
     err = build_hands(g, spec->mu1, spec->mu2, spec->strength);

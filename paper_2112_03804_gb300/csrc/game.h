@@ -51,6 +51,8 @@ inline uint32_t pack_hinfo(int a, int b, bool tied, bool last, int off) {
 
 struct HostGame {
     kps_game_spec spec{};          // copy; the pointer fields are cleared
+    kps_bet_menu menu{};           // copy of *spec.menu when has_menu
+    bool has_menu = false;
     int H = 0, hs = 0, k = 0, ncards = 0;
     int n[2] = {0, 0};
     int nodes[2] = {0, 0};

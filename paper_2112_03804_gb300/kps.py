@@ -30,6 +30,17 @@ class KpsError(RuntimeError):
         self.status = status
 
 
+SITUATIONS = 5
+
+
+class BetMenu(C.Structure):
+    """kps_bet_menu: per player and situation (first action, after a check,
+    facing the first bet, facing one raise, facing two or more raises) the
+    bet/raise pot fractions."""
+    _fields_ = [("nbet", (C.c_int32 * SITUATIONS) * 2),
+                ("bet_frac", ((C.c_double * MAX_BETS) * SITUATIONS) * 2)]
+
+
 class GameSpec(C.Structure):
     _fields_ = [("ranks", C.c_int32), ("suits", C.c_int32), ("cards_per_hand", C.c_int32),
                 ("nboard", C.c_int32), ("board", C.c_int32 * MAX_BOARD),
@@ -37,7 +48,7 @@ class GameSpec(C.Structure):
                 ("nbet", C.c_int32), ("bet_frac", C.c_double * MAX_BETS),
                 ("raise_cap", C.c_int32), ("allow_allin", C.c_int32),
                 ("mu1", C.POINTER(C.c_double)), ("mu2", C.POINTER(C.c_double)),
-                ("strength", C.POINTER(C.c_int32))]
+                ("strength", C.POINTER(C.c_int32)), ("menu", C.POINTER(BetMenu))]
 
 
 class Info(C.Structure):
@@ -212,6 +223,20 @@ class Game:
             s.bet_frac[i] = float(f)
         s.raise_cap = int(spec.get("raise_cap", -1))
         s.allow_allin = 1 if spec.get("allow_allin", False) else 0
+        # optional menu: spec["menu"][player][situation] = list of fractions
+        self._menu = None
+        if spec.get("menu") is not None:
+            m = BetMenu()
+            for p in range(2):
+                for k in range(SITUATIONS):
+                    fr = list(spec["menu"][p][k])
+                    if len(fr) > MAX_BETS:
+                        raise ValueError("too many bet sizes in the menu")
+                    m.nbet[p][k] = len(fr)
+                    for i, f in enumerate(fr):
+                        m.bet_frac[p][k][i] = float(f)
+            self._menu = m
+            s.menu = C.pointer(m)
         self._strength = np.ascontiguousarray(spec["strength"], dtype=np.int32)
         mu1, mu2 = spec.get("mu1"), spec.get("mu2")
         self._mu1 = None if mu1 is None else np.ascontiguousarray(mu1, dtype=np.float64)

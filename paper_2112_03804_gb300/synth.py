@@ -100,6 +100,39 @@ def river_spec(seed: int = 2, nboard: int = 5, bet_frac=(0.5, 1.0), raise_cap: i
                 mu1=mu1, mu2=mu2)
 
 
+# The betting abstraction of the paper's experiments (appendix "Libratus'
+# betting abstraction"), pot fractions per situation: first action of the
+# round, after a check, facing the first bet, facing one raise, facing two
+# or more raises.  All-in is always on offer and raises are not capped.  The
+# opponent's list has no single-raise entry: its "subsequent raises" list
+# serves both raise situations.
+LIBRATUS_AI = ([0.25, 0.5, 1.0, 2.0, 4.0, 8.0], [0.25, 0.5, 1.0, 2.0, 4.0, 8.0], [0.4, 0.7, 1.1, 2.0],
+               [0.4, 0.7, 2.0], [0.7])
+LIBRATUS_OPPONENT = ([0.35, 0.65, 1.0], [0.5, 0.75, 1.0], [0.7, 1.1], [0.7], [0.7])
+
+
+def libratus_spec(seed: int = 2, ai_player: int = 0, pot: float = 1000.0, total: float = 20000.0,
+                  ranks: int = 13, suits: int = 4, nboard: int = 5) -> dict:
+    """River endgame with the Libratus betting menus: the AI (`ai_player`)
+    and its opponent bet from their own per-situation lists, all-in always
+    allowed, no raise cap; each player has put pot/2 in and holds `total`
+    chips in all (200 big blinds of 100 at the default).  Deck, board,
+    strengths and beliefs as river_spec."""
+    r = _rng(seed)
+    board = sorted(r.choice(ranks * suits, size=nboard, replace=False).tolist())
+    H = num_hands(ranks, suits, nboard, 2)
+    strength = r.integers(0, HAND_RANKS, size=H).tolist()
+    mu1 = r.uniform(0.5, 1.5, size=H)
+    mu2 = r.uniform(0.5, 1.5, size=H)
+    menu = [None, None]
+    menu[ai_player] = [list(x) for x in LIBRATUS_AI]
+    menu[1 - ai_player] = [list(x) for x in LIBRATUS_OPPONENT]
+    half = pot / 2.0
+    return dict(ranks=ranks, suits=suits, cards_per_hand=2, board=board,
+                stack=[total - half, total - half], contrib0=[half, half], bet_frac=[],
+                raise_cap=-1, allow_allin=True, menu=menu, strength=strength, mu1=mu1, mu2=mu2)
+
+
 # Betting menus for the batched workload: (bet fractions, raise cap, all-in,
 # stack).  Chosen to cover trees from about ten to about two hundred terminals.
 BATCH_MENU = [

@@ -27,6 +27,7 @@ def _all_ties_zero_beliefs():
 
 
 SPECS.append(("all_ties_zero_beliefs", _all_ties_zero_beliefs()))
+SPECS.append(("libratus_menus", synth.libratus_spec(seed=3, pot=5000.0, ranks=4, suits=2, nboard=2)))
 
 
 def _dense(csr):
