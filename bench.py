@@ -44,7 +44,7 @@ def _args():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--workload", default="matvec", choices=["matvec", "batch", "solver", "warmstart", "factors", "libratus"],
+    ap.add_argument("--workload", default="matvec", choices=["matvec", "batch", "solver", "warmstart", "factors", "libratus", "libratus_solve"],
                     help="matvec: the headline line; batch / solver / warmstart / factors / libratus: print "
                          "only that measurement")
     ap.add_argument("--games", type=int, default=4096, help="games of the batched workload")
@@ -474,6 +474,45 @@ def measure_solver(target: float = 1e-3, block: int = 10, max_iters: int = 4000)
             "target_expl_pot": target, "check_every": block, "by_storage": res}
 
 
+def measure_libratus_solve(target: float = 1e-3, block: int = 10, max_iters: int = 5000, seeds=(2, 3, 4, 5)):
+    """Time to solve one river endgame with the Libratus betting menus (1081
+    hands, 247 + 247 sequences at a 1000-chip pot) to `target` of the pot:
+    the paper's GPU claim is stated per endgame (Sec. 5).  DCFR (1.5, 0, 2)
+    and RM+, FP32 storage, FP64 exploitability of the averages checked every
+    `block` iterations (inside the timed region); one game per solver."""
+    import torch
+    from paper_2112_03804_gb300 import kps, synth
+    out = {}
+    for method, name in ((1, "dcfr_f32"), (0, "rmplus_f32")):
+        rows = []
+        for seed in seeds:
+            g = kps.Game(synth.libratus_spec(seed=seed))
+            b = kps.Batch([g])
+            s = kps.Solver(b, kps.F32)
+            if method == 1:
+                s.set_method(1, 1.5, 0.0, 2.0)
+            e = torch.zeros(1, dtype=torch.float64, device="cuda")
+            s.step(block)
+            s.exploitability(e)
+            s.reset()
+            torch.cuda.synchronize()
+            it, v = 0, float("inf")
+            t0 = time.perf_counter()
+            while it < max_iters:
+                s.step(block)
+                it += block
+                s.exploitability(e)
+                v = float(e.item())
+                if v < target:
+                    break
+            rows.append({"seed": seed, "iterations": it, "expl": v, "seconds": time.perf_counter() - t0})
+            s.close()
+        out[name] = rows
+    return {"workload": "one river endgame with the Libratus betting menus per solve: 1081 hands, 247+247 "
+                        "sequences, 329 terminals (synthetic strengths and beliefs)",
+            "target_expl_pot": target, "check_every": block, "solves": out}
+
+
 def measure_warmstart(train_games: int = 20480, per_game: int = 64, heldout: int = 512, epochs: int = 12,
                       kappa: float = 0.02, t0: int = 0):
     """Learned warm start: equilibria of `train_games` river endgames (the
@@ -578,7 +617,8 @@ def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec):
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_seconds)
     if not args.no_secondary:
         for key, fn in (("batched", lambda: measure_batch(args.games, 10, 3)), ("solver", measure_solver),
-                        ("technique_b", measure_factors), ("libratus", measure_libratus)):
+                        ("technique_b", measure_factors), ("libratus", measure_libratus),
+                        ("libratus_solve", lambda: measure_libratus_solve(seeds=(2, 3)))):
             try:
                 line[key] = fn()
             except Exception as exc:   # reported, never silently dropped
@@ -602,6 +642,10 @@ def main():
         import torch
         torch.cuda.set_device(_dist()[2])
         print(json.dumps(measure_solver()), flush=True)
+    elif args.workload == "libratus_solve":
+        import torch
+        torch.cuda.set_device(_dist()[2])
+        print(json.dumps(measure_libratus_solve()), flush=True)
     elif args.workload == "libratus":
         import torch
         torch.cuda.set_device(_dist()[2])

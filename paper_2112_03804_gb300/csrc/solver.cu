@@ -53,7 +53,7 @@ using namespace kps_abi;
 
 namespace {
 
-constexpr int kThreads = 64;     // hands per block
+constexpr int kThreads = 64;     // hands per block (32 for trees whose sequences need more shared memory)
 constexpr int kMaxActions = 12;  // fold, check/call, up to 8 bets, all-in
 
 struct SolverGame {
@@ -89,10 +89,11 @@ struct Where {
     int game, h;
 };
 
+template <int BW>
 __device__ __forceinline__ Where locate(const SolverGame *games, const int *block_game) {
     Where w;
     w.game = block_game[blockIdx.x];
-    w.h = (blockIdx.x - games[w.game].block0) * kThreads + threadIdx.x;
+    w.h = (blockIdx.x - games[w.game].block0) * BW + threadIdx.x;
     return w;
 }
 
@@ -144,15 +145,15 @@ struct UpdateArgs {
 // walks run in shared memory (child values are added into the parent's
 // value slot, which the walk reads after all children; the slots then take
 // the new sequence form), and regrets and strategy are written back last.
-template <typename S, typename C>
-__global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S, C> u) {
+template <typename S, typename C, int BW>
+__global__ void __launch_bounds__(BW) rm_update_kernel(const UpdateArgs<S, C> u) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Where w = locate(u.games, u.block_game);
+    const Where w = locate<BW>(u.games, u.block_game);
     const SolverGame &G = u.games[w.game];
     if (w.h >= G.H) return;
     const int p = u.player, n = G.n[p], hs = G.hs;
-    C *qv = reinterpret_cast<C *>(smem_raw) + threadIdx.x;      // [s * kThreads]
-    C *rg = qv + (size_t)u.nmax * kThreads;
+    C *qv = reinterpret_cast<C *>(smem_raw) + threadIdx.x;      // [s * BW]
+    C *rg = qv + (size_t)u.nmax * BW;
     const long long base = G.off[p] + w.h;
     const S *__restrict__ gp = u.g + base;
     C *__restrict__ Rp = u.regret + base;
@@ -174,8 +175,8 @@ __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S,
 #pragma unroll 4
     for (int s = 0; s < n; ++s) {
         const long long i = (long long)s * hs;
-        qv[s * kThreads] = u.sign * C(Cv<S>::ld(gp + i));
-        rg[s * kThreads] = Rp[i];
+        qv[s * BW] = u.sign * C(Cv<S>::ld(gp + i));
+        rg[s * BW] = Rp[i];
         xsp[i] += wt * C(Cv<S>::ld(xp + i));
     }
     // bottom-up: values and regrets
@@ -186,8 +187,8 @@ __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S,
 #pragma unroll
         for (int a = 0; a < kMaxActions; ++a)
             if (a < na) {
-                r[a] = rg[(s0 + a) * kThreads];
-                q[a] = qv[(s0 + a) * kThreads];
+                r[a] = rg[(s0 + a) * BW];
+                q[a] = qv[(s0 + a) * BW];
             }
         if (init) {
 #pragma unroll
@@ -204,9 +205,9 @@ __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S,
         for (int a = 0; a < kMaxActions; ++a)
             if (a < na) {
                 const C rn = r[a] + q[a] - v;
-                rg[(s0 + a) * kThreads] = u.method == 0 ? (rn > C(0) ? rn : C(0)) : rn * (rn > C(0) ? dpos : dneg);
+                rg[(s0 + a) * BW] = u.method == 0 ? (rn > C(0) ? rn : C(0)) : rn * (rn > C(0) ? dpos : dneg);
             }
-        if (par >= 0) qv[par * kThreads] += v;
+        if (par >= 0) qv[par * BW] += v;
     }
     // top-down: next behavioural strategy and its sequence form
     for (int k = 0; k < nn; ++k) {
@@ -215,30 +216,30 @@ __global__ void __launch_bounds__(kThreads) rm_update_kernel(const UpdateArgs<S,
         C r[kMaxActions], b[kMaxActions];
 #pragma unroll
         for (int a = 0; a < kMaxActions; ++a)
-            if (a < na) r[a] = rg[(s0 + a) * kThreads];
+            if (a < na) r[a] = rg[(s0 + a) * BW];
         regret_match<C>(r, na, b, theta);
-        const C xpar = par >= 0 ? qv[par * kThreads] : C(1);
+        const C xpar = par >= 0 ? qv[par * BW] : C(1);
 #pragma unroll
         for (int a = 0; a < kMaxActions; ++a)
-            if (a < na) qv[(s0 + a) * kThreads] = xpar * b[a];
+            if (a < na) qv[(s0 + a) * BW] = xpar * b[a];
     }
     // regrets and strategy back
 #pragma unroll 4
     for (int s = 0; s < n; ++s) {
         const long long i = (long long)s * hs;
-        Rp[i] = rg[s * kThreads];
-        xp[i] = Cv<S>::st(qv[s * kThreads]);
+        Rp[i] = rg[s * BW];
+        xp[i] = Cv<S>::st(qv[s * BW]);
     }
 }
 
 // Start of a run: x <- sequence form of the initial behavioural strategy
 // beh0 (uniform if none); with a warm start also R <- kappa V_p beh0 (so that
 // regret matching returns beh0) and xsum <- w0 x.
-template <typename S, typename C>
-__global__ void __launch_bounds__(kThreads) seqform_kernel(const UpdateArgs<S, C> u, int has_beh) {
+template <typename S, typename C, int BW>
+__global__ void __launch_bounds__(BW) seqform_kernel(const UpdateArgs<S, C> u, int has_beh) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    const Where w = locate(u.games, u.block_game);
+    const Where w = locate<BW>(u.games, u.block_game);
     const SolverGame &G = u.games[w.game];
     if (w.h >= G.H) return;
     const int p = u.player, hs = G.hs, tid = threadIdx.x;
@@ -248,11 +249,11 @@ __global__ void __launch_bounds__(kThreads) seqform_kernel(const UpdateArgs<S, C
     for (int k = 0; k < G.nnodes[p]; ++k) {
         const int4 nd = nodes[k];
         const int s0 = nd.x, na = nd.y, par = nd.z;
-        const C xp = par >= 0 ? buf[par * kThreads + tid] : C(1);
+        const C xp = par >= 0 ? buf[par * BW + tid] : C(1);
         for (int a = 0; a < na; ++a) {
             const long long i = base + (long long)(s0 + a) * hs;
             const C b = has_beh ? C(u.beh0[i]) : C(1) / C(na);
-            buf[(s0 + a) * kThreads + tid] = xp * b;
+            buf[(s0 + a) * BW + tid] = xp * b;
             u.x[i] = Cv<S>::st(xp * b);
             u.regret[i] = rscale * b;
             u.xsum[i] = u.w0 * C(Cv<S>::ld(u.x + i));
@@ -269,9 +270,9 @@ __global__ void bump_kernel(long long *iter, double *wsum, int method, const dou
 // FP64 averages: sequence form xsum / sum_t t (the current strategy before
 // any iteration), or behavioural (x[sigma] / x[parent], uniform where the
 // parent is never reached).
-template <typename S, typename C, typename O>
-__global__ void __launch_bounds__(kThreads) average_kernel(const UpdateArgs<S, C> u, O *out, int behavioural) {
-    const Where w = locate(u.games, u.block_game);
+template <typename S, typename C, typename O, int BW>
+__global__ void __launch_bounds__(BW) average_kernel(const UpdateArgs<S, C> u, O *out, int behavioural) {
+    const Where w = locate<BW>(u.games, u.block_game);
     const SolverGame &G = u.games[w.game];
     if (w.h >= G.H) return;
     const int p = u.player, hs = G.hs;
@@ -309,11 +310,11 @@ struct BrArgs {
 // actions on the values loaded into shared memory ([sequence][thread]; a
 // child's value is added into its parent's slot, read after all children);
 // the sum over the block's hands goes to partial[block].
-template <typename V>
-__global__ void __launch_bounds__(kThreads) best_response_kernel(const BrArgs a) {
+template <typename V, int BW>
+__global__ void __launch_bounds__(BW) best_response_kernel(const BrArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[kThreads];
-    const Where w = locate(a.games, a.block_game);
+    __shared__ double red[BW];
+    const Where w = locate<BW>(a.games, a.block_game);
     const SolverGame &G = a.games[w.game];
     double root = 0.0;
     if (w.h < G.H) {
@@ -321,23 +322,23 @@ __global__ void __launch_bounds__(kThreads) best_response_kernel(const BrArgs a)
         const V *__restrict__ gp = static_cast<const V *>(a.g) + G.off[p] + w.h;
         double *qv = reinterpret_cast<double *>(smem_raw) + threadIdx.x;
 #pragma unroll 4
-        for (int s = 0; s < n; ++s) qv[s * kThreads] = a.sign * (double)gp[(long long)s * hs];
+        for (int s = 0; s < n; ++s) qv[s * BW] = a.sign * (double)gp[(long long)s * hs];
         const int4 *nodes = a.nodes + G.node_off[p];
         for (int k = G.nnodes[p] - 1; k >= 0; --k) {
             const int4 nd = nodes[k];
             const int s0 = nd.x, na = nd.y, par = nd.z;
             double v = -1e300;
             for (int q = 0; q < na; ++q) {
-                const double val = qv[(s0 + q) * kThreads];
+                const double val = qv[(s0 + q) * BW];
                 v = val > v ? val : v;
             }
-            if (par >= 0) qv[par * kThreads] += v;
+            if (par >= 0) qv[par * BW] += v;
             else root += v;
         }
     }
     red[threadIdx.x] = root;
     __syncthreads();
-    for (int st = kThreads / 2; st > 0; st >>= 1) {
+    for (int st = BW / 2; st > 0; st >>= 1) {
         if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
         __syncthreads();
     }
@@ -366,6 +367,7 @@ struct kps_solver {
     kps_batch *batch = nullptr;
     kps_dtype dt = KPS_F32;
     int nblocks = 0, nmax = 0;
+    int bw = kThreads;              // hands per block of the node kernels
     void *blob = nullptr;           // games, block_game, nblocks, nodes
     SolverGame *games = nullptr;
     int *block_game = nullptr, *game_blocks = nullptr;
@@ -437,34 +439,38 @@ template <typename S, typename C, typename K>
 cudaError_t launch_node_kernel(kps_solver *s, K kernel, const UpdateArgs<S, C> &u, size_t smem, cudaStream_t st) {
     cudaError_t e = smem_limit(reinterpret_cast<const void *>(kernel), smem);
     if (e != cudaSuccess) return e;
-    kernel<<<s->nblocks, kThreads, smem, st>>>(u);
+    kernel<<<s->nblocks, s->bw, smem, st>>>(u);
     return cudaGetLastError();
 }
 
 template <typename S, typename C>
 cudaError_t update_t(kps_solver *s, int p, cudaStream_t st) {
-    const size_t smem = 2 * (size_t)s->nmax * kThreads * sizeof(C);
-    return launch_node_kernel(s, rm_update_kernel<S, C>, make_args<S, C>(s, p), smem, st);
+    const size_t smem = 2 * (size_t)s->nmax * s->bw * sizeof(C);
+    return launch_node_kernel(s, s->bw == kThreads ? rm_update_kernel<S, C, kThreads> : rm_update_kernel<S, C, kThreads / 2>,
+                              make_args<S, C>(s, p), smem, st);
 }
 
 template <typename S, typename C>
 cudaError_t seqform_t(kps_solver *s, int p, cudaStream_t st) {
-    const size_t smem = (size_t)s->nmax * kThreads * sizeof(C);
-    cudaError_t e = smem_limit(reinterpret_cast<const void *>(seqform_kernel<S, C>), smem);
+    const size_t smem = (size_t)s->nmax * s->bw * sizeof(C);
+    auto kern = s->bw == kThreads ? seqform_kernel<S, C, kThreads> : seqform_kernel<S, C, kThreads / 2>;
+    cudaError_t e = smem_limit(reinterpret_cast<const void *>(kern), smem);
     if (e != cudaSuccess) return e;
-    seqform_kernel<S, C><<<s->nblocks, kThreads, smem, st>>>(make_args<S, C>(s, p), s->has_beh);
+    kern<<<s->nblocks, s->bw, smem, st>>>(make_args<S, C>(s, p), s->has_beh);
     return cudaGetLastError();
 }
 
 template <typename S, typename C>
 cudaError_t average_t(kps_solver *s, int p, double *out, int behavioural, cudaStream_t st) {
-    average_kernel<S, C, double><<<s->nblocks, kThreads, 0, st>>>(make_args<S, C>(s, p), out, behavioural);
+    auto kern = s->bw == kThreads ? average_kernel<S, C, double, kThreads> : average_kernel<S, C, double, kThreads / 2>;
+    kern<<<s->nblocks, s->bw, 0, st>>>(make_args<S, C>(s, p), out, behavioural);
     return cudaGetLastError();
 }
 
 template <typename S, typename C>
 cudaError_t average32_t(kps_solver *s, int p, float *out, cudaStream_t st) {
-    average_kernel<S, C, float><<<s->nblocks, kThreads, 0, st>>>(make_args<S, C>(s, p), out, 0);
+    auto kern = s->bw == kThreads ? average_kernel<S, C, float, kThreads> : average_kernel<S, C, float, kThreads / 2>;
+    kern<<<s->nblocks, s->bw, 0, st>>>(make_args<S, C>(s, p), out, 0);
     return cudaGetLastError();
 }
 
@@ -545,6 +551,14 @@ kps_status kps_solver_create(kps_batch *b, kps_dtype dt, kps_solver **out) {
     s->batch = b;
     s->dt = dt;
     const int ng = (int)b->games.size();
+    // hands per block: 64, or 32 when the values and regrets of every
+    // sequence of 64 hands do not fit in shared memory
+    {
+        int nm = 0;
+        for (kps_game *g : b->games) nm = std::max(nm, std::max(g->host.n[0], g->host.n[1]));
+        const size_t per = 2 * (size_t)nm * std::max<size_t>(compute_size(dt), 8);
+        if (per * kThreads > (size_t)kps::max_dyn_smem()) s->bw = kThreads / 2;
+    }
     std::vector<SolverGame> games(ng);
     std::vector<int> block_game, game_blocks(ng);
     std::vector<int4> nodes;
@@ -568,7 +582,7 @@ kps_status kps_solver_create(kps_batch *b, kps_dtype dt, kps_solver **out) {
                 G.theta[p] = eps * G.V[p];
             }
         }
-        const int nb = (h.H + kThreads - 1) / kThreads;
+        const int nb = (h.H + s->bw - 1) / s->bw;
         game_blocks[i] = nb;
         for (int k = 0; k < nb; ++k) block_game.push_back(i);
         for (int p = 0; p < 2; ++p) {
@@ -593,7 +607,7 @@ kps_status kps_solver_create(kps_batch *b, kps_dtype dt, kps_solver **out) {
     }
     s->nblocks = (int)block_game.size();
     const size_t csz = compute_size(dt);
-    if (2 * (size_t)s->nmax * kThreads * std::max<size_t>(csz, 8) > (size_t)kps::max_dyn_smem()) {
+    if (2 * (size_t)s->nmax * s->bw * std::max<size_t>(csz, 8) > (size_t)kps::max_dyn_smem()) {
         free_solver(s);
         return fail(KPS_ENOTSUP, "too many sequences per player for the solver's shared memory");
     }
@@ -809,9 +823,11 @@ kps_status exploitability_impl(kps_solver *s, bool f32, double *expl, double *br
     kps_status r = batch_matvec(s->batch, 0, s->xa[1], s->g64[0], pd, st);
     if (r == KPS_OK) r = batch_matvec(s->batch, 1, s->xa[0], s->g64[1], pd, st);
     if (r != KPS_OK) return r;
-    const size_t smem = (size_t)s->nmax * kThreads * sizeof(double);
-    const void *kern = f32 ? reinterpret_cast<const void *>(best_response_kernel<float>)
-                           : reinterpret_cast<const void *>(best_response_kernel<double>);
+    const size_t smem = (size_t)s->nmax * s->bw * sizeof(double);
+    const bool wide = s->bw == kThreads;
+    auto kf = wide ? best_response_kernel<float, kThreads> : best_response_kernel<float, kThreads / 2>;
+    auto kd = wide ? best_response_kernel<double, kThreads> : best_response_kernel<double, kThreads / 2>;
+    const void *kern = f32 ? reinterpret_cast<const void *>(kf) : reinterpret_cast<const void *>(kd);
     cudaError_t e = smem_limit(kern, smem);
     if (e != cudaSuccess) return cuda_fail(e, "best response");
     for (int p = 0; p < 2; ++p) {
@@ -823,8 +839,8 @@ kps_status exploitability_impl(kps_solver *s, bool f32, double *expl, double *br
         a.sign = p == 0 ? 1.0 : -1.0;
         a.g = s->g64[p];
         a.partial = s->partial[p];
-        if (f32) best_response_kernel<float><<<s->nblocks, kThreads, smem, st>>>(a);
-        else best_response_kernel<double><<<s->nblocks, kThreads, smem, st>>>(a);
+        if (f32) kf<<<s->nblocks, s->bw, smem, st>>>(a);
+        else kd<<<s->nblocks, s->bw, smem, st>>>(a);
     }
     const int ng = (int)s->batch->games.size();
     expl_kernel<<<(ng + 127) / 128, 128, 0, st>>>(s->games, ng, s->game_blocks, s->partial[0], s->partial[1], expl, br1,

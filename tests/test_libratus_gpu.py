@@ -56,3 +56,20 @@ def test_fp64_rmplus_matches_oracle():
     torch.cuda.synchronize()
     e_or = og.rmplus(30)[0]
     assert abs(float(e.item()) - e_or) <= 1e-9 * max(1.0, abs(e_or))
+
+
+def test_fp64_rmplus_large_tree_matches_oracle():
+    """247 sequences per player (1000-chip pot): the solver runs its node
+    kernels with 32 hands per block so that every sequence of a hand fits in
+    shared memory."""
+    spec = synth.libratus_spec(seed=7, ranks=5, suits=2, nboard=2)
+    og = OracleGame(spec)
+    assert og.n1 == 247
+    b = kps.Batch([kps.Game(spec)])
+    s = kps.Solver(b, kps.F64)
+    s.step(30)
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s.exploitability(e)
+    torch.cuda.synchronize()
+    e_or = og.rmplus(30)[0]
+    assert abs(float(e.item()) - e_or) <= 1e-9 * max(1.0, abs(e_or))
