@@ -419,14 +419,53 @@ kps_status matvec_host(kps_game *g, int dir, const void *vin, void *vout, int32_
         if (e != cudaSuccess) return fail(KPS_ENOMEM, "staging buffer");
         g->stage_out_bytes = out_bytes;
     }
-    e = cudaMemcpyAsync(g->stage_in, vin, in_bytes, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "copying input to the device");
-    kps_status st = matvec(g, dir, g->stage_in, g->stage_out, batch, dt, stream_ptr);
-    if (st != KPS_OK) return st;
-    e = cudaMemcpyAsync(vout, g->stage_out, out_bytes, cudaMemcpyDeviceToHost, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "copying output to the host");
-    e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) return cuda_fail(e, "synchronising");
+    // The batch goes in chunks of vectors: chunk c's copy in, product and
+    // copy out run on three streams ordered by per-chunk events, so the two
+    // copy directions and the products of neighbouring chunks overlap.  All
+    // three streams start after the work already queued on `stream`.
+    if (!g->host_streams) {
+        for (auto &hs_ : g->hstream)
+            if ((e = cudaStreamCreateWithFlags(&hs_, cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(e, "creating copy streams");
+        if ((e = cudaEventCreateWithFlags(&g->hentry, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "creating events");
+        for (int c = 0; c < kps_game::kHostChunks; ++c)
+            if ((e = cudaEventCreateWithFlags(&g->hin[c], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&g->hdone[c], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "creating events");
+        g->host_streams = true;
+    }
+    cudaStream_t s_in = g->hstream[0], s_mv = g->hstream[1], s_out = g->hstream[2];
+    if ((e = cudaEventRecord(g->hentry, stream)) != cudaSuccess) return cuda_fail(e, "ordering the copies");
+    for (cudaStream_t q : {s_in, s_mv, s_out})
+        if ((e = cudaStreamWaitEvent(q, g->hentry, 0)) != cudaSuccess) return cuda_fail(e, "ordering the copies");
+    const int nch = std::min(kps_game::kHostChunks, (int)batch);
+    const size_t vin_bytes = in_bytes / batch, vout_bytes = out_bytes / batch;
+    for (int c = 0; c < nch; ++c) {
+        const size_t b0 = (size_t)batch * c / nch, b1 = (size_t)batch * (c + 1) / nch;
+        char *din = static_cast<char *>(g->stage_in) + b0 * vin_bytes;
+        char *dout = static_cast<char *>(g->stage_out) + b0 * vout_bytes;
+        e = cudaMemcpyAsync(din, static_cast<const char *>(vin) + b0 * vin_bytes, (b1 - b0) * vin_bytes,
+                            cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(g->hin[c], s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_mv, g->hin[c], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "copying input to the device");
+        kps_status st = matvec(g, dir, din, dout, (int32_t)(b1 - b0), dt, s_mv);
+        if (st != KPS_OK) {
+            cudaStreamSynchronize(s_in);
+            cudaStreamSynchronize(s_mv);
+            cudaStreamSynchronize(s_out);
+            return st;
+        }
+        e = cudaEventRecord(g->hdone[c], s_mv);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, g->hdone[c], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(static_cast<char *>(vout) + b0 * vout_bytes, dout, (b1 - b0) * vout_bytes,
+                                cudaMemcpyDeviceToHost, s_out);
+        if (e != cudaSuccess) return cuda_fail(e, "copying output to the host");
+    }
+    for (cudaStream_t q : {s_in, s_mv, s_out})
+        if ((e = cudaStreamSynchronize(q)) != cudaSuccess) return cuda_fail(e, "synchronising");
     return KPS_OK;
 }
 
@@ -464,6 +503,15 @@ kps_status kps_game_destroy(kps_game *g) {
     if (g->dev.blob) cudaFree(g->dev.blob);
     if (g->stage_in) cudaFree(g->stage_in);
     if (g->stage_out) cudaFree(g->stage_out);
+    if (g->host_streams) {
+        for (cudaStream_t q : g->hstream)
+            if (q) cudaStreamDestroy(q);
+        if (g->hentry) cudaEventDestroy(g->hentry);
+        for (int c = 0; c < kps_game::kHostChunks; ++c) {
+            if (g->hin[c]) cudaEventDestroy(g->hin[c]);
+            if (g->hdone[c]) cudaEventDestroy(g->hdone[c]);
+        }
+    }
     if (g->scratch) cudaFree(g->scratch);
     for (auto &kv : g->tiles) cudaFree(kv.second.dev);
     delete g;

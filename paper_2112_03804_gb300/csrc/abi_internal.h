@@ -44,6 +44,12 @@ struct kps_game {
     kps_abi::DeviceTables dev;
     void *stage_in = nullptr, *stage_out = nullptr;
     size_t stage_in_bytes = 0, stage_out_bytes = 0;
+    // host-buffer products: streams for copies in, products and copies out,
+    // and one event per chunk and stage (created on first use)
+    static constexpr int kHostChunks = 8;
+    bool host_streams = false;
+    cudaStream_t hstream[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t hentry = nullptr, hin[kHostChunks] = {}, hdone[kHostChunks] = {};
     // tie-aligned tile lists on the device, per warp count
     struct Tiles {
         int2 *dev = nullptr;          // tile list, then tie work, then tie entries (one allocation)

@@ -161,6 +161,34 @@ def test_host_buffer_variant(river):
     assert normwise_error(got, og.matvec_A(y.astype(np.float64))) <= 1e-5
 
 
+def test_host_buffer_chunks_match_device_path(river):
+    """37 vectors (eight uneven chunks on the copy/product/copy streams), both
+    directions: within the FP32 bound of the oracle, and equal bit for bit
+    to the device-resident product launched on the same chunks of vectors
+    (the copies neither lose nor reorder data; a single 37-vector launch
+    groups columns into tiles differently, and a tile's column kinds select
+    the scan variant, so it may differ in the last bit)."""
+    spec, og, g, order = river
+    inf = g.info()
+    batch, nch = 37, 8
+    bounds = [batch * c // nch for c in range(nch + 1)]
+    for transpose in (False, True):
+        n_out = inf["n2"] if transpose else inf["n1"]
+        v = _inputs(og, batch, seed=61, transpose=transpose).astype(np.float32)
+        vl = np.ascontiguousarray(to_library(v, order, inf["hs"]))
+        out = np.zeros((batch, n_out, inf["hs"]), dtype=np.float32)
+        (kps.matvec_AT_host if transpose else kps.matvec_A_host)(g, vl, out, batch, kps.F32)
+        want = og.matvec_AT(v.astype(np.float64)) if transpose else og.matvec_A(v.astype(np.float64))
+        assert normwise_error(from_library(out, order, inf["H"]), want) <= 1e-5
+        vd = torch.from_numpy(vl).cuda()
+        dev = torch.empty((batch, n_out, inf["hs"]), device="cuda")
+        for c in range(nch):
+            b0, b1 = bounds[c], bounds[c + 1]
+            (kps.matvec_AT if transpose else kps.matvec_A)(g, vd[b0:b1], dev[b0:b1], b1 - b0)
+        torch.cuda.synchronize()
+        assert np.array_equal(out, dev.cpu().numpy())
+
+
 def test_overlap_rejected(river):
     spec, og, g, order = river
     inf = g.info()
