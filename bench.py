@@ -479,7 +479,8 @@ def measure_libratus_solve(target: float = 1e-3, block: int = 10, max_iters: int
     hands, 247 + 247 sequences at a 1000-chip pot) to `target` of the pot:
     the paper's GPU claim is stated per endgame (Sec. 5).  DCFR (1.5, 0, 2)
     and RM+, FP32 storage, FP64 exploitability of the averages checked every
-    `block` iterations (inside the timed region); one game per solver."""
+    `block` iterations (inside the timed region); one game per solver.  The
+    same number of iterations is then timed again without the checks."""
     import torch
     from paper_2112_03804_gb300 import kps, synth
     out = {}
@@ -505,7 +506,17 @@ def measure_libratus_solve(target: float = 1e-3, block: int = 10, max_iters: int
                 v = float(e.item())
                 if v < target:
                     break
-            rows.append({"seed": seed, "iterations": it, "expl": v, "seconds": time.perf_counter() - t0})
+            secs = time.perf_counter() - t0
+            # the same iterations again without the checks (one graph launch)
+            s.reset()
+            s.step(it)
+            s.reset()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            s.step(it)
+            torch.cuda.synchronize()
+            rows.append({"seed": seed, "iterations": it, "expl": v, "seconds": secs,
+                         "seconds_without_checks": time.perf_counter() - t1})
             s.close()
         out[name] = rows
     return {"workload": "one river endgame with the Libratus betting menus per solve: 1081 hands, 247+247 "
