@@ -89,11 +89,13 @@ cudaError_t launch_vec_scan(const FastParams &p, int storage, int cards_per_hand
 namespace kps {
 
 // Tensor-memory path (FP32 arithmetic; FP32/BF16/FP16 storage): partial
-// results stay on chip.  A warp owns kTmemRegion tensor-memory columns (one
-// per hand, written 16 hands at a time from a tile's offset in the chunk)
-// for every tile of its chunk but the last, whose partial results stay in
-// shared memory.  `scratch` is unused.
+// results stay on chip.  A warp keeps one column per hand (written 16 hands
+// at a time from a tile's offset in the chunk) for every tile of its chunk
+// but the last: columns below kTmemRegion in tensor memory, the next
+// kTmemSpill in spill rows of its shared-memory partial tile; the last
+// tile's partial results stay in the partial tile.  `scratch` is unused.
 constexpr int kTmemRegion = 256;
+constexpr int kTmemSpill = 16;
 
 // Does a chunk fit?  `tile(i)` gives the (start, length) of its i-th of n
 // tiles.
@@ -103,7 +105,7 @@ inline bool tmem_chunk_fits(int n, TileAt tile) {
     const int cs = tile(0).first;
     for (int i = 0; i + 1 < n; ++i) {
         const auto t = tile(i);
-        if (t.first - cs + (t.second + 15) / 16 * 16 > kTmemRegion) return false;
+        if (t.first - cs + (t.second + 15) / 16 * 16 > kTmemRegion + kTmemSpill) return false;
     }
     return true;
 }

@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 namespace kps {
@@ -84,6 +85,14 @@ __device__ __forceinline__ void tm_wait_ld16(float *r) {
                    "+f"(r[8]), "+f"(r[9]), "+f"(r[10]), "+f"(r[11]), "+f"(r[12]), "+f"(r[13]), "+f"(r[14]), "+f"(r[15])::"memory");
 }
 
+// one column of this warp's lanes <-> v
+__device__ __forceinline__ void tm_st1(uint32_t taddr, float v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "f"(v));
+}
+__device__ __forceinline__ void tm_ld1(uint32_t taddr, float &v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=f"(v) : "r"(taddr));
+}
+
 // 16 consecutive tensor-memory columns of this warp's lanes <-> r[0..15]
 __device__ __forceinline__ void tm_st16(uint32_t taddr, const float *r) {
     asm volatile(
@@ -102,13 +111,16 @@ __device__ __forceinline__ void tm_ld16(uint32_t taddr, float *r) {
 
 // Shared memory: header (columns, coefficients, per-warp sums, the tensor-
 // memory slot, per-warp tile descriptors) then, per warp, state [nc][32]
-// float2, stage [32][kPitch] float2 and a [32][kPitch] float tile.
+// float2, stage [32][kPitch] float2 and a [32 + kTmemSpill][kPitch] float
+// tile (rows 32.. hold the columns kTmemRegion.. of the tensor-memory tiles).
 constexpr int kTlCache = 16;       // tile descriptors of a chunk kept in shared memory
 __host__ __device__ inline size_t tm_tls_offset(int nw) {
     return (32 * sizeof(Col) + (2 * 32 + (size_t)nw * 3 * 32) * sizeof(float) + 16 + 15) & ~(size_t)15;
 }
 __host__ __device__ inline size_t tm_header_bytes(int nw) { return tm_tls_offset(nw) + (size_t)nw * kTlCache * 8; }
-__host__ __device__ inline size_t tm_warp_floats(int nc) { return 2 * (size_t)nc * 32 + 3 * 32 * kPitch; }
+__host__ __device__ inline size_t tm_warp_floats(int nc) {
+    return 2 * (size_t)nc * 32 + (3 * 32 + kTmemSpill) * kPitch;
+}
 
 struct Cta {
     const Col *ci;
@@ -322,8 +334,17 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
             // columns past the tile's end are rewritten by the next tile),
             // the last tile's to the partial tile, where the finishing pass
             // takes them first
-            if (t + 1 < te) {
-                tm_st16(treg + (uint32_t)(t0 - cstart + 16 * half), r);
+            const int c0 = t0 - cstart + 16 * half;
+            if (t + 1 < te && c0 + 16 <= kRegion) {
+                tm_st16(treg + (uint32_t)c0, r);
+            } else if (t + 1 < te) {
+                // a half crossing the end of the tensor-memory region: its
+                // columns past the end go to the spill rows
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    if (c0 + k < kRegion) tm_st1(treg + (uint32_t)(c0 + k), r[k]);
+                    else ptile[(32 + c0 + k - kRegion) * kPitch + lane] = r[k];
+                }
             } else {
 #pragma unroll
                 for (int k = 0; k < 16; ++k) ptile[(16 * half + k) * kPitch + lane] = r[k];
@@ -416,8 +437,15 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
         for (int half = 0; half < 2; ++half) {
             if (16 * half >= len) break;
             float r[16], za[16], zb[16];
-            if (i > 0) {
-                tm_ld16(treg + (uint32_t)(t0 - cstart + 16 * half), r);
+            const int c0 = t0 - cstart + 16 * half;
+            if (i > 0 && c0 + 16 <= kRegion) {
+                tm_ld16(treg + (uint32_t)c0, r);
+            } else if (i > 0) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    if (c0 + k < kRegion) tm_ld1(treg + (uint32_t)(c0 + k), r[k]);
+                    else r[k] = ptile[(32 + c0 + k - kRegion) * kPitch + lane];
+                }
             } else {
 #pragma unroll
                 for (int k = 0; k < 16; ++k) r[k] = ptile[(16 * half + k) * kPitch + lane];
@@ -623,10 +651,26 @@ cudaError_t launch_multi_t(const MultiParams &m, size_t smem, int grid, cudaStre
 
 template <typename S, int K2>
 int ctas_t(size_t smem, int nw) {
+    // Resident CTAs per SM from the SM's limits: shared memory (1 KB
+    // reserved per CTA), registers (allocated per warp in units of 256) and
+    // thread slots.  The runtime's occupancy query reports one CTA per SM for
+    // this kernel at every size, while two 4-warp CTAs do run side by side
+    // (measured), so it is not used.
     auto fn = tmem_multi_kernel<S, K2>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * nw, smem) != cudaSuccess) return 0;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 0;
+    int dev = 0, sm_smem = 0, sm_regs = 0, sm_threads = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm_threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
+        return 0;
+    const size_t per_cta_smem = smem + fa.sharedSizeBytes + 1024;
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+    int n = (int)((size_t)sm_smem / per_cta_smem);
+    n = std::min(n, sm_regs / (warp_regs * nw));
+    n = std::min(n, sm_threads / (32 * nw));
     return n;
 }
 
