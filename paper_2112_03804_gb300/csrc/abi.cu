@@ -152,7 +152,7 @@ kps_status tiles_for(kps_game *g, int nw, cudaStream_t stream, const kps_game::T
     auto it = g->tiles.find(nw);
     if (it == g->tiles.end()) {
         kps_game::Tiles t;
-        std::vector<std::pair<int, int>> tl = kps::tie_tiles(g->host, nw, kps::kTile, t.tchunk);
+        std::vector<std::pair<int, int>> tl = layout_tiles(g->host, nw, t.tchunk, &t.spill);
         std::vector<int2> host(tl.size());
         for (size_t i = 0; i < tl.size(); ++i) host[i] = make_int2(tl[i].first, tl[i].second);
         t.host = host;
@@ -187,23 +187,45 @@ kps_status tiles_for(kps_game *g, int nw, cudaStream_t stream, const kps_game::T
     return KPS_OK;
 }
 
+namespace {
+bool list_fits(const std::vector<std::pair<int, int>> &tl, const std::vector<int> &tchunk, int nw, int limit) {
+    for (int k = 0; k < nw; ++k) {
+        const int a = tchunk[k];
+        if (!kps::tmem_chunk_fits(tchunk[k + 1] - a, [&](int i) { return tl[a + i]; }, limit)) return false;
+    }
+    return true;
+}
+}  // namespace
+
+std::vector<std::pair<int, int>> layout_tiles(const kps::HostGame &h, int nw, std::vector<int> &tchunk, bool *spill) {
+    *spill = false;
+    std::vector<std::pair<int, int>> tl = kps::tie_tiles(h, nw, kps::kTile, tchunk);
+    if (list_fits(tl, tchunk, nw, kps::kTmemRegion)) return tl;
+    std::vector<int> tc2;
+    std::vector<std::pair<int, int>> tl2 = kps::tie_tiles(h, nw, kps::kTile, tc2, true);
+    if (h.k == 2 && list_fits(tl2, tc2, nw, kps::kTmemRegion + kps::kTmemSpill)) {
+        tchunk = tc2;
+        *spill = true;
+        return tl2;
+    }
+    return tl;
+}
+
 bool tmem_chunks_fit(const kps_game::Tiles &t, int nw) {
+    const int limit = kps::kTmemRegion + (t.spill ? kps::kTmemSpill : 0);
     for (int k = 0; k < nw; ++k) {
         const int a = t.tchunk[k];
         auto at = [&](int i) { return std::make_pair(t.host[a + i].x, t.host[a + i].y); };
-        if (!kps::tmem_chunk_fits(t.tchunk[k + 1] - a, at)) return false;
+        if (!kps::tmem_chunk_fits(t.tchunk[k + 1] - a, at, limit)) return false;
     }
     return true;
 }
 
 bool tmem_split_fits(const kps::HostGame &h, int nw) {
     std::vector<int> tchunk;
-    const std::vector<std::pair<int, int>> tl = kps::tie_tiles(h, nw, kps::kTile, tchunk);
-    for (int k = 0; k < nw; ++k) {
-        const int a = tchunk[k];
-        if (!kps::tmem_chunk_fits(tchunk[k + 1] - a, [&](int i) { return tl[a + i]; })) return false;
-    }
-    return true;
+    bool spill = false;
+    const std::vector<std::pair<int, int>> tl = layout_tiles(h, nw, tchunk, &spill);
+    return list_fits(tl, tchunk, nw, kps::kTmemRegion + (spill ? kps::kTmemSpill : 0));
 }
 
 int tmem_warps(kps_game *g, int nc) {
@@ -310,6 +332,7 @@ kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int stor
     p.tiles = tiles->dev;
     p.tie_work = tiles->tie_work;
     p.tie_trip = tiles->tie_trip;
+    p.spill = tiles->spill ? 1 : 0;
     p.nw = nw;
     for (int i = 0; i <= nw; ++i) p.tchunk[i] = tiles->tchunk[i];
     (void)dir;

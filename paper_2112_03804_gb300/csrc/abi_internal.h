@@ -57,6 +57,7 @@ struct kps_game {
         uint32_t *tie_trip = nullptr;
         std::vector<int2> host;
         std::vector<int> tchunk;
+        bool spill = false;           // cut from the chunk ends, spill rows in use
     };
     std::map<int, Tiles> tiles;
     // warps per CTA of the tensor-memory path (0 = not chosen yet)
@@ -80,6 +81,11 @@ kps_status tiles_for(kps_game *g, int nw, cudaStream_t stream, const kps_game::T
 // second builds the list on the host.
 bool tmem_chunks_fit(const kps_game::Tiles &t, int nw);
 bool tmem_split_fits(const kps::HostGame &h, int nw);
+
+// Tile list of `nw` chunks: cut from each chunk's start when every chunk
+// then fits the tensor-memory region, else from each chunk's end (a full
+// last tile) with the spill rows (*spill).
+std::vector<std::pair<int, int>> layout_tiles(const kps::HostGame &h, int nw, std::vector<int> &tchunk, bool *spill);
 
 // Warps per CTA of the tensor-memory path for a game with `nc` cards left:
 // four (two CTAs per SM, whose phases overlap) when the four-way split fits

@@ -69,6 +69,7 @@ kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t str
     std::vector<long long> tstart(ng + 1, 0), in_off(ng), out_off(ng);
     std::vector<int> tgame;
     int nc = 0;
+    bool any_spill = false;
     for (int i = 0; i < ng; ++i) {
         kps_game *g = b->games[i];
         const kps::HostGame &h = g->host;
@@ -96,6 +97,8 @@ kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t str
         p.tiles = t->dev;
         p.tie_work = t->tie_work;
         p.tie_trip = t->tie_trip;
+        p.spill = t->spill ? 1 : 0;
+        any_spill = any_spill || t->spill;
         p.nw = nw;
         for (int k = 0; k <= nw; ++k) p.tchunk[k] = t->tchunk[k];
         nc = std::max(nc, p.nc);
@@ -136,6 +139,7 @@ kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t str
     tb.m.total_tiles = (int)tstart[ng];
     tb.m.nw = nw;
     tb.m.nc = nc;
+    tb.m.spill = any_spill ? 1 : 0;
     tb.m.schedule = 0;
     *out = &b->tables.emplace(key, tb).first->second;
     return KPS_OK;

@@ -351,17 +351,24 @@ std::vector<int> chunk_bounds(const HostGame &g, int parts) {
 }
 
 std::vector<std::pair<int, int>> tie_tiles(const HostGame &g, int parts, int tile,
-                                           std::vector<int> &tchunk) {
+                                           std::vector<int> &tchunk, bool from_end) {
     std::vector<int> cb = chunk_bounds(g, parts);
     std::vector<std::pair<int, int>> tiles;
     tchunk.assign(parts + 1, 0);
-    // Tiles are cut from the end of each chunk, so that the short remainder
-    // is the chunk's first tile and its last tile is a full one (the
-    // tensor-memory kernel keeps the last tile's partial results in shared
-    // memory).
     std::vector<std::pair<int, int>> rev;
     for (int k = 0; k < parts; ++k) {
         tchunk[k] = (int)tiles.size();
+        if (!from_end) {
+            int s = cb[k];
+            while (s < cb[k + 1]) {
+                int e = std::min(s + tile, cb[k + 1]);
+                // back off to a tie-group boundary unless the tile ends the chunk
+                if (e < cb[k + 1] && g.group_lo[e] > s) e = g.group_lo[e];
+                tiles.emplace_back(s, e - s);
+                s = e;
+            }
+            continue;
+        }
         rev.clear();
         int e = cb[k + 1];
         while (e > cb[k]) {

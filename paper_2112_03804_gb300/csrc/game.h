@@ -114,11 +114,12 @@ void technique_b_factors(const HostGame &g, TechniqueB &f);
 std::vector<int> chunk_bounds(const HostGame &g, int parts);
 
 // Tiles of at most `tile` hands inside each chunk, never splitting a tie
-// group (requires max_tie <= tile), cut from the chunk's end (the first
-// tile of a chunk takes the remainder).  Returns (start, length) pairs; tchunk
-// receives parts+1 offsets into the tile list.
+// group (requires max_tie <= tile), cut from the chunk's start (the last
+// tile takes the remainder) or, with from_end, from its end (the first tile
+// takes the remainder).  Returns (start, length) pairs; tchunk receives
+// parts+1 offsets into the tile list.
 std::vector<std::pair<int, int>> tie_tiles(const HostGame &g, int parts, int tile,
-                                           std::vector<int> &tchunk);
+                                           std::vector<int> &tchunk, bool from_end = false);
 
 // Tie work of a tile list: for every tile, the ordered pairs (q, r), q != r,
 // of compatible hands (no shared card) in one tie group, packed as

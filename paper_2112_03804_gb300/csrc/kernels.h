@@ -69,6 +69,7 @@ struct FastParams {
     // r offsets in the tile.
     const int2 *tie_work;
     const uint32_t *tie_trip;
+    int spill;                   // the tile list uses the tensor-memory spill rows
 };
 
 size_t fast_smem_bytes(int storage, int nc, int nw);
@@ -97,15 +98,16 @@ namespace kps {
 constexpr int kTmemRegion = 256;
 constexpr int kTmemSpill = 16;
 
-// Does a chunk fit?  `tile(i)` gives the (start, length) of its i-th of n
-// tiles.
+// Does a chunk fit `limit` columns (kTmemRegion, or kTmemRegion +
+// kTmemSpill with the spill rows)?  `tile(i)` gives the (start, length) of
+// its i-th of n tiles.
 template <typename TileAt>
-inline bool tmem_chunk_fits(int n, TileAt tile) {
+inline bool tmem_chunk_fits(int n, TileAt tile, int limit) {
     if (n <= 1) return true;
     const int cs = tile(0).first;
     for (int i = 0; i + 1 < n; ++i) {
         const auto t = tile(i);
-        if (t.first - cs + (t.second + 15) / 16 * 16 > kTmemRegion + kTmemSpill) return false;
+        if (t.first - cs + (t.second + 15) / 16 * 16 > limit) return false;
     }
     return true;
 }
@@ -145,6 +147,7 @@ struct MultiParams {
     int *ticket;
     int ngames;
     int total_tiles;
+    int spill;                      // some game's tiles use the spill rows
     int nw;                         // warps per CTA
     int nc;                         // largest per-card row count of the games
     int schedule;

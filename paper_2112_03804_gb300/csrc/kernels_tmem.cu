@@ -130,7 +130,7 @@ struct Cta {
     uint32_t tmem;    // tensor-memory base address of the CTA
 };
 
-template <typename S, int K2, int KIND>
+template <typename S, int K2, int KIND, bool SP>
 __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem, const Cta &cta,
                                         const float *fco_s, const float *sco_s) {
     constexpr bool HF = (KIND & kKindF) != 0, HS = (KIND & kKindS) != 0;
@@ -335,9 +335,9 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
             // the last tile's to the partial tile, where the finishing pass
             // takes them first
             const int c0 = t0 - cstart + 16 * half;
-            if (t + 1 < te && c0 + 16 <= kRegion) {
+            if (t + 1 < te && (!SP || c0 + 16 <= kRegion)) {
                 tm_st16(treg + (uint32_t)c0, r);
-            } else if (t + 1 < te) {
+            } else if (SP && t + 1 < te) {
                 // a half crossing the end of the tensor-memory region: its
                 // columns past the end go to the spill rows
 #pragma unroll
@@ -438,9 +438,9 @@ __device__ __forceinline__ void tm_body(const FastParams &p, unsigned char *smem
             if (16 * half >= len) break;
             float r[16], za[16], zb[16];
             const int c0 = t0 - cstart + 16 * half;
-            if (i > 0 && c0 + 16 <= kRegion) {
+            if (i > 0 && (!SP || c0 + 16 <= kRegion)) {
                 tm_ld16(treg + (uint32_t)c0, r);
-            } else if (i > 0) {
+            } else if (SP && i > 0) {
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     if (c0 + k < kRegion) tm_ld1(treg + (uint32_t)(c0 + k), r[k]);
@@ -504,7 +504,7 @@ __device__ __forceinline__ uint32_t *tm_slot(unsigned char *smem_raw, int nw) {
 
 // One tile of 32 output columns (col = ctile * 32 + lane) of game p.  Ends
 // with every tensor-memory access of the tile complete.
-template <typename S, int K2>
+template <typename S, int K2, bool SP>
 __device__ __forceinline__ void tm_tile(const FastParams &p, long long ctile, unsigned char *smem_raw,
                                         uint32_t tmem) {
     const int hs = p.hs;
@@ -557,15 +557,15 @@ __device__ __forceinline__ void tm_tile(const FastParams &p, long long ctile, un
     cta.uni = __syncthreads_and(same) != 0;
     cta.nvalid = __syncthreads_count(valid);
     cta.tmem = tmem;
-    if (has_f && has_s) tm_body<S, K2, kKindFS>(p, smem_raw, cta, fco_s, sco_s);
-    else if (has_s) tm_body<S, K2, kKindS>(p, smem_raw, cta, fco_s, sco_s);
-    else tm_body<S, K2, kKindF>(p, smem_raw, cta, fco_s, sco_s);
+    if (has_f && has_s) tm_body<S, K2, kKindFS, SP>(p, smem_raw, cta, fco_s, sco_s);
+    else if (has_s) tm_body<S, K2, kKindS, SP>(p, smem_raw, cta, fco_s, sco_s);
+    else tm_body<S, K2, kKindF, SP>(p, smem_raw, cta, fco_s, sco_s);
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
 }
 
-template <typename S, int K2>
+template <typename S, int K2, bool SP>
 __global__ void __launch_bounds__(32 * kMaxWarps)
 tmem_scan_kernel(const FastParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -577,12 +577,12 @@ tmem_scan_kernel(const FastParams p) {
     __syncthreads();
     tm_fence_after();
     const uint32_t tmem = *tmem_slot;
-    tm_tile<S, K2>(p, blockIdx.x, smem_raw, tmem);
+    tm_tile<S, K2, SP>(p, blockIdx.x, smem_raw, tmem);
     if (threadIdx.x < 32) tm_dealloc(tmem, ncols);
 }
 
 // Persistent launch over the column tiles of several games.
-template <typename S, int K2>
+template <typename S, int K2, bool SP>
 __global__ void __launch_bounds__(32 * kMaxWarps)
 tmem_multi_kernel(const MultiParams m) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -613,15 +613,15 @@ tmem_multi_kernel(const MultiParams m) {
         }
         __syncthreads();
         if (s_game < 0) break;
-        tm_tile<S, K2>(sp, s_tile, smem_raw, tmem);
+        tm_tile<S, K2, SP>(sp, s_tile, smem_raw, tmem);
     }
     if (threadIdx.x < 32) tm_dealloc(tmem, ncols);
 }
 
-template <typename S, int K2>
+template <typename S, int K2, bool SP = false>
 cudaError_t launch_t(const FastParams &p, size_t smem, cudaStream_t stream) {
     static size_t configured = 0;
-    auto fn = tmem_scan_kernel<S, K2>;
+    auto fn = tmem_scan_kernel<S, K2, SP>;
     if (configured < smem) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -635,10 +635,10 @@ cudaError_t launch_t(const FastParams &p, size_t smem, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
-template <typename S, int K2>
+template <typename S, int K2, bool SP = false>
 cudaError_t launch_multi_t(const MultiParams &m, size_t smem, int grid, cudaStream_t stream) {
     static size_t configured = 0;
-    auto fn = tmem_multi_kernel<S, K2>;
+    auto fn = tmem_multi_kernel<S, K2, SP>;
     if (configured < smem) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -649,14 +649,14 @@ cudaError_t launch_multi_t(const MultiParams &m, size_t smem, int grid, cudaStre
     return cudaGetLastError();
 }
 
-template <typename S, int K2>
+template <typename S, int K2, bool SP = false>
 int ctas_t(size_t smem, int nw) {
     // Resident CTAs per SM from the SM's limits: shared memory (1 KB
     // reserved per CTA), registers (allocated per warp in units of 256) and
     // thread slots.  The runtime's occupancy query reports one CTA per SM for
     // this kernel at every size, while two 4-warp CTAs do run side by side
     // (measured), so it is not used.
-    auto fn = tmem_multi_kernel<S, K2>;
+    auto fn = tmem_multi_kernel<S, K2, SP>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 0;
@@ -682,10 +682,16 @@ cudaError_t launch_tmem_scan(const FastParams &p, int storage, int k, cudaStream
     if (p.nc > 66 || p.nw < 1 || p.nw > kMaxWarps) return cudaErrorInvalidValue;
     const size_t smem = tmem_smem_bytes(p.nc, p.nw);
     switch (storage) {
-        case kStoreF32: return k == 1 ? launch_t<float, 1>(p, smem, stream) : launch_t<float, 2>(p, smem, stream);
+        case kStoreF32:
+            return k == 1 ? launch_t<float, 1>(p, smem, stream)
+                          : p.spill ? launch_t<float, 2, true>(p, smem, stream) : launch_t<float, 2>(p, smem, stream);
         case kStoreBF16:
-            return k == 1 ? launch_t<__nv_bfloat16, 1>(p, smem, stream) : launch_t<__nv_bfloat16, 2>(p, smem, stream);
-        case kStoreF16: return k == 1 ? launch_t<__half, 1>(p, smem, stream) : launch_t<__half, 2>(p, smem, stream);
+            return k == 1 ? launch_t<__nv_bfloat16, 1>(p, smem, stream)
+                          : p.spill ? launch_t<__nv_bfloat16, 2, true>(p, smem, stream)
+                                    : launch_t<__nv_bfloat16, 2>(p, smem, stream);
+        case kStoreF16:
+            return k == 1 ? launch_t<__half, 1>(p, smem, stream)
+                          : p.spill ? launch_t<__half, 2, true>(p, smem, stream) : launch_t<__half, 2>(p, smem, stream);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -695,12 +701,17 @@ cudaError_t launch_tmem_multi(const MultiParams &m, int storage, int k, int grid
     const size_t smem = tmem_smem_bytes(m.nc, m.nw);
     switch (storage) {
         case kStoreF32:
-            return k == 1 ? launch_multi_t<float, 1>(m, smem, grid, stream) : launch_multi_t<float, 2>(m, smem, grid, stream);
+            return k == 1 ? launch_multi_t<float, 1>(m, smem, grid, stream)
+                          : m.spill ? launch_multi_t<float, 2, true>(m, smem, grid, stream)
+                                    : launch_multi_t<float, 2>(m, smem, grid, stream);
         case kStoreBF16:
-            return k == 1 ? launch_multi_t<__nv_bfloat16, 1>(m, smem, grid, stream)
-                          : launch_multi_t<__nv_bfloat16, 2>(m, smem, grid, stream);
+            return k == 1   ? launch_multi_t<__nv_bfloat16, 1>(m, smem, grid, stream)
+                   : m.spill ? launch_multi_t<__nv_bfloat16, 2, true>(m, smem, grid, stream)
+                             : launch_multi_t<__nv_bfloat16, 2>(m, smem, grid, stream);
         case kStoreF16:
-            return k == 1 ? launch_multi_t<__half, 1>(m, smem, grid, stream) : launch_multi_t<__half, 2>(m, smem, grid, stream);
+            return k == 1   ? launch_multi_t<__half, 1>(m, smem, grid, stream)
+                   : m.spill ? launch_multi_t<__half, 2, true>(m, smem, grid, stream)
+                             : launch_multi_t<__half, 2>(m, smem, grid, stream);
         default: return cudaErrorInvalidValue;
     }
 }

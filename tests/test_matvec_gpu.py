@@ -264,3 +264,24 @@ def test_unaligned_vectors(river):
     torch.cuda.synchronize()
     o = obuf[1:].reshape(B, inf["n1"], inf["hs"]).double().cpu().numpy()
     assert normwise_error(from_library(o, order, inf["H"]), og.matvec_A(y)) <= 1e-5
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_flop_size_game_uses_spill_rows(transpose):
+    """A 1176-hand game (3-card board): its four chunks of ~294 hands need the
+    tiles cut from the chunk ends and the spill rows past the tensor-memory
+    region; FP32 products within the FP32 bound of the oracle."""
+    spec = synth.river_spec(seed=9, nboard=3)
+    og, g = OracleGame(spec), kps.Game(spec)
+    inf = g.info()
+    assert inf["H"] == 1176
+    order = library_order(spec["strength"])
+    v = _inputs(og, 3, seed=67, transpose=transpose)
+    n_out = inf["n2"] if transpose else inf["n1"]
+    vin = torch.from_numpy(to_library(v, order, inf["hs"])).to("cuda", torch.float32).contiguous()
+    out = torch.full((3, n_out, inf["hs"]), float("nan"), device="cuda")
+    (kps.matvec_AT if transpose else kps.matvec_A)(g, vin, out, 3)
+    torch.cuda.synchronize()
+    got = from_library(out.double().cpu().numpy(), order, inf["H"])
+    want = og.matvec_AT(v) if transpose else og.matvec_A(v)
+    assert normwise_error(got, want) <= 1e-5
