@@ -73,11 +73,18 @@ KERNEL_SOURCES = ("kernels.h", "kernels_tmem.cu")
 
 
 def _kernel_hash():
-    """Hash of the benchmarked kernel's sources (changes whenever it does)."""
+    """Hash of the benchmarked kernel's code (its sources without comments
+    and blank lines: changes whenever the code does, not when a comment
+    does)."""
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
+        src = open(os.path.join(CSRC, f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        code = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
         h.update(f.encode())
-        h.update(open(os.path.join(CSRC, f), "rb").read())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

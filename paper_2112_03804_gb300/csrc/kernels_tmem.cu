@@ -14,14 +14,20 @@
 //     (lane = hand) and transposed through shared memory, while the previous
 //     tile is scanned (lane = column; per-card state [card][lane] in shared
 //     memory, conflict free, two hands per step when they share no card);
-//   * the partial result of every (hand, column) goes to tensor memory: the
-//     warp's 32 lanes are the 32 columns, a tensor-memory column is a hand,
-//     so a tile leaves in one tcgen05.st and comes back in one tcgen05.ld.
-//     Shared memory keeps only per-warp state (about 25 KB), the partial
-//     results never travel to global memory;
+//   * the partial result of every (hand, column) stays on chip: the chunk's
+//     last tile in the warp's partial tile in shared memory, the other
+//     tiles in tensor memory (the warp's 32 lanes are the 32 columns, a
+//     tensor-memory column is a hand, so a half tile leaves in one
+//     tcgen05.st and comes back in one tcgen05.ld), and, for chunks longer
+//     than the warp's 256 columns allow (the SP instantiation), the columns
+//     past the region in spill rows of the partial tile.  Shared memory
+//     keeps only per-warp state (about 27 KB); the partial results never
+//     travel to global memory.  With 4 warps a CTA takes 256 tensor-memory
+//     columns and ~110 KB of shared memory, so two CTAs share an SM and one
+//     CTA's scan overlaps the other's combination and finishing pass;
 //   * after the chunks' per-card sums are combined (fold totals and the mass
-//     of earlier chunks), each warp finishes its hands and writes the output
-//     with coalesced stores (lane = hand).
+//     of earlier chunks), each warp finishes its hands, the last tile first,
+//     and writes the output with coalesced stores (lane = hand).
 // Scans are specialised by column kind: fold only, showdown only, or both.
 // No atomics: results are bit-reproducible.
 #include "kernels.h"
