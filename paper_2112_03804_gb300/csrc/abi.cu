@@ -459,9 +459,17 @@ kps_status matvec_host(kps_game *g, int dir, const void *vin, void *vout, int32_
         g->host_streams = true;
     }
     cudaStream_t s_in = g->hstream[0], s_mv = g->hstream[1], s_out = g->hstream[2];
+    // on an error after work was queued, wait for it before returning: the
+    // copies read and write the caller's host buffers
+    auto drain = [&]() {
+        for (cudaStream_t q : {s_in, s_mv, s_out}) cudaStreamSynchronize(q);
+    };
     if ((e = cudaEventRecord(g->hentry, stream)) != cudaSuccess) return cuda_fail(e, "ordering the copies");
     for (cudaStream_t q : {s_in, s_mv, s_out})
-        if ((e = cudaStreamWaitEvent(q, g->hentry, 0)) != cudaSuccess) return cuda_fail(e, "ordering the copies");
+        if ((e = cudaStreamWaitEvent(q, g->hentry, 0)) != cudaSuccess) {
+            drain();
+            return cuda_fail(e, "ordering the copies");
+        }
     const int nch = std::min(kps_game::kHostChunks, (int)batch);
     const size_t vin_bytes = in_bytes / batch, vout_bytes = out_bytes / batch;
     for (int c = 0; c < nch; ++c) {
@@ -472,12 +480,13 @@ kps_status matvec_host(kps_game *g, int dir, const void *vin, void *vout, int32_
                             cudaMemcpyHostToDevice, s_in);
         if (e == cudaSuccess) e = cudaEventRecord(g->hin[c], s_in);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s_mv, g->hin[c], 0);
-        if (e != cudaSuccess) return cuda_fail(e, "copying input to the device");
+        if (e != cudaSuccess) {
+            drain();
+            return cuda_fail(e, "copying input to the device");
+        }
         kps_status st = matvec(g, dir, din, dout, (int32_t)(b1 - b0), dt, s_mv);
         if (st != KPS_OK) {
-            cudaStreamSynchronize(s_in);
-            cudaStreamSynchronize(s_mv);
-            cudaStreamSynchronize(s_out);
+            drain();
             return st;
         }
         e = cudaEventRecord(g->hdone[c], s_mv);
@@ -485,10 +494,16 @@ kps_status matvec_host(kps_game *g, int dir, const void *vin, void *vout, int32_
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(static_cast<char *>(vout) + b0 * vout_bytes, dout, (b1 - b0) * vout_bytes,
                                 cudaMemcpyDeviceToHost, s_out);
-        if (e != cudaSuccess) return cuda_fail(e, "copying output to the host");
+        if (e != cudaSuccess) {
+            drain();
+            return cuda_fail(e, "copying output to the host");
+        }
     }
     for (cudaStream_t q : {s_in, s_mv, s_out})
-        if ((e = cudaStreamSynchronize(q)) != cudaSuccess) return cuda_fail(e, "synchronising");
+        if ((e = cudaStreamSynchronize(q)) != cudaSuccess) {
+            drain();
+            return cuda_fail(e, "synchronising");
+        }
     return KPS_OK;
 }
 
