@@ -18,6 +18,7 @@
 #include <climits>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -332,15 +333,13 @@ kps_status kps_tb_create(const kps_game *game, kps_tb **out) {
     if (!game || !out) return fail(KPS_EINVAL, "NULL argument");
     *out = nullptr;
     try {
-        kps_tb *tb = new kps_tb();
+        std::unique_ptr<kps_tb> owner(new kps_tb());
+        kps_tb *tb = owner.get();
         tb->game = game;
         kps::technique_b_factors(game->host, tb->f);
         const kps::HostGame &g = game->host;
         for (int w = 0; w < kFactors; ++w)
-            if (factor(tb, w).col.size() > (size_t)INT_MAX) {
-                delete tb;
-                return fail(KPS_ENOTSUP, "factor with more than 2^31 nonzeros");
-            }
+            if (factor(tb, w).col.size() > (size_t)INT_MAX) return fail(KPS_ENOTSUP, "factor with more than 2^31 nonzeros");
         const int64_t pad = (int64_t)g.n[0] * (g.hs - g.H);    // M's diagonal on padding rows
         tb->sizes[0] = tb->f.ahat.rows;
         tb->sizes[1] = tb->f.ahat.cols;
@@ -349,7 +348,7 @@ kps_status kps_tb_create(const kps_game *game, kps_tb **out) {
         tb->sizes[4] = (int64_t)tb->f.u.col.size();
         tb->sizes[5] = (int64_t)tb->f.m.col.size() - pad;
         tb->sizes[6] = (int64_t)tb->f.vt.col.size();
-        *out = tb;
+        *out = owner.release();
         return KPS_OK;
     } catch (const std::bad_alloc &) {
         return fail(KPS_ENOMEM, "Technique B factors");
