@@ -338,10 +338,12 @@ def measure_batch(ngames: int, steps: int, warmup: int, rank: int = 0):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    # A*y reads n2 rows and writes n1 rows of H values per game, A^T*x reads
+    # n1 and writes n2: 2 * 4 * H * (n1 + n2) bytes per game and step
     alg = 0.0
     for g in games:
         inf = g.info()
-        alg += 4.0 * inf["H"] * (inf["n1"] + inf["n2"])
+        alg += 8.0 * inf["H"] * (inf["n1"] + inf["n2"])
     return {"workload": BATCH_WORKLOAD, "games": ngames, "matvecs_per_s": 2 * ngames / (ms / 1e3),
             "ms_per_step": ms, "alg_bytes_per_step": alg, "achieved_gbs": alg / (ms / 1e3) / 1e9,
             "launch_shape": {k: shape[k] for k in ("warps", "grid", "schedule")},

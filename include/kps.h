@@ -251,7 +251,10 @@ kps_status kps_partition(const int64_t *weights, int32_t n, int32_t parts, int32
  * is the per-iteration cost that the sparsification of Prop. 1 makes cheap;
  * Sec. 5 runs such a solver).  One iteration t:
  *   xsum += t x;  R1 <- max(0, R1 + q - v) bottom-up against g = A y;
- *   x <- sequence form of R1 / sum R1 (uniform where the sum is 0);
+ *   x <- sequence form of R1 / sum R1 (uniform where the sum is at most
+ *        a noise floor theta_p = eps * V_p, V_p a bound on player p's
+ *        counterfactual values: eps = 2^-40 for KPS_F64 storage, 2^-16
+ *        otherwise);
  *   ysum += t y;  the same for player 2 against g = -A^T x (the new x).
  * `dt` is the storage type of strategies and values (KPS_F32, KPS_F64,
  * KPS_BF16, KPS_F16); regrets, averages and arithmetic are FP32 (FP64 for
@@ -393,7 +396,9 @@ kps_status kps_mlp_adam(kps_mlp *mlp, float lr, float beta1, float beta2, float 
  *   - batch * n1 * hs must not exceed KPS_STATIC_SCRATCH_FLOATS; larger
  *     requests fail with KPS_EINVAL and a message giving both numbers.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress).
+ *   - The call cannot be recorded into a CUDA graph: on a stream that is
+ *     capturing it returns KPS_EINVAL and queues nothing.
  *   - All calls share the array: calls that overlap on the GPU (other
  *     streams, other threads) race and produce wrong results.  Every element
  *     the kernel reads is written by the same call first, so nothing needs to

@@ -689,13 +689,22 @@ kps_status kps_matvec_A_static_scratch(kps_game *g, const void *y, void *out, in
     const int nw = fast_warps(storage, nc, h.H, false);
     if (kps::fast_smem_bytes(storage, nc, nw) > (size_t)kps::max_dyn_smem())
         return fail(KPS_ENOTSUP, "card count too large for shared memory");
+    // the tile list kps_matvec_A's scalar-staging path uses for nw warps
+    // (same chunk boundaries, hence the same summation order)
     std::vector<int> tchunk;
-    std::vector<std::pair<int, int>> tl = kps::tie_tiles(h, nw, kps::kTile, tchunk);
+    bool spill = false;
+    std::vector<std::pair<int, int>> tl = layout_tiles(h, nw, tchunk, &spill);
     if (tl.size() * sizeof(int2) > kps::kStaticTileBytes) return fail(KPS_ENOTSUP, "tile list too long");
-    void *base = nullptr;
-    cudaError_t e = kps::static_scratch_address(&base);
-    if (e != cudaSuccess) return cuda_fail(e, "looking up the static scratch");
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    // the tile list is copied from a host vector that dies with this call,
+    // so the call cannot be recorded into a graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "querying the stream's capture status");
+    if (cap != cudaStreamCaptureStatusNone) return fail(KPS_EINVAL, "the stream is capturing a graph: this call cannot be captured");
+    void *base = nullptr;
+    e = kps::static_scratch_address(&base);
+    if (e != cudaSuccess) return cuda_fail(e, "looking up the static scratch");
     std::vector<int2> tiles(tl.size());
     for (size_t i = 0; i < tl.size(); ++i) tiles[i] = make_int2(tl[i].first, tl[i].second);
     if (!tiles.empty()) {

@@ -31,6 +31,9 @@
 // shared memory.  No atomics: results are bit-reproducible.
 #include "kernels.h"
 
+#include <map>
+#include <mutex>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -416,15 +419,9 @@ pair_scan_kernel(const ScanParams p) {
 
 template <typename S, int K2, bool PIN>
 cudaError_t launch_t(const ScanParams &p, size_t smem, cudaStream_t stream) {
-    static bool configured = false;
-    static size_t configured_bytes = 0;
     auto fn = pair_scan_kernel<S, K2, PIN>;
-    if (!configured || configured_bytes < smem) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-        configured_bytes = smem;
-    }
+    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem);
+    if (e != cudaSuccess) return e;
     const long long ncols = (long long)p.n_out * p.batch;
     const long long blocks = (ncols + kColsPerCta - 1) / kColsPerCta;
     if (blocks <= 0) return cudaSuccess;
@@ -441,6 +438,23 @@ size_t scan_smem_bytes(int storage, int H, int nc, int nw, bool pin) {
     bytes += (size_t)nw * (3 * (size_t)nc * 32 + 2 * 32 * kPad) * cs;
     if (pin) bytes += (size_t)H * kPad * cs;
     return bytes;
+}
+
+cudaError_t ensure_dyn_smem(const void *fn, size_t smem) {
+    // the limit is a per-device property of the kernel: remember, per
+    // (kernel, device), the largest size already set
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &have = done[std::make_pair(fn, dev)];
+    if (have >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    have = smem;
+    return cudaSuccess;
 }
 
 int max_dyn_smem() {

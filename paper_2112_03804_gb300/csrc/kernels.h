@@ -37,6 +37,10 @@ size_t scan_smem_bytes(int storage, int H, int nc, int nw, bool partial_in_smem)
 // Largest dynamic shared memory per block on the current device.
 int max_dyn_smem();
 
+// Raises kernel `fn`'s dynamic shared-memory limit to at least `smem` bytes
+// on the current device (set once per kernel, device and size; thread safe).
+cudaError_t ensure_dyn_smem(const void *fn, size_t smem);
+
 cudaError_t launch_pair_scan(const ScanParams &p, int storage, int cards_per_hand,
                              bool partial_in_smem, cudaStream_t stream);
 

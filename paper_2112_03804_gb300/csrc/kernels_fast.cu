@@ -354,12 +354,10 @@ fast_scan_kernel(const FastParams p) {
 
 template <typename S, int K2>
 cudaError_t launch_t(const FastParams &p, size_t smem, cudaStream_t stream) {
-    static size_t configured = 0;
     auto fn = fast_scan_kernel<S, K2>;
-    if (configured < smem) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
     }
     const long long ncols = (long long)p.n_out * p.batch;
     const long long blocks = (ncols + 31) / 32;

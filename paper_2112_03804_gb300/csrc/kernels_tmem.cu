@@ -626,12 +626,10 @@ tmem_multi_kernel(const MultiParams m) {
 
 template <typename S, int K2, bool SP = false>
 cudaError_t launch_t(const FastParams &p, size_t smem, cudaStream_t stream) {
-    static size_t configured = 0;
     auto fn = tmem_scan_kernel<S, K2, SP>;
-    if (configured < smem) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
     }
     const long long ncols = (long long)p.n_out * p.batch;
     const long long blocks = (ncols + 31) / 32;
@@ -643,12 +641,10 @@ cudaError_t launch_t(const FastParams &p, size_t smem, cudaStream_t stream) {
 
 template <typename S, int K2, bool SP = false>
 cudaError_t launch_multi_t(const MultiParams &m, size_t smem, int grid, cudaStream_t stream) {
-    static size_t configured = 0;
     auto fn = tmem_multi_kernel<S, K2, SP>;
-    if (configured < smem) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
     }
     if (m.total_tiles <= 0) return cudaSuccess;
     fn<<<grid, 32 * m.nw, smem, stream>>>(m);

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "abi_internal.h"
+#include "kernels.h"
 #include "batch_internal.h"
 #include "mlp_internal.h"
 
@@ -573,12 +574,7 @@ kps_status kps_warm_predict(kps_batch *b, kps_mlp *m, float *beh1, float *beh2, 
         e = mlp_gemm_xw(nn, kWidth, kOffHand - kOffNode, t->d.node_feat, kOffHand - kOffNode,
                         W1 + (size_t)kOffNode * kWidth, kWidth, N1, kWidth, s);
     if (e == cudaSuccess) {
-        static bool configured = false;
-        if (!configured) {
-            e = cudaFuncSetAttribute(predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)predict_smem_bytes());
-            configured = e == cudaSuccess;
-        }
+        e = kps::ensure_dyn_smem(reinterpret_cast<const void *>(predict_kernel), predict_smem_bytes());
     }
     if (e == cudaSuccess) {
         PredictArgs a;

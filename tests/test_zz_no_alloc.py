@@ -115,3 +115,26 @@ def test_oversize_and_bad_arguments_rejected(river):
     with pytest.raises(kps.KpsError) as e:
         kps.matvec_A_static_scratch(fresh, y, out, 1)
     assert e.value.status == kps.EINVAL
+
+
+def test_refused_while_capturing(river):
+    """The tile list is copied from host memory that lives only for the
+    call, so a captured call would replay a dangling copy: the call refuses
+    a capturing stream and queues nothing."""
+    spec, g, order = river
+    inf = g.info()
+    y = _vectors(g, order, 2, seed=3, dt=kps.BF16)
+    out = torch.zeros((2, inf["n1"], inf["hs"]), device="cuda", dtype=torch.bfloat16)
+    kps.matvec_A_static_scratch(g, y, out, 2)     # device set-up outside the capture
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    status = None
+    with torch.cuda.graph(graph, stream=side):
+        try:
+            kps.matvec_A_static_scratch(g, y, out, 2, stream=side)
+        except kps.KpsError as e:
+            status = e.status
+    assert status == kps.EINVAL
+    graph.replay()      # an empty graph
+    torch.cuda.synchronize()
