@@ -173,6 +173,20 @@ kps_status kps_game_terminals(const kps_game *game, int32_t *s1, int32_t *s2,
  * Call it before capturing GPU calls into a CUDA graph. */
 kps_status kps_game_upload(kps_game *game, void *stream);
 
+/* Which kernel ran the last product of a direction (dir 0 = A * y,
+ * 1 = A^T * x) on this game: one of the KPS_KERNEL_* codes, 0 before the
+ * first product.  The library picks the kernel from the dtype, the
+ * vectors' alignment and the game's shape (tie groups, hand and card
+ * counts); the environment variable KPS_KERNEL = tma | tmem | vec | fast
+ * forces one where it applies.  Diagnostics only: results agree within the
+ * stated tolerances whichever kernel runs. */
+#define KPS_KERNEL_TMA 1      /* TMA-staged boxes, tensor-memory partials (FP32) */
+#define KPS_KERNEL_TMEM 2     /* register staging, tensor-memory partials */
+#define KPS_KERNEL_VEC 3      /* 16-byte asynchronous copies, partials through L2 */
+#define KPS_KERNEL_SCALAR 4   /* scalar staging, partials through L2 */
+#define KPS_KERNEL_GENERAL 5  /* tie groups longer than a tile */
+kps_status kps_game_kernel(const kps_game *game, int32_t dir, int32_t *kernel);
+
 /* out_b = A * y_b for b < batch (Prop. 1; the gradient of Sec. 2, "First-
  * order methods").  y: device [batch][n2][hs], out: device [batch][n1][hs],
  * both of type dt, non-overlapping.  batch >= 0 (0 is a no-op).

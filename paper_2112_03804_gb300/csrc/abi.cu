@@ -338,10 +338,41 @@ kps_status matvec_fast(kps_game *g, int dir, const kps::ScanParams &sp, int stor
     (void)dir;
     (void)dt;
     cudaError_t e;
+    g->last_kernel[dir] = path == kTmem ? KPS_KERNEL_TMEM : vec ? KPS_KERNEL_VEC : KPS_KERNEL_SCALAR;
     if (path == kTmem) e = kps::launch_tmem_scan(p, storage, h.k, stream);
     else if (vec) e = kps::launch_vec_scan(p, storage, h.k, stream);
     else e = kps::launch_fast_scan(p, storage, h.k, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launching the payoff scan");
+    return KPS_OK;
+}
+
+// The TMA-staged FP32 path (kernels_tma.cu) when the game and the vectors
+// allow it; *taken tells whether it ran.  KPS_KERNEL=tma|tmem|vec|fast
+// forces a path where it applies (any value other than tma disables this
+// one).
+kps_status matvec_tma(kps_game *g, int dir, const void *vin, void *vout, int32_t batch, cudaStream_t stream,
+                      bool *taken) {
+    *taken = false;
+    const char *force = std::getenv("KPS_KERNEL");
+    if (force && std::strcmp(force, "tma") != 0) return KPS_OK;
+    if (((reinterpret_cast<uintptr_t>(vin) | reinterpret_cast<uintptr_t>(vout)) & 15) != 0) return KPS_OK;
+    if (g->tma_state[dir] == 0) {
+        const kps::HostGame &h = g->host;
+        const double *lin = dir == 0 ? h.lam2.data() : h.lam1.data();
+        const double *lout = dir == 0 ? h.lam1.data() : h.lam2.data();
+        std::string why;
+        kps::TmaParams *p = kps::tma_create(h, lin, lout, dir == 0 ? h.n[0] : h.n[1], dir == 0 ? h.n[1] : h.n[0],
+                                            g->dev.fcol[dir], g->dev.scol[dir], g->dev.fcoef_f[dir],
+                                            g->dev.scoef_f[dir], g->fcol[dir].data(), g->scol[dir].data(), &why);
+        g->tma[dir].reset(p);
+        g->tma_state[dir] = p ? 1 : -1;
+    }
+    if (g->tma_state[dir] != 1) return KPS_OK;
+    *taken = true;
+    g->last_kernel[dir] = KPS_KERNEL_TMA;
+    cudaError_t e = kps::launch_tma_scan(g->tma[dir].get(), static_cast<const float *>(vin),
+                                         static_cast<float *>(vout), batch, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the TMA-staged payoff scan");
     return KPS_OK;
 }
 
@@ -387,6 +418,11 @@ kps_status matvec(kps_game *g, int dir, const void *vin, void *vout, int32_t bat
     p.lam_out = dir == 0 ? l1 : l2;
     const int storage = dt == KPS_F32 ? kps::kStoreF32 : dt == KPS_F64 ? kps::kStoreF64
                         : dt == KPS_BF16 ? kps::kStoreBF16 : kps::kStoreF16;
+    if (storage == kps::kStoreF32) {
+        bool taken = false;
+        kps_status s2 = matvec_tma(g, dir, vin, vout, batch, stream, &taken);
+        if (taken || s2 != KPS_OK) return s2;
+    }
     if (h.max_tie <= kps::kTile) return matvec_fast(g, dir, p, storage, dt, stream);
     // general path: as many hand chunks (warps) as shared memory allows
     const int smem_max = kps::max_dyn_smem();
@@ -406,6 +442,7 @@ kps_status matvec(kps_game *g, int dir, const void *vin, void *vout, int32_t bat
     p.nw = nw;
     std::vector<int> cb = kps::chunk_bounds(h, nw);
     for (int i = 0; i <= nw; ++i) p.chunk[i] = cb[i];
+    g->last_kernel[dir] = KPS_KERNEL_GENERAL;
     cudaError_t e = kps::launch_pair_scan(p, storage, h.k, pin, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launching the payoff scan");
     return KPS_OK;
@@ -638,6 +675,13 @@ kps_status kps_game_terminals(const kps_game *g, int32_t *s1, int32_t *s2, int32
 kps_status kps_game_upload(kps_game *g, void *stream) {
     if (!g) return fail(KPS_EINVAL, "game is NULL");
     return upload(g, static_cast<cudaStream_t>(stream));
+}
+
+kps_status kps_game_kernel(const kps_game *g, int32_t dir, int32_t *kernel) {
+    if (!g || !kernel) return fail(KPS_EINVAL, "NULL argument");
+    if (dir != 0 && dir != 1) return fail(KPS_EINVAL, "dir must be 0 (A) or 1 (A^T)");
+    *kernel = g->last_kernel[dir];
+    return KPS_OK;
 }
 
 kps_status kps_matvec_A(kps_game *g, const void *y, void *out, int32_t batch, kps_dtype dt, void *stream) {

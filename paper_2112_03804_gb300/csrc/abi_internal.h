@@ -11,6 +11,9 @@
 
 #include "../../include/kps.h"
 #include "game.h"
+#include "kernels.h"
+
+#include <memory>
 
 namespace kps_abi {
 
@@ -65,6 +68,15 @@ struct kps_game {
     // FP32 partial results for half-precision outputs
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    // parameter blocks of the TMA-staged FP32 path per direction, built on
+    // first use (state 1), or -1 when the game cannot take that path
+    struct TmaDel {
+        void operator()(kps::TmaParams *p) const { kps::tma_destroy(p); }
+    };
+    std::unique_ptr<kps::TmaParams, TmaDel> tma[2];
+    int tma_state[2] = {0, 0};
+    // kernel of the last product per direction (KPS_KERNEL_* of kps.h)
+    int last_kernel[2] = {0, 0};
 };
 
 namespace kps_abi {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <string>
 #include <utility>
 
 namespace kps {
@@ -162,5 +163,29 @@ cudaError_t launch_vec_multi(const MultiParams &m, int storage, int cards_per_ha
 // Resident CTAs per SM of the multi-game kernels for the given shape.
 int tmem_multi_ctas_per_sm(int storage, int cards_per_hand, int nc, int nw);
 int vec_multi_ctas_per_sm(int storage, int cards_per_hand, int nc, int nw);
+
+}  // namespace kps
+
+namespace kps {
+
+// TMA-staged single-game path (FP32 storage, kernels_tma.cu).  A CTA owns
+// one output sequence and 32 consecutive vectors of the batch (one per
+// lane); its warps scan chunks of the hand order, each a run of 16-hand
+// boxes that the tensor memory accelerator copies into shared memory.  The
+// parameter block is opaque here: built once per game and direction.
+struct TmaParams;
+struct HostGame;
+
+// Builds the parameter block for one direction (lam_in / lam_out: library
+// order; fcol, scol, fcoef, scoef: the device tables of that direction;
+// hfcol / hscol: their host copies).  Returns nullptr with *why set when
+// the game cannot take this path.
+TmaParams *tma_create(const HostGame &h, const double *lam_in, const double *lam_out, int n_out, int n_in,
+                      const int *fcol, const int *scol, const float *fcoef, const float *scoef,
+                      const int *hfcol, const int *hscol, std::string *why);
+void tma_destroy(TmaParams *p);
+// One product: out (device, [batch][n_out][hs]) from vin ([batch][n_in][hs]),
+// both 16-byte aligned.
+cudaError_t launch_tma_scan(TmaParams *p, const float *vin, float *vout, int batch, cudaStream_t stream);
 
 }  // namespace kps

@@ -1,0 +1,736 @@
+// Kronecker-form payoff products, TMA-staged (sm_103a): single game, FP32.
+//
+// Mathematics (Prop. 1, Sec. 3; the fold block is the card-removal
+// compatibility of Sec. 4's eq. for C, the showdown block the strength sign
+// times compatibility, whose inverse-D prefix sums are Technique B's):
+//   out / lambda_out = K_F(w) + S (2 Lo(b) + TieC(b)),
+//   a = lambda_in * y_f,  b = lambda_in * y_s,  w = F a - S b,
+// with y_f / y_s the input rows of the output sequence's fold and showdown
+// terminals (payoffs F and S), K_F(w)[h] = Tot - P[c1] - P[c2] + w[h]
+// (P[c] the per-card totals; one-card hands: Tot - P[c1]), Lo the
+// compatible strictly weaker mass and TieC the compatible tied mass.
+//
+// Ties without tie-aligned tiles.  The scan walks hands in library order
+// (strength, then canonical index) and accumulates the compatible mass of
+// every hand *before* the current one, Lo_ord.  With TB / TA the compatible
+// tied mass before / after a hand in that order, Lo = Lo_ord - TB and
+// TieC = TB + TA, so
+//   2 Lo + TieC = 2 Lo_ord - TB + TA.
+// Every tie group has at most 4 hands (the host checks it): a hand's tied
+// partners are at most 3 positions away, and the two corrections are made in
+// registers (the current 16-hand box and the previous one are held there).
+//
+// Organisation.  A CTA = one output sequence sigma and 32 consecutive
+// vectors (lane j = vector b0 + j): all its columns share their input rows,
+// payoffs and column kind (fold only, showdown only, both).  Four warps scan
+// four chunks of the hand order (chunk boundaries at 16-hand boxes that cut
+// no tie group).  For each box one lane issues cp.async.bulk.tensor copies
+// of the box's [32 vectors][16 hands] from each input row into a 64-byte
+// swizzled slot of the warp's ring (an mbarrier per slot); lanes read their
+// row four hands at a time (conflict free under the swizzle).  Per-card sums
+// live in shared memory [card][lane] (float2: mass of b for Lo, total of w
+// for K_F), addressed by per-hand byte offsets from the parameter block.
+// Two hands per step: all four per-card loads are issued together; when the
+// second hand holds a card of the first, its loaded sums get the first
+// hand's update in registers.  Partial results stay on chip: the first 16
+// boxes of a chunk in tensor memory (lane = column, a column per hand, one
+// tcgen05.st per box), later boxes in shared memory.  After a barrier the
+// four chunks' per-card sums are combined in place into
+// Q[c] = Pall[c] + 2 S R_before[c], and each warp finishes its boxes:
+// out = lambda_out (partial + C - Q[c1] - Q[c2]) with
+// C = Tot + 2 S G_before, written into a swizzled box and stored with one
+// cp.async.bulk.tensor per box.  No atomics: results are bit-reproducible.
+//
+// Waits are bounded: a wait that gives up sets *err, the CTA runs to its end
+// without waiting again, waits (bounded) for its copies still in flight and
+// frees its tensor memory.
+#include "kernels.h"
+#include "game.h"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace kps {
+
+constexpr int kTmaBox = 16;        // hands per box
+constexpr int kTmaWarps = 4;       // chunks per CTA
+constexpr int kTmaMaxHands = 1344; // records in the parameter block (hs <= this)
+constexpr int kTmaMaxExtra = 2;    // boxes of a chunk past the 256 tensor-memory columns
+
+// Per-hand record (library order, padding hands included): byte offsets of
+// the hand's card rows in a warp's per-card table (card * 256; one-card
+// hands: ob unused) and the two lambda weights.
+struct alignas(16) TmaHand {
+    uint32_t oa, ob;
+    float lam_in, lam_out;
+};
+
+// Per-pair flags (hands 2i and 2i+1 of the library order):
+//   bit 0 / 1   the first / second card of hand 2i+1 is a card of hand 2i
+//   bits 2-4    hand 2i has a compatible tied hand 1, 2, 3 positions before it
+//   bits 5-7    the same for hand 2i+1
+struct alignas(128) TmaParams {
+    CUtensorMap tin;               // input  [batch][n_in][H]  fp32, box 16 x 1 x 32, 64-byte swizzle
+    CUtensorMap tout;              // output [batch][n_out][hs] fp32, same box
+    int H, hs, nc, k, n_out, n_in, batch, nbb, nbox, extra;
+    int bchunk[kTmaWarps + 1];     // warp k scans boxes [bchunk[k], bchunk[k+1])
+    const int *fcol, *scol;        // per output sequence: its fold / showdown input sequence or -1
+    const float *fcoef, *scoef;    // and the payoffs
+    unsigned int *err;             // set to 1 when a wait gives up
+    uint32_t pflag[kTmaMaxHands / 2];
+    TmaHand rec[kTmaMaxHands];
+};
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRingBytes = 12288;          // per warp: 3 slots of 4 KB or 6 of 2 KB
+constexpr int kTmemCols = 256;             // per CTA (two CTAs per SM)
+constexpr int kHdrBytes = 2048;            // tensor-memory slot, barriers, per-warp sums
+constexpr int kBarOff = 64;                // 4 warps x 8 mbarriers
+constexpr int kSumOff = 512;               // [2][4][32] floats: G_k, Tot_k
+constexpr unsigned long long kWaitNs = 2000000000ull;   // give up after 2 s
+
+enum Kind { kKindF = 1, kKindS = 2, kKindFS = 3 };
+
+__host__ __device__ inline size_t ring_off(int w) { return kHdrBytes + (size_t)w * kRingBytes; }
+__host__ __device__ inline size_t state_off(int w, int nc) {
+    return kHdrBytes + (size_t)kTmaWarps * kRingBytes + (size_t)w * nc * 256;
+}
+__host__ __device__ inline size_t extra_off(int w, int nc, int extra) {
+    return state_off(kTmaWarps, nc) + (size_t)w * extra * kTmaBox * 32 * 4;
+}
+
+// ---- PTX wrappers ------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for phase `parity` of a barrier; false when it gave up.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = gtime();
+    for (int i = 0; i < (1 << 26); ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 63) == 63 && gtime() - t0 > kWaitNs) break;
+    }
+    return false;
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_store3(const CUtensorMap *map, int x, int y, int z, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void tm_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tm_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_st16(uint32_t taddr, const float *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "f"(r[0]), "f"(r[1]), "f"(r[2]), "f"(r[3]), "f"(r[4]), "f"(r[5]), "f"(r[6]), "f"(r[7]), "f"(r[8]), "f"(r[9]),
+        "f"(r[10]), "f"(r[11]), "f"(r[12]), "f"(r[13]), "f"(r[14]), "f"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, float *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]), "=f"(r[8]),
+          "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+// waits for this thread's tensor-memory loads; names the 16 destination
+// registers so that no use of them is scheduled before the data arrive
+__device__ __forceinline__ void tm_wait_ld16(float *r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(r[0]), "+f"(r[1]), "+f"(r[2]), "+f"(r[3]), "+f"(r[4]), "+f"(r[5]), "+f"(r[6]), "+f"(r[7]),
+                   "+f"(r[8]), "+f"(r[9]), "+f"(r[10]), "+f"(r[11]), "+f"(r[12]), "+f"(r[13]), "+f"(r[14]), "+f"(r[15])::"memory");
+}
+
+// Byte offset of lane `row`'s 16-byte chunk q (hands 4q..4q+3) in a
+// [32][16] fp32 box written by the 64-byte swizzle: chunk bits 4-5 are
+// XORed with address bits 7-8 (the row pair).
+__device__ __forceinline__ uint32_t swz(int row, int q) {
+    return (uint32_t)(row * 64 + ((q ^ ((row >> 1) & 3)) << 4));
+}
+
+// The CTA's column set, its warp's chunk and its shared-memory regions.
+struct Ctx {
+    unsigned char *sm;
+    int lane, warp;
+    int bb, sigma, rf, rs;
+    float F, S;
+    int b0, nb;                // first box of the chunk, boxes in it
+    uint32_t tmem;             // the warp's tensor-memory lanes, column 0
+    unsigned char *lb;         // this lane's entry of card 0 in the per-card table
+    bool ok;                   // no wait gave up
+};
+
+template <int KIND, int K2>
+__device__ __forceinline__ void tma_body(const TmaParams &P, Ctx &c) {
+    constexpr bool HF = (KIND & kKindF) != 0, HS = (KIND & kKindS) != 0;
+    constexpr int NS = KIND == kKindFS ? 3 : 6;                    // ring slots
+    constexpr int SLOT = KIND == kKindFS ? 4096 : 2048;            // bytes per slot
+    const int lane = c.lane, warp = c.warp, nc = P.nc;
+    unsigned char *ring = c.sm + ring_off(warp);
+    const uint32_t ring_s = smem_u32(ring);
+    const uint32_t bar0 = smem_u32(c.sm + kBarOff) + 8u * 8u * (uint32_t)warp;
+    float2 *st = reinterpret_cast<float2 *>(c.sm + state_off(warp, nc));
+    float *xpart = reinterpret_cast<float *>(c.sm + extra_off(warp, nc, P.extra));
+    float *sums = reinterpret_cast<float *>(c.sm + kSumOff);
+    const float F = c.F, S = c.S, S2 = 2.f * c.S;
+    const int nb = c.nb;
+    const int z0 = 32 * c.bb;
+
+    for (int q = 0; q < nc; ++q) st[q * 32 + lane] = make_float2(0.f, 0.f);
+
+    auto issue = [&](int m) {
+        const int s = m % NS;
+        const uint32_t bar = bar0 + 8u * (uint32_t)s;
+        const uint32_t dst = ring_s + (uint32_t)(s * SLOT);
+        const int x = kTmaBox * (c.b0 + m);
+        mbar_expect_tx(bar, (uint32_t)SLOT);
+        if (HF) tma_load3(dst, &P.tin, x, c.rf, z0, bar);
+        if (HS) tma_load3(dst + (HF ? 2048u : 0u), &P.tin, x, c.rs, z0, bar);
+    };
+    if (lane == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8u * (uint32_t)s, 1);
+        fence_barrier_init();
+        for (int m = 0; m < NS && m < nb; ++m) issue(m);
+    }
+    __syncwarp();
+    int nissued = min(NS, nb), nwaited = 0;   // boxes copied in / waited for (warp-uniform)
+
+    // ---- scan (lane = column)
+    float G = 0.f;
+    float pp[16];                 // the previous box's partial results (stored one box late)
+    float bq1 = 0.f, bq2 = 0.f, bq3 = 0.f;   // b of the previous box's hands 15, 14, 13
+#pragma unroll
+    for (int i = 0; i < 16; ++i) pp[i] = 0.f;
+    auto store_box = [&](int m, const float *r) {
+        if (m < 16) {
+            tm_st16(c.tmem + (uint32_t)(16 * m), r);
+        } else {
+            float *xp = xpart + (m - 16) * (kTmaBox * 32);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) xp[i * 32 + lane] = r[i];
+        }
+    };
+    for (int m = 0; m < nb; ++m) {
+        const int s = m % NS;
+        if (c.ok) {
+            const bool got = mbar_wait(bar0 + 8u * (uint32_t)s, (uint32_t)((m / NS) & 1));
+            c.ok = __all_sync(kFull, got);
+            if (c.ok) nwaited = m + 1;
+        }
+        const unsigned char *slot = ring + s * SLOT;
+        float yf[16], ys[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (HF) {
+                const float4 v = *reinterpret_cast<const float4 *>(slot + swz(lane, q));
+                yf[4 * q] = v.x; yf[4 * q + 1] = v.y; yf[4 * q + 2] = v.z; yf[4 * q + 3] = v.w;
+            } else {
+                yf[4 * q] = yf[4 * q + 1] = yf[4 * q + 2] = yf[4 * q + 3] = 0.f;
+            }
+            if (HS) {
+                const float4 v = *reinterpret_cast<const float4 *>(slot + (HF ? 2048 : 0) + swz(lane, q));
+                ys[4 * q] = v.x; ys[4 * q + 1] = v.y; ys[4 * q + 2] = v.z; ys[4 * q + 3] = v.w;
+            } else {
+                ys[4 * q] = ys[4 * q + 1] = ys[4 * q + 2] = ys[4 * q + 3] = 0.f;
+            }
+        }
+        const int h0 = kTmaBox * (c.b0 + m);
+        float p[16], bv[16];
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) {
+            const TmaHand r1 = P.rec[h0 + i], r2 = P.rec[h0 + i + 1];
+            const uint32_t pf = P.pflag[(h0 + i) >> 1];
+            float2 *A1 = reinterpret_cast<float2 *>(c.lb + r1.oa);
+            float2 *A2 = reinterpret_cast<float2 *>(c.lb + r2.oa);
+            float2 *B1 = reinterpret_cast<float2 *>(c.lb + r1.ob);
+            float2 *B2 = reinterpret_cast<float2 *>(c.lb + r2.ob);
+            float2 sa1 = *A1, sa2 = *A2, sb1 = make_float2(0.f, 0.f), sb2 = make_float2(0.f, 0.f);
+            if (K2 == 2) {
+                sb1 = *B1;
+                sb2 = *B2;
+            }
+            // the two hands' inputs: a (fold side), b (showdown side), w
+            const float a1 = r1.lam_in * yf[i], a2 = r2.lam_in * yf[i + 1];
+            const float b1 = r1.lam_in * ys[i], b2 = r2.lam_in * ys[i + 1];
+            bv[i] = b1;
+            bv[i + 1] = b2;
+            float w1, w2;
+            if (KIND == kKindFS) {
+                w1 = fmaf(F, a1, -(S * b1));
+                w2 = fmaf(F, a2, -(S * b2));
+            } else if (HF) {
+                w1 = F * a1;
+                w2 = F * a2;
+            } else {
+                w1 = w2 = 0.f;   // a showdown-only column tracks b alone
+            }
+            // the first hand's update, seen by the second when they share a card
+            const float d1 = HS ? b1 : w1;
+            if (pf & 3u) {
+                if (pf & 1u) {
+                    sa2.x += d1;
+                    if (KIND == kKindFS) sa2.y += w1;
+                }
+                if (K2 == 2 && (pf & 2u)) {
+                    sb2.x += d1;
+                    if (KIND == kKindFS) sb2.y += w1;
+                }
+            }
+            if (HS) {
+                // t = 2 Lo_ord - TB (b units); partial = w + S t (+ w only
+                // for two-card hands, see K_F)
+                float t1 = 2.f * (G - sa1.x - sb1.x);
+                const float g1 = G + b1;
+                float t2 = 2.f * (g1 - sa2.x - sb2.x);
+                G = g1 + b2;
+                if (pf & 0xfcu) {
+                    // tie corrections: TB for each hand, TA into the
+                    // earlier partner's partial result
+                    auto bat = [&](int j) { return j >= 0 ? bv[j] : (j == -1 ? bq1 : j == -2 ? bq2 : bq3); };
+                    auto pat = [&](int j) -> float & { return j >= 0 ? p[j] : pp[16 + j]; };
+#pragma unroll
+                    for (int d = 1; d <= 3; ++d)
+                        if (pf & (1u << (1 + d))) t1 -= bat(i - d);
+#pragma unroll
+                    for (int d = 2; d <= 3; ++d)
+                        if (pf & (1u << (4 + d))) t2 -= bat(i + 1 - d);
+                    if (pf & (1u << 5)) t2 -= b1;
+                    p[i] = (K2 == 2 ? w1 : 0.f) + S * t1;
+                    p[i + 1] = (K2 == 2 ? w2 : 0.f) + S * t2;
+#pragma unroll
+                    for (int d = 1; d <= 3; ++d)
+                        if (pf & (1u << (1 + d))) pat(i - d) += S * b1;
+#pragma unroll
+                    for (int d = 1; d <= 3; ++d)
+                        if (pf & (1u << (4 + d))) pat(i + 1 - d) += S * b2;
+                } else {
+                    p[i] = (K2 == 2 ? w1 : 0.f) + S * t1;
+                    p[i + 1] = (K2 == 2 ? w2 : 0.f) + S * t2;
+                }
+                if (!HF) {
+                    // showdown only: w = -S b
+                    if (K2 == 2) {
+                        p[i] -= S * b1;
+                        p[i + 1] -= S * b2;
+                    }
+                }
+            } else {
+                p[i] = K2 == 2 ? w1 : 0.f;
+                p[i + 1] = K2 == 2 ? w2 : 0.f;
+            }
+            // per-card updates (the second hand's store is the later one)
+            if (KIND == kKindFS) {
+                *A1 = make_float2(sa1.x + b1, sa1.y + w1);
+                if (K2 == 2) *B1 = make_float2(sb1.x + b1, sb1.y + w1);
+                *A2 = make_float2(sa2.x + b2, sa2.y + w2);
+                if (K2 == 2) *B2 = make_float2(sb2.x + b2, sb2.y + w2);
+            } else {
+                const float d2 = HS ? b2 : w2;
+                reinterpret_cast<float *>(A1)[0] = sa1.x + d1;
+                if (K2 == 2) reinterpret_cast<float *>(B1)[0] = sb1.x + d1;
+                reinterpret_cast<float *>(A2)[0] = sa2.x + d2;
+                if (K2 == 2) reinterpret_cast<float *>(B2)[0] = sb2.x + d2;
+            }
+        }
+        // every lane has used the slot's values: refill it
+        __syncwarp();
+        if (c.ok && m + NS < nb) {
+            if (lane == 0) {
+                fence_proxy_async();
+                issue(m + NS);
+            }
+            nissued = m + NS + 1;
+        }
+        if (m > 0) store_box(m - 1, pp);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) pp[i] = p[i];
+        bq1 = bv[15];
+        bq2 = bv[14];
+        bq3 = bv[13];
+    }
+    if (nb > 0) store_box(nb - 1, pp);
+    tm_wait_st();
+    if (!c.ok && lane == 0) {
+        // a wait gave up: wait (bounded) for the copies still in flight
+        // before the ring is reused or the CTA exits
+        for (int m = nwaited; m < nissued; ++m)
+            if (!mbar_wait(bar0 + 8u * (uint32_t)(m % NS), (uint32_t)((m / NS) & 1))) break;
+    }
+    __syncwarp();
+
+    // per-warp totals: G (b mass) and Tot (w total; K_F's Tot)
+    float tot = 0.f;
+    if (HF) {
+        for (int q = 0; q < nc; ++q) tot += KIND == kKindFS ? st[q * 32 + lane].y : st[q * 32 + lane].x;
+        if (K2 == 2) tot *= 0.5f;
+    } else {
+        tot = -S * G;
+    }
+    sums[(0 * kTmaWarps + warp) * 32 + lane] = G;
+    sums[(1 * kTmaWarps + warp) * 32 + lane] = tot;
+    __syncthreads();
+
+    // ---- combination: Q_k[c] = Pall[c] + 2 S (mass of card c in chunks < k),
+    // in place in the .x entries of every warp's table
+    for (int q = warp; q < nc; q += kTmaWarps) {
+        float rr[kTmaWarps], pw[kTmaWarps];
+#pragma unroll
+        for (int k = 0; k < kTmaWarps; ++k) {
+            const float2 v = reinterpret_cast<const float2 *>(c.sm + state_off(k, nc))[q * 32 + lane];
+            if (KIND == kKindFS) {
+                rr[k] = v.x;
+                pw[k] = v.y;
+            } else if (HF) {
+                rr[k] = 0.f;
+                pw[k] = v.x;
+            } else {
+                rr[k] = v.x;
+                pw[k] = -S * v.x;
+            }
+        }
+        const float pall = (pw[0] + pw[1]) + (pw[2] + pw[3]);
+        float run = 0.f;
+#pragma unroll
+        for (int k = 0; k < kTmaWarps; ++k) {
+            reinterpret_cast<float *>(c.sm + state_off(k, nc))[2 * (q * 32 + lane)] = pall + S2 * run;
+            run += rr[k];
+        }
+    }
+    float Cw;
+    {
+        float T = 0.f, gb = 0.f;
+#pragma unroll
+        for (int k = 0; k < kTmaWarps; ++k) {
+            T += sums[(1 * kTmaWarps + k) * 32 + lane];
+            if (k < warp) gb += sums[(0 * kTmaWarps + k) * 32 + lane];
+        }
+        Cw = T + S2 * gb;
+    }
+    __syncthreads();
+
+    // ---- finishing pass: out = lambda_out (partial + C - Q[c1] - Q[c2]),
+    // staged in swizzled boxes (the ring, 2 KB each) and stored by TMA
+    const unsigned char *qb = c.lb;
+    float cur[16], nxt[16];
+    auto load_box = [&](int m, float *r) {
+        if (m < 16) {
+            tm_ld16(c.tmem + (uint32_t)(16 * m), r);
+        } else {
+            const float *xp = xpart + (m - 16) * (kTmaBox * 32);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) r[i] = xp[i * 32 + lane];
+        }
+    };
+    if (nb > 0) {
+        load_box(0, cur);
+        tm_wait_ld16(cur);
+    }
+    for (int m = 0; m < nb; ++m) {
+        if (m + 1 < nb) load_box(m + 1, nxt);
+        const int h0 = kTmaBox * (c.b0 + m);
+        float o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const TmaHand r = P.rec[h0 + i];
+            float q = *reinterpret_cast<const float *>(qb + r.oa);
+            if (K2 == 2) q += *reinterpret_cast<const float *>(qb + r.ob);
+            o[i] = r.lam_out * ((cur[i] + Cw) - q);
+        }
+        const int ob = m % 6;
+        unsigned char *buf = ring + ob * 2048;
+        if (m >= 6) {
+            if (lane == 0) bulk_wait_read<5>();
+            __syncwarp();
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<float4 *>(buf + swz(lane, q)) = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+            tma_store3(&P.tout, kTmaBox * (c.b0 + m), c.sigma, z0, smem_u32(buf));
+            bulk_commit();
+        }
+        if (m + 1 < nb) {
+            tm_wait_ld16(nxt);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
+        }
+    }
+    if (lane == 0) bulk_wait_read<0>();
+    __syncwarp();
+}
+
+template <int K2>
+__global__ void __launch_bounds__(128, 2) tma_scan_kernel(const __grid_constant__ TmaParams P) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // the swizzled boxes need 1 KB alignment (one KB of slack is allocated)
+    unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    Ctx c;
+    c.sm = sm;
+    c.lane = threadIdx.x & 31;
+    c.warp = threadIdx.x >> 5;
+    c.bb = blockIdx.x / P.n_out;
+    c.sigma = blockIdx.x - c.bb * P.n_out;
+    c.rf = P.fcol[c.sigma];
+    c.rs = P.scol[c.sigma];
+    c.F = c.rf >= 0 ? P.fcoef[c.sigma] : 0.f;
+    c.S = c.rs >= 0 ? P.scoef[c.sigma] : 0.f;
+    c.b0 = P.bchunk[c.warp];
+    c.nb = P.bchunk[c.warp + 1] - c.b0;
+    c.ok = true;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm);
+    if (c.warp == 0) tm_alloc(smem_u32(tslot), kTmemCols);
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    const uint32_t tbase = *tslot;
+    c.tmem = tbase + ((uint32_t)(32 * c.warp) << 16);
+    c.lb = sm + state_off(c.warp, P.nc) + 8 * c.lane;
+    const int kind = (c.rf >= 0 ? kKindF : 0) | (c.rs >= 0 ? kKindS : 0);
+    if (kind == kKindFS) tma_body<kKindFS, K2>(P, c);
+    else if (kind == kKindF) tma_body<kKindF, K2>(P, c);
+    else tma_body<kKindS, K2>(P, c);
+    if (!c.ok && c.lane == 0) atomicExch(P.err, 1u);
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (c.warp == 0) tm_dealloc(tbase, kTmemCols);
+}
+
+// ---- host ------------------------------------------------------------------
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn(cudaError_t *err) {
+    static std::once_flag once;
+    static EncodeFn fn = nullptr;
+    static cudaError_t status = cudaSuccess;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        status = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (status == cudaSuccess && (q != cudaDriverEntryPointSuccess || !p)) status = cudaErrorSymbolNotFound;
+        if (status == cudaSuccess) fn = reinterpret_cast<EncodeFn>(p);
+    });
+    *err = status;
+    return fn;
+}
+
+cudaError_t encode3(CUtensorMap *map, const void *base, int x, int y, int z, int pitch) {
+    cudaError_t e;
+    EncodeFn fn = encode_fn(&e);
+    if (!fn) return e;
+    const cuuint64_t dims[3] = {(cuuint64_t)x, (cuuint64_t)y, (cuuint64_t)z};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * 4 * (cuuint64_t)y};
+    const cuuint32_t box[3] = {(cuuint32_t)kTmaBox, 1, 32};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+__device__ unsigned int g_tma_err;
+
+}  // namespace
+
+static size_t tma_smem_bytes(int nc, int extra) { return extra_off(kTmaWarps, nc, extra) + 1024; }
+
+static std::string tma_prepare(const HostGame &h, const double *lam_in, const double *lam_out, TmaParams &p) {
+    if (h.k != 1 && h.k != 2) return "cards per hand";
+    if (h.hs > kTmaMaxHands) return "too many hands for the parameter block";
+    const int nc = h.ncards + 1;
+    if (nc > 64) return "too many cards";
+    const int H = h.H, hs = h.hs;
+    const int nbox = (hs + kTmaBox - 1) / kTmaBox;
+    if (nbox * kTmaBox > kTmaMaxHands) return "too many hands for the parameter block";
+    // tie groups: at most 4 hands (partners within 3 positions)
+    for (int i = 0; i < H; ++i)
+        if (h.group_hi[i] - h.group_lo[i] > 3) return "tie group longer than 4 hands";
+    // chunk boundaries at box boundaries that cut no tie group, as close to
+    // an even split as possible
+    auto clean = [&](int bx) { return bx <= 0 || bx >= nbox || 16 * bx >= H || h.group_lo[16 * bx] == 16 * bx; };
+    p.bchunk[0] = 0;
+    p.bchunk[kTmaWarps] = nbox;
+    for (int k = 1; k < kTmaWarps; ++k) {
+        const int ideal = (int)((long long)nbox * k / kTmaWarps);
+        int best = -1;
+        for (int d = 0; d <= 4 && best < 0; ++d) {
+            for (int s : {ideal - d, ideal + d})
+                if (best < 0 && s >= p.bchunk[k - 1] && s <= nbox && clean(s)) best = s;
+        }
+        if (best < 0) return "no chunk boundary free of tie groups";
+        p.bchunk[k] = best;
+    }
+    int extra = 0;
+    for (int k = 0; k < kTmaWarps; ++k) {
+        const int n = p.bchunk[k + 1] - p.bchunk[k];
+        if (n < 0) return "chunk order";
+        extra = std::max(extra, n - 16);
+    }
+    if (extra > kTmaMaxExtra) return "chunk longer than tensor memory and its shared-memory overflow";
+    p.H = H;
+    p.hs = hs;
+    p.nc = nc;
+    p.k = h.k;
+    p.nbox = nbox;
+    p.extra = extra;
+    std::memset(p.pflag, 0, sizeof(p.pflag));
+    std::memset(p.rec, 0, sizeof(p.rec));
+    auto card = [&](int hand, int j) { return h.hand_slots[2 * hand + j]; };
+    for (int i = 0; i < nbox * kTmaBox; ++i) {
+        TmaHand &r = p.rec[i];
+        if (i < H) {
+            r.oa = (uint32_t)card(i, 0) * 256u;
+            r.ob = (uint32_t)(h.k == 2 ? card(i, 1) : h.ncards) * 256u;
+            r.lam_in = (float)lam_in[i];
+            r.lam_out = (float)lam_out[i];
+        } else {
+            // padding: zero weights, the spare card row
+            r.oa = r.ob = (uint32_t)h.ncards * 256u;
+        }
+    }
+    auto share = [&](int x, int y) {   // any card of hand y in hand x
+        for (int j = 0; j < h.k; ++j)
+            for (int l = 0; l < h.k; ++l)
+                if (card(x, j) == card(y, l)) return true;
+        return false;
+    };
+    for (int i = 0; i + 1 < H; i += 2) {
+        uint32_t f = 0;
+        for (int j = 0; j < h.k; ++j)
+            for (int l = 0; l < h.k; ++l)
+                if (card(i + 1, j) == card(i, l)) f |= 1u << j;
+        p.pflag[i >> 1] |= f;
+    }
+    for (int i = 0; i < H; ++i) {
+        for (int d = 1; d <= 3; ++d) {
+            const int q = i - d;
+            if (q < h.group_lo[i]) break;
+            if (share(i, q)) continue;
+            p.pflag[i >> 1] |= 1u << ((i & 1) ? 4 + d : 1 + d);
+        }
+    }
+    return "";
+}
+
+TmaParams *tma_create(const HostGame &h, const double *lam_in, const double *lam_out, int n_out, int n_in,
+                      const int *fcol, const int *scol, const float *fcoef, const float *scoef,
+                      const int *hfcol, const int *hscol, std::string *why) {
+    TmaParams *p = new (std::nothrow) TmaParams();
+    if (!p) {
+        *why = "host allocation";
+        return nullptr;
+    }
+    std::string w = tma_prepare(h, lam_in, lam_out, *p);
+    for (int r = 0; r < n_out && w.empty(); ++r)
+        if (hfcol[r] < 0 && hscol[r] < 0) w = "an output sequence without terminals";
+    if (w.empty() && std::max<size_t>(tma_smem_bytes(p->nc, p->extra), 80 * 1024) > (size_t)max_dyn_smem())
+        w = "shared memory";
+    if (!w.empty()) {
+        delete p;
+        *why = w;
+        return nullptr;
+    }
+    p->n_out = n_out;
+    p->n_in = n_in;
+    p->fcol = fcol;
+    p->scol = scol;
+    p->fcoef = fcoef;
+    p->scoef = scoef;
+    p->err = nullptr;
+    return p;
+}
+
+void tma_destroy(TmaParams *p) { delete p; }
+
+cudaError_t launch_tma_scan(TmaParams *pp, const float *vin, float *vout, int batch, cudaStream_t stream) {
+    TmaParams &p = *pp;
+    p.batch = batch;
+    p.nbb = (batch + 31) / 32;
+    cudaError_t e = encode3(&p.tin, vin, p.H, p.n_in, batch, p.hs);
+    if (e == cudaSuccess) e = encode3(&p.tout, vout, p.hs, p.n_out, batch, p.hs);
+    if (e != cudaSuccess) return e;
+    if (!p.err) {
+        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p.err), g_tma_err);
+        if (e != cudaSuccess) return e;
+    }
+    // at least 80 KB: never more than two CTAs per SM, so that their tensor
+    // memory (256 columns each) always fits
+    const size_t smem = std::max<size_t>(tma_smem_bytes(p.nc, p.extra), 80 * 1024);
+    const long long blocks = (long long)p.n_out * p.nbb;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    auto fn = p.k == 1 ? tma_scan_kernel<1> : tma_scan_kernel<2>;
+    e = ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem);
+    if (e != cudaSuccess) return e;
+    fn<<<(unsigned)blocks, 32 * kTmaWarps, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace kps

@@ -74,7 +74,7 @@ class BatchShape(C.Structure):
 
 
 EXPORTED = ["kps_sparsify", "kps_game_destroy", "kps_game_info", "kps_game_hands",
-            "kps_game_sequences", "kps_game_terminals", "kps_game_upload",
+            "kps_game_sequences", "kps_game_terminals", "kps_game_upload", "kps_game_kernel",
             "kps_matvec_A", "kps_matvec_AT", "kps_matvec_A_host", "kps_matvec_AT_host",
             "kps_matvec_A_static_scratch",
             "kps_batch_create", "kps_batch_destroy", "kps_batch_offsets", "kps_batch_matvec_A",
@@ -108,6 +108,7 @@ def lib():
         L.kps_game_sequences.argtypes = [P, C.c_int32, P, P, P, P, P]
         L.kps_game_terminals.argtypes = [P, P, P, P, P, P, P]
         L.kps_game_upload.argtypes = [P, P]
+        L.kps_game_kernel.argtypes = [P, C.c_int32, C.POINTER(C.c_int32)]
         for f in (L.kps_matvec_A, L.kps_matvec_AT, L.kps_matvec_A_host, L.kps_matvec_AT_host,
                   L.kps_matvec_A_static_scratch):
             f.argtypes = [P, P, P, C.c_int32, C.c_int, P]
@@ -300,6 +301,13 @@ class Game:
     def upload(self, stream=None):
         _check(lib().kps_game_upload(self._h, _stream(stream)))
 
+    def kernel(self, direction: int) -> str:
+        """kps_game_kernel: name of the kernel that ran the last product of
+        a direction (0 = A*y, 1 = A^T*x); "" before the first."""
+        k = C.c_int32(0)
+        _check(lib().kps_game_kernel(self._h, int(direction), C.byref(k)))
+        return KERNEL_NAMES.get(k.value, "")
+
 
 def sparsify(spec: dict) -> Game:
     return Game(spec)
@@ -372,6 +380,7 @@ class TechniqueB:
 
 
 STATIC_SCRATCH_FLOATS = 4194304
+KERNEL_NAMES = {1: "tma", 2: "tmem", 3: "vec", 4: "fast", 5: "general"}
 
 
 def matvec_A_static_scratch(game: Game, y, out, batch: int, dtype=None, stream=None):

@@ -52,12 +52,12 @@ EXACT = [("kuhn", _kuhn_exact), ("micro", _micro_exact)]
 TDT = {kps.F32: torch.float32, kps.F64: torch.float64}
 
 
-@pytest.mark.parametrize("kernel", ["tmem", "vec", "fast"])
+@pytest.mark.parametrize("kernel", ["tma", "tmem", "vec", "fast"])
 @pytest.mark.parametrize("dt", [kps.F32, kps.F64])
 @pytest.mark.parametrize("name,mk", EXACT, ids=[e[0] for e in EXACT])
 def test_products_bit_exact(name, mk, dt, kernel, monkeypatch):
-    if kernel == "tmem" and dt == kps.F64:
-        pytest.skip("tensor-memory path is FP32 arithmetic")
+    if kernel in ("tmem", "tma") and dt == kps.F64:
+        pytest.skip("tensor-memory paths are FP32 arithmetic")
     monkeypatch.setenv("KPS_KERNEL", kernel)
     spec = mk()
     og, g = OracleGame(spec), kps.Game(spec)

@@ -70,7 +70,7 @@ def river():
     return spec, OracleGame(spec), kps.Game(spec), library_order(spec["strength"])
 
 
-KERNELS = ["tmem", "vec", "fast"]
+KERNELS = ["tma", "tmem", "vec", "fast"]
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
