@@ -63,52 +63,72 @@ namespace kps {
 
 constexpr int kTmaBox = 16;        // hands per box
 constexpr int kTmaWarps = 4;       // chunks per CTA
-constexpr int kTmaMaxHands = 1344; // records in the parameter block (hs <= this)
 constexpr int kTmaMaxExtra = 2;    // boxes of a chunk past the 256 tensor-memory columns
 
-// Per-hand record (library order, padding hands included): byte offsets of
-// the hand's card rows in a warp's per-card table (card * 256; one-card
-// hands: ob unused) and the two lambda weights.
-struct alignas(16) TmaHand {
-    uint32_t oa, ob;
-    float lam_in, lam_out;
+// Scan records of a pair of hands (2i, 2i+1 of the library order, padding
+// hands included): byte offsets of the hands' card rows in a warp's per-card
+// table (card * 128; one-card hands: ob unused), their input weights
+// lambda_in, and ma / mb = 1 when the first / second card of hand 2i+1 is a
+// card of hand 2i (else 0).  A box's block is its 8 pair records followed by
+// two tie words: byte 8j + (k - 4j) of word j (pair k) has
+//   bits 2-4  hand 2k has a compatible tied hand 1, 2, 3 positions before it
+//   bits 5-7  the same for hand 2k+1.
+struct alignas(16) TmaScanRec {
+    uint32_t oa1, ob1, oa2, ob2;
+    float lin1, lin2, ma, mb;
+};
+constexpr int kScanBlock = 8 * 32 + 16;   // bytes per box
+// Finishing records of a pair: the card offsets and the output weights.
+struct alignas(16) TmaFinRec {
+    uint32_t oa1, ob1, oa2, ob2;
+    float lout1, lout2, pad0, pad1;
 };
 
-// Per-pair flags (hands 2i and 2i+1 of the library order):
-//   bit 0 / 1   the first / second card of hand 2i+1 is a card of hand 2i
-//   bits 2-4    hand 2i has a compatible tied hand 1, 2, 3 positions before it
-//   bits 5-7    the same for hand 2i+1
-struct alignas(128) TmaParams {
+// Kernel arguments (__grid_constant__).
+struct alignas(128) TmaArgs {
     CUtensorMap tin;               // input  [batch][n_in][H]  fp32, box 16 x 1 x 32, 64-byte swizzle
     CUtensorMap tout;              // output [batch][n_out][hs] fp32, same box
     int H, hs, nc, k, n_out, n_in, batch, nbb, nbox, extra;
     int bchunk[kTmaWarps + 1];     // warp k scans boxes [bchunk[k], bchunk[k+1])
     const int *fcol, *scol;        // per output sequence: its fold / showdown input sequence or -1
     const float *fcoef, *scoef;    // and the payoffs
+    const unsigned char *rscan;    // [nbox][kScanBlock]
+    const TmaFinRec *rfin;         // [nbox * 8]
     unsigned int *err;             // set to 1 when a wait gives up
-    uint32_t pflag[kTmaMaxHands / 2];
-    TmaHand rec[kTmaMaxHands];
+};
+
+// Host side of one direction: the arguments and the record tables.
+struct TmaParams {
+    TmaArgs a;
+    void *dev = nullptr;           // device copy of the records (scan blocks, then finishing records)
+    std::vector<unsigned char> host;
+    int device = -1;
 };
 
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRingBytes = 12288;          // per warp: 3 slots of 4 KB or 6 of 2 KB
+constexpr int kRecRing = 6 * kScanBlock;   // per warp: one scan block per slot
 constexpr int kTmemCols = 256;             // per CTA (two CTAs per SM)
-constexpr int kHdrBytes = 2048;            // tensor-memory slot, barriers, per-warp sums
-constexpr int kBarOff = 64;                // 4 warps x 8 mbarriers
-constexpr int kSumOff = 512;               // [2][4][32] floats: G_k, Tot_k
+constexpr int kHdrBytes = 1536;            // tensor-memory slot, barriers, per-warp sums
 constexpr unsigned long long kWaitNs = 2000000000ull;   // give up after 2 s
 
 enum Kind { kKindF = 1, kKindS = 2, kKindFS = 3 };
 
-__host__ __device__ inline size_t ring_off(int w) { return kHdrBytes + (size_t)w * kRingBytes; }
-__host__ __device__ inline size_t state_off(int w, int nc) {
-    return kHdrBytes + (size_t)kTmaWarps * kRingBytes + (size_t)w * nc * 256;
-}
+// Shared memory (from a 1 KB aligned base): the four warps' rings, their
+// per-card tables (nc rows of 256 bytes), their overflow boxes of partial
+// results, their record rings, then the header (tensor-memory slot at +0,
+// 4 x 8 mbarriers at +16, per-warp sums [2][4][32] floats at +272).
+__host__ __device__ inline size_t ring_off(int w) { return (size_t)w * kRingBytes; }
+__host__ __device__ inline size_t state_off(int w, int nc) { return (size_t)kTmaWarps * kRingBytes + (size_t)w * nc * 256; }
 __host__ __device__ inline size_t extra_off(int w, int nc, int extra) {
     return state_off(kTmaWarps, nc) + (size_t)w * extra * kTmaBox * 32 * 4;
 }
+__host__ __device__ inline size_t rec_off(int w, int nc, int extra) {
+    return extra_off(kTmaWarps, nc, extra) + (size_t)w * kRecRing;
+}
+__host__ __device__ inline size_t hdr_off(int nc, int extra) { return rec_off(kTmaWarps, nc, extra); }
 
 // ---- PTX wrappers ------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -158,6 +178,19 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap *map, 
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ TmaFinRec ldg_fin(const TmaFinRec *p) {
+    const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
+    const float4 y = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+    TmaFinRec r;
+    r.oa1 = x.x; r.ob1 = x.y; r.oa2 = x.z; r.ob2 = x.w;
+    r.lout1 = y.x; r.lout2 = y.y; r.pad0 = y.z; r.pad1 = y.w;
+    return r;
+}
 __device__ __forceinline__ void tma_store3(const CUtensorMap *map, int x, int y, int z, uint32_t src) {
     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
                      reinterpret_cast<uint64_t>(map)),
@@ -168,6 +201,15 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 template <int N>
 __device__ __forceinline__ void bulk_wait_read() {
     asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// the same with a run-time count of at most 5 groups still reading
+__device__ __forceinline__ void bulk_wait_read_n(int n) {
+    if (n <= 0) bulk_wait_read<0>();
+    else if (n == 1) bulk_wait_read<1>();
+    else if (n == 2) bulk_wait_read<2>();
+    else if (n == 3) bulk_wait_read<3>();
+    else if (n == 4) bulk_wait_read<4>();
+    else bulk_wait_read<5>();
 }
 
 __device__ __forceinline__ void tm_alloc(uint32_t dst_smem, uint32_t ncols) {
@@ -219,39 +261,47 @@ struct Ctx {
     float F, S;
     int b0, nb;                // first box of the chunk, boxes in it
     uint32_t tmem;             // the warp's tensor-memory lanes, column 0
-    unsigned char *lb;         // this lane's entry of card 0 in the per-card table
     bool ok;                   // no wait gave up
 };
 
 template <int KIND, int K2>
-__device__ __forceinline__ void tma_body(const TmaParams &P, Ctx &c) {
-    constexpr bool HF = (KIND & kKindF) != 0, HS = (KIND & kKindS) != 0;
-    constexpr int NS = KIND == kKindFS ? 3 : 6;                    // ring slots
-    constexpr int SLOT = KIND == kKindFS ? 4096 : 2048;            // bytes per slot
+__device__ __forceinline__ void tma_body(const TmaArgs &P, Ctx &c) {
+    constexpr bool HF = (KIND & kKindF) != 0, HS = (KIND & kKindS) != 0, FS = KIND == kKindFS;
+    constexpr int NS = FS ? 3 : 6;                    // ring slots
+    constexpr int SLOT = FS ? 4096 : 2048;            // bytes per slot
     const int lane = c.lane, warp = c.warp, nc = P.nc;
     unsigned char *ring = c.sm + ring_off(warp);
     const uint32_t ring_s = smem_u32(ring);
-    const uint32_t bar0 = smem_u32(c.sm + kBarOff) + 8u * 8u * (uint32_t)warp;
-    float2 *st = reinterpret_cast<float2 *>(c.sm + state_off(warp, nc));
+    unsigned char *hdr = c.sm + hdr_off(nc, P.extra);
+    const uint32_t bar0 = smem_u32(hdr + 16) + 8u * 8u * (uint32_t)warp;
+    unsigned char *rring = c.sm + rec_off(warp, nc, P.extra);
+    const uint32_t rring_s = smem_u32(rring);
+    // per-card table of the chunk, [card][lane]: float2 {b mass, w total}
+    // for columns of both kinds (rows of 256 bytes, row offset 2 * off),
+    // one float otherwise (rows of 128 bytes, offset off)
+    unsigned char *stb = c.sm + state_off(warp, nc);
+    unsigned char *lb = stb + (FS ? 8 : 4) * lane;
     float *xpart = reinterpret_cast<float *>(c.sm + extra_off(warp, nc, P.extra));
-    float *sums = reinterpret_cast<float *>(c.sm + kSumOff);
+    float *sums = reinterpret_cast<float *>(hdr + 272);
     const float F = c.F, S = c.S, S2 = 2.f * c.S;
     const int nb = c.nb;
     const int z0 = 32 * c.bb;
+    auto row = [&](uint32_t off) -> unsigned char * { return lb + (FS ? 2 * off : off); };
 
-    for (int q = 0; q < nc; ++q) st[q * 32 + lane] = make_float2(0.f, 0.f);
+    for (int q = lane; q < nc * (FS ? 64 : 32); q += 32) reinterpret_cast<float *>(stb)[q] = 0.f;
 
     auto issue = [&](int m) {
-        const int s = m % NS;
-        const uint32_t bar = bar0 + 8u * (uint32_t)s;
-        const uint32_t dst = ring_s + (uint32_t)(s * SLOT);
+        const int sl = m % NS;
+        const uint32_t bar = bar0 + 8u * (uint32_t)sl;
+        const uint32_t dst = ring_s + (uint32_t)(sl * SLOT);
         const int x = kTmaBox * (c.b0 + m);
-        mbar_expect_tx(bar, (uint32_t)SLOT);
+        mbar_expect_tx(bar, (uint32_t)(SLOT + kScanBlock));
         if (HF) tma_load3(dst, &P.tin, x, c.rf, z0, bar);
         if (HS) tma_load3(dst + (HF ? 2048u : 0u), &P.tin, x, c.rs, z0, bar);
+        bulk_load(rring_s + (uint32_t)(sl * kScanBlock), P.rscan + (size_t)(c.b0 + m) * kScanBlock, kScanBlock, bar);
     };
     if (lane == 0) {
-        for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8u * (uint32_t)s, 1);
+        for (int sl = 0; sl < NS; ++sl) mbar_init(bar0 + 8u * (uint32_t)sl, 1);
         fence_barrier_init();
         for (int m = 0; m < NS && m < nb; ++m) issue(m);
     }
@@ -274,13 +324,13 @@ __device__ __forceinline__ void tma_body(const TmaParams &P, Ctx &c) {
         }
     };
     for (int m = 0; m < nb; ++m) {
-        const int s = m % NS;
+        const int sl = m % NS;
         if (c.ok) {
-            const bool got = mbar_wait(bar0 + 8u * (uint32_t)s, (uint32_t)((m / NS) & 1));
+            const bool got = mbar_wait(bar0 + 8u * (uint32_t)sl, (uint32_t)((m / NS) & 1));
             c.ok = __all_sync(kFull, got);
             if (c.ok) nwaited = m + 1;
         }
-        const unsigned char *slot = ring + s * SLOT;
+        const unsigned char *slot = ring + sl * SLOT;
         float yf[16], ys[16];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -297,102 +347,111 @@ __device__ __forceinline__ void tma_body(const TmaParams &P, Ctx &c) {
                 ys[4 * q] = ys[4 * q + 1] = ys[4 * q + 2] = ys[4 * q + 3] = 0.f;
             }
         }
-        const int h0 = kTmaBox * (c.b0 + m);
+        // the box's records: the next pair's are read before this pair's
+        // per-card stores (program order keeps them ahead)
+        const unsigned char *rs = rring + sl * kScanBlock;
+        const uint32_t tw0 = reinterpret_cast<const uint32_t *>(rs + 256)[0];
+        const uint32_t tw1 = reinterpret_cast<const uint32_t *>(rs + 256)[1];
+        TmaScanRec rn = *reinterpret_cast<const TmaScanRec *>(rs);
         float p[16], bv[16];
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
-            const TmaHand r1 = P.rec[h0 + i], r2 = P.rec[h0 + i + 1];
-            const uint32_t pf = P.pflag[(h0 + i) >> 1];
-            float2 *A1 = reinterpret_cast<float2 *>(c.lb + r1.oa);
-            float2 *A2 = reinterpret_cast<float2 *>(c.lb + r2.oa);
-            float2 *B1 = reinterpret_cast<float2 *>(c.lb + r1.ob);
-            float2 *B2 = reinterpret_cast<float2 *>(c.lb + r2.ob);
-            float2 sa1 = *A1, sa2 = *A2, sb1 = make_float2(0.f, 0.f), sb2 = make_float2(0.f, 0.f);
-            if (K2 == 2) {
-                sb1 = *B1;
-                sb2 = *B2;
+            const TmaScanRec r = rn;
+            if (i + 2 < 16) rn = reinterpret_cast<const TmaScanRec *>(rs)[i / 2 + 1];
+            unsigned char *A1 = row(r.oa1), *A2 = row(r.oa2), *B1 = row(r.ob1), *B2 = row(r.ob2);
+            float2 sa1, sa2, sb1 = make_float2(0.f, 0.f), sb2 = make_float2(0.f, 0.f);
+            if (FS) {
+                sa1 = *reinterpret_cast<const float2 *>(A1);
+                sa2 = *reinterpret_cast<const float2 *>(A2);
+                if (K2 == 2) {
+                    sb1 = *reinterpret_cast<const float2 *>(B1);
+                    sb2 = *reinterpret_cast<const float2 *>(B2);
+                }
+            } else {
+                sa1.x = *reinterpret_cast<const float *>(A1);
+                sa2.x = *reinterpret_cast<const float *>(A2);
+                sa1.y = sa2.y = 0.f;
+                if (K2 == 2) {
+                    sb1.x = *reinterpret_cast<const float *>(B1);
+                    sb2.x = *reinterpret_cast<const float *>(B2);
+                }
             }
             // the two hands' inputs: a (fold side), b (showdown side), w
-            const float a1 = r1.lam_in * yf[i], a2 = r2.lam_in * yf[i + 1];
-            const float b1 = r1.lam_in * ys[i], b2 = r2.lam_in * ys[i + 1];
+            const float b1 = HS ? r.lin1 * ys[i] : 0.f, b2 = HS ? r.lin2 * ys[i + 1] : 0.f;
             bv[i] = b1;
             bv[i + 1] = b2;
             float w1, w2;
-            if (KIND == kKindFS) {
-                w1 = fmaf(F, a1, -(S * b1));
-                w2 = fmaf(F, a2, -(S * b2));
+            if (FS) {
+                w1 = fmaf(F, r.lin1 * yf[i], -(S * b1));
+                w2 = fmaf(F, r.lin2 * yf[i + 1], -(S * b2));
             } else if (HF) {
-                w1 = F * a1;
-                w2 = F * a2;
+                w1 = F * (r.lin1 * yf[i]);
+                w2 = F * (r.lin2 * yf[i + 1]);
             } else {
                 w1 = w2 = 0.f;   // a showdown-only column tracks b alone
             }
-            // the first hand's update, seen by the second when they share a card
+            // the first hand's update, seen by the second hand's sums when
+            // they share a card (ma, mb are 0 or 1)
             const float d1 = HS ? b1 : w1;
-            if (pf & 3u) {
-                if (pf & 1u) {
-                    sa2.x += d1;
-                    if (KIND == kKindFS) sa2.y += w1;
-                }
-                if (K2 == 2 && (pf & 2u)) {
-                    sb2.x += d1;
-                    if (KIND == kKindFS) sb2.y += w1;
-                }
+            sa2.x = fmaf(r.ma, d1, sa2.x);
+            if (FS) sa2.y = fmaf(r.ma, w1, sa2.y);
+            if (K2 == 2) {
+                sb2.x = fmaf(r.mb, d1, sb2.x);
+                if (FS) sb2.y = fmaf(r.mb, w1, sb2.y);
             }
             if (HS) {
-                // t = 2 Lo_ord - TB (b units); partial = w + S t (+ w only
-                // for two-card hands, see K_F)
-                float t1 = 2.f * (G - sa1.x - sb1.x);
+                // t = 2 Lo_ord - TB (b units); partial = w + S t, the w only
+                // for two-card hands (see K_F)
+                float t1 = 2.f * (G - (sa1.x + sb1.x));
                 const float g1 = G + b1;
-                float t2 = 2.f * (g1 - sa2.x - sb2.x);
+                float t2 = 2.f * (g1 - (sa2.x + sb2.x));
                 G = g1 + b2;
-                if (pf & 0xfcu) {
+                const uint32_t tb = ((i / 2 < 4 ? tw0 : tw1) >> (8 * ((i / 2) & 3))) & 0xfcu;
+                if (tb) {
                     // tie corrections: TB for each hand, TA into the
                     // earlier partner's partial result
                     auto bat = [&](int j) { return j >= 0 ? bv[j] : (j == -1 ? bq1 : j == -2 ? bq2 : bq3); };
                     auto pat = [&](int j) -> float & { return j >= 0 ? p[j] : pp[16 + j]; };
 #pragma unroll
                     for (int d = 1; d <= 3; ++d)
-                        if (pf & (1u << (1 + d))) t1 -= bat(i - d);
+                        if (tb & (1u << (1 + d))) t1 -= bat(i - d);
 #pragma unroll
                     for (int d = 2; d <= 3; ++d)
-                        if (pf & (1u << (4 + d))) t2 -= bat(i + 1 - d);
-                    if (pf & (1u << 5)) t2 -= b1;
+                        if (tb & (1u << (4 + d))) t2 -= bat(i + 1 - d);
+                    if (tb & (1u << 5)) t2 -= b1;
                     p[i] = (K2 == 2 ? w1 : 0.f) + S * t1;
                     p[i + 1] = (K2 == 2 ? w2 : 0.f) + S * t2;
 #pragma unroll
                     for (int d = 1; d <= 3; ++d)
-                        if (pf & (1u << (1 + d))) pat(i - d) += S * b1;
+                        if (tb & (1u << (1 + d))) pat(i - d) += S * b1;
 #pragma unroll
                     for (int d = 1; d <= 3; ++d)
-                        if (pf & (1u << (4 + d))) pat(i + 1 - d) += S * b2;
+                        if (tb & (1u << (4 + d))) pat(i + 1 - d) += S * b2;
                 } else {
-                    p[i] = (K2 == 2 ? w1 : 0.f) + S * t1;
-                    p[i + 1] = (K2 == 2 ? w2 : 0.f) + S * t2;
+                    p[i] = fmaf(S, t1, K2 == 2 ? w1 : 0.f);
+                    p[i + 1] = fmaf(S, t2, K2 == 2 ? w2 : 0.f);
                 }
-                if (!HF) {
+                if (!HF && K2 == 2) {
                     // showdown only: w = -S b
-                    if (K2 == 2) {
-                        p[i] -= S * b1;
-                        p[i + 1] -= S * b2;
-                    }
+                    p[i] = fmaf(-S, b1, p[i]);
+                    p[i + 1] = fmaf(-S, b2, p[i + 1]);
                 }
             } else {
                 p[i] = K2 == 2 ? w1 : 0.f;
                 p[i + 1] = K2 == 2 ? w2 : 0.f;
             }
             // per-card updates (the second hand's store is the later one)
-            if (KIND == kKindFS) {
-                *A1 = make_float2(sa1.x + b1, sa1.y + w1);
-                if (K2 == 2) *B1 = make_float2(sb1.x + b1, sb1.y + w1);
-                *A2 = make_float2(sa2.x + b2, sa2.y + w2);
-                if (K2 == 2) *B2 = make_float2(sb2.x + b2, sb2.y + w2);
+            if (FS) {
+                *reinterpret_cast<float2 *>(A1) = make_float2(sa1.x + b1, sa1.y + w1);
+                if (K2 == 2) *reinterpret_cast<float2 *>(B1) = make_float2(sb1.x + b1, sb1.y + w1);
+                *reinterpret_cast<float2 *>(A2) = make_float2(sa2.x + b2, sa2.y + w2);
+                if (K2 == 2) *reinterpret_cast<float2 *>(B2) = make_float2(sb2.x + b2, sb2.y + w2);
             } else {
                 const float d2 = HS ? b2 : w2;
-                reinterpret_cast<float *>(A1)[0] = sa1.x + d1;
-                if (K2 == 2) reinterpret_cast<float *>(B1)[0] = sb1.x + d1;
-                reinterpret_cast<float *>(A2)[0] = sa2.x + d2;
-                if (K2 == 2) reinterpret_cast<float *>(B2)[0] = sb2.x + d2;
+                *reinterpret_cast<float *>(A1) = sa1.x + d1;
+                if (K2 == 2) *reinterpret_cast<float *>(B1) = sb1.x + d1;
+                *reinterpret_cast<float *>(A2) = sa2.x + d2;
+                if (K2 == 2) *reinterpret_cast<float *>(B2) = sb2.x + d2;
             }
         }
         // every lane has used the slot's values: refill it
@@ -424,7 +483,9 @@ __device__ __forceinline__ void tma_body(const TmaParams &P, Ctx &c) {
     // per-warp totals: G (b mass) and Tot (w total; K_F's Tot)
     float tot = 0.f;
     if (HF) {
-        for (int q = 0; q < nc; ++q) tot += KIND == kKindFS ? st[q * 32 + lane].y : st[q * 32 + lane].x;
+        for (int q = 0; q < nc; ++q)
+            tot += FS ? reinterpret_cast<const float2 *>(stb)[q * 32 + lane].y
+                      : reinterpret_cast<const float *>(stb)[q * 32 + lane];
         if (K2 == 2) tot *= 0.5f;
     } else {
         tot = -S * G;
@@ -434,28 +495,28 @@ __device__ __forceinline__ void tma_body(const TmaParams &P, Ctx &c) {
     __syncthreads();
 
     // ---- combination: Q_k[c] = Pall[c] + 2 S (mass of card c in chunks < k),
-    // in place in the .x entries of every warp's table
+    // [card][lane] floats at the start of warp k's ring (free now: every
+    // copy in has been consumed)
     for (int q = warp; q < nc; q += kTmaWarps) {
         float rr[kTmaWarps], pw[kTmaWarps];
 #pragma unroll
         for (int k = 0; k < kTmaWarps; ++k) {
-            const float2 v = reinterpret_cast<const float2 *>(c.sm + state_off(k, nc))[q * 32 + lane];
-            if (KIND == kKindFS) {
+            const unsigned char *sk = c.sm + state_off(k, nc);
+            if (FS) {
+                const float2 v = reinterpret_cast<const float2 *>(sk)[q * 32 + lane];
                 rr[k] = v.x;
                 pw[k] = v.y;
-            } else if (HF) {
-                rr[k] = 0.f;
-                pw[k] = v.x;
             } else {
-                rr[k] = v.x;
-                pw[k] = -S * v.x;
+                const float v = reinterpret_cast<const float *>(sk)[q * 32 + lane];
+                rr[k] = HS ? v : 0.f;
+                pw[k] = HS ? -S * v : v;
             }
         }
         const float pall = (pw[0] + pw[1]) + (pw[2] + pw[3]);
         float run = 0.f;
 #pragma unroll
         for (int k = 0; k < kTmaWarps; ++k) {
-            reinterpret_cast<float *>(c.sm + state_off(k, nc))[2 * (q * 32 + lane)] = pall + S2 * run;
+            reinterpret_cast<float *>(c.sm + ring_off(k))[q * 32 + lane] = pall + S2 * run;
             run += rr[k];
         }
     }
@@ -472,8 +533,11 @@ __device__ __forceinline__ void tma_body(const TmaParams &P, Ctx &c) {
     __syncthreads();
 
     // ---- finishing pass: out = lambda_out (partial + C - Q[c1] - Q[c2]),
-    // staged in swizzled boxes (the ring, 2 KB each) and stored by TMA
-    const unsigned char *qb = c.lb;
+    // staged in swizzled boxes (the rest of the ring, 2 KB each) and stored
+    // by TMA
+    const unsigned char *qb = ring + 4 * lane;
+    const int qbytes = (nc * 128 + 1023) & ~1023;
+    const int nbuf = (kRingBytes - qbytes) / 2048;
     float cur[16], nxt[16];
     auto load_box = [&](int m, float *r) {
         if (m < 16) {
@@ -490,19 +554,26 @@ __device__ __forceinline__ void tma_body(const TmaParams &P, Ctx &c) {
     }
     for (int m = 0; m < nb; ++m) {
         if (m + 1 < nb) load_box(m + 1, nxt);
-        const int h0 = kTmaBox * (c.b0 + m);
+        const TmaFinRec *fr = P.rfin + (size_t)kTmaBox / 2 * (c.b0 + m);
         float o[16];
+        TmaFinRec fnx = ldg_fin(fr);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const TmaHand r = P.rec[h0 + i];
-            float q = *reinterpret_cast<const float *>(qb + r.oa);
-            if (K2 == 2) q += *reinterpret_cast<const float *>(qb + r.ob);
-            o[i] = r.lam_out * ((cur[i] + Cw) - q);
+        for (int i = 0; i < 16; i += 2) {
+            const TmaFinRec r = fnx;
+            if (i + 2 < 16) fnx = ldg_fin(fr + i / 2 + 1);
+            float q1 = *reinterpret_cast<const float *>(qb + r.oa1);
+            float q2 = *reinterpret_cast<const float *>(qb + r.oa2);
+            if (K2 == 2) {
+                q1 += *reinterpret_cast<const float *>(qb + r.ob1);
+                q2 += *reinterpret_cast<const float *>(qb + r.ob2);
+            }
+            o[i] = r.lout1 * ((cur[i] + Cw) - q1);
+            o[i + 1] = r.lout2 * ((cur[i + 1] + Cw) - q2);
         }
-        const int ob = m % 6;
-        unsigned char *buf = ring + ob * 2048;
-        if (m >= 6) {
-            if (lane == 0) bulk_wait_read<5>();
+        const int ob = m % nbuf;
+        unsigned char *buf = ring + qbytes + ob * 2048;
+        if (m >= nbuf) {
+            if (lane == 0) bulk_wait_read_n(nbuf - 1);
             __syncwarp();
         }
 #pragma unroll
@@ -525,7 +596,7 @@ __device__ __forceinline__ void tma_body(const TmaParams &P, Ctx &c) {
 }
 
 template <int K2>
-__global__ void __launch_bounds__(128, 2) tma_scan_kernel(const __grid_constant__ TmaParams P) {
+__global__ void __launch_bounds__(128, 2) tma_scan_kernel(const __grid_constant__ TmaArgs P) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // the swizzled boxes need 1 KB alignment (one KB of slack is allocated)
     unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -542,14 +613,13 @@ __global__ void __launch_bounds__(128, 2) tma_scan_kernel(const __grid_constant_
     c.b0 = P.bchunk[c.warp];
     c.nb = P.bchunk[c.warp + 1] - c.b0;
     c.ok = true;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + hdr_off(P.nc, P.extra));
     if (c.warp == 0) tm_alloc(smem_u32(tslot), kTmemCols);
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
     const uint32_t tbase = *tslot;
     c.tmem = tbase + ((uint32_t)(32 * c.warp) << 16);
-    c.lb = sm + state_off(c.warp, P.nc) + 8 * c.lane;
     const int kind = (c.rf >= 0 ? kKindF : 0) | (c.rs >= 0 ? kKindS : 0);
     if (kind == kKindFS) tma_body<kKindFS, K2>(P, c);
     else if (kind == kKindF) tma_body<kKindF, K2>(P, c);
@@ -599,85 +669,111 @@ __device__ unsigned int g_tma_err;
 
 }  // namespace
 
-static size_t tma_smem_bytes(int nc, int extra) { return extra_off(kTmaWarps, nc, extra) + 1024; }
+static size_t tma_smem_bytes(int nc, int extra) { return hdr_off(nc, extra) + kHdrBytes + 1024; }
 
+// Chunks, records and eligibility of one direction; fills p.a (but the
+// tensor maps, pointers and batch) and p.host.  Empty string on success.
 static std::string tma_prepare(const HostGame &h, const double *lam_in, const double *lam_out, TmaParams &p) {
+    TmaArgs &A = p.a;
     if (h.k != 1 && h.k != 2) return "cards per hand";
-    if (h.hs > kTmaMaxHands) return "too many hands for the parameter block";
     const int nc = h.ncards + 1;
     if (nc > 64) return "too many cards";
     const int H = h.H, hs = h.hs;
     const int nbox = (hs + kTmaBox - 1) / kTmaBox;
-    if (nbox * kTmaBox > kTmaMaxHands) return "too many hands for the parameter block";
     // tie groups: at most 4 hands (partners within 3 positions)
     for (int i = 0; i < H; ++i)
         if (h.group_hi[i] - h.group_lo[i] > 3) return "tie group longer than 4 hands";
     // chunk boundaries at box boundaries that cut no tie group, as close to
     // an even split as possible
     auto clean = [&](int bx) { return bx <= 0 || bx >= nbox || 16 * bx >= H || h.group_lo[16 * bx] == 16 * bx; };
-    p.bchunk[0] = 0;
-    p.bchunk[kTmaWarps] = nbox;
+    A.bchunk[0] = 0;
+    A.bchunk[kTmaWarps] = nbox;
     for (int k = 1; k < kTmaWarps; ++k) {
         const int ideal = (int)((long long)nbox * k / kTmaWarps);
         int best = -1;
         for (int d = 0; d <= 4 && best < 0; ++d) {
             for (int s : {ideal - d, ideal + d})
-                if (best < 0 && s >= p.bchunk[k - 1] && s <= nbox && clean(s)) best = s;
+                if (best < 0 && s >= A.bchunk[k - 1] && s <= nbox && clean(s)) best = s;
         }
         if (best < 0) return "no chunk boundary free of tie groups";
-        p.bchunk[k] = best;
+        A.bchunk[k] = best;
     }
     int extra = 0;
     for (int k = 0; k < kTmaWarps; ++k) {
-        const int n = p.bchunk[k + 1] - p.bchunk[k];
+        const int n = A.bchunk[k + 1] - A.bchunk[k];
         if (n < 0) return "chunk order";
         extra = std::max(extra, n - 16);
     }
     if (extra > kTmaMaxExtra) return "chunk longer than tensor memory and its shared-memory overflow";
-    p.H = H;
-    p.hs = hs;
-    p.nc = nc;
-    p.k = h.k;
-    p.nbox = nbox;
-    p.extra = extra;
-    std::memset(p.pflag, 0, sizeof(p.pflag));
-    std::memset(p.rec, 0, sizeof(p.rec));
+    A.H = H;
+    A.hs = hs;
+    A.nc = nc;
+    A.k = h.k;
+    A.nbox = nbox;
+    A.extra = extra;
+    // records: scan blocks, then finishing records
+    const size_t scan_bytes = (size_t)nbox * kScanBlock, fin_bytes = (size_t)nbox * 8 * sizeof(TmaFinRec);
+    p.host.assign(scan_bytes + fin_bytes, 0);
     auto card = [&](int hand, int j) { return h.hand_slots[2 * hand + j]; };
-    for (int i = 0; i < nbox * kTmaBox; ++i) {
-        TmaHand &r = p.rec[i];
-        if (i < H) {
-            r.oa = (uint32_t)card(i, 0) * 256u;
-            r.ob = (uint32_t)(h.k == 2 ? card(i, 1) : h.ncards) * 256u;
-            r.lam_in = (float)lam_in[i];
-            r.lam_out = (float)lam_out[i];
-        } else {
-            // padding: zero weights, the spare card row
-            r.oa = r.ob = (uint32_t)h.ncards * 256u;
-        }
-    }
+    auto off = [&](int hand, int j) -> uint32_t {
+        // padding hands use the spare card row (their weights are zero)
+        if (hand >= H || j >= h.k) return (uint32_t)h.ncards * 128u;
+        return (uint32_t)card(hand, j) * 128u;
+    };
     auto share = [&](int x, int y) {   // any card of hand y in hand x
         for (int j = 0; j < h.k; ++j)
             for (int l = 0; l < h.k; ++l)
                 if (card(x, j) == card(y, l)) return true;
         return false;
     };
-    for (int i = 0; i + 1 < H; i += 2) {
-        uint32_t f = 0;
-        for (int j = 0; j < h.k; ++j)
-            for (int l = 0; l < h.k; ++l)
-                if (card(i + 1, j) == card(i, l)) f |= 1u << j;
-        p.pflag[i >> 1] |= f;
-    }
-    for (int i = 0; i < H; ++i) {
-        for (int d = 1; d <= 3; ++d) {
-            const int q = i - d;
-            if (q < h.group_lo[i]) break;
-            if (share(i, q)) continue;
-            p.pflag[i >> 1] |= 1u << ((i & 1) ? 4 + d : 1 + d);
+    for (int bx = 0; bx < nbox; ++bx) {
+        unsigned char *blk = p.host.data() + (size_t)bx * kScanBlock;
+        TmaFinRec *fin = reinterpret_cast<TmaFinRec *>(p.host.data() + scan_bytes) + 8 * bx;
+        uint32_t tw[2] = {0u, 0u};
+        for (int k = 0; k < 8; ++k) {
+            const int i = 16 * bx + 2 * k;
+            TmaScanRec r{};
+            r.oa1 = off(i, 0);
+            r.ob1 = off(i, 1);
+            r.oa2 = off(i + 1, 0);
+            r.ob2 = off(i + 1, 1);
+            r.lin1 = i < H ? (float)lam_in[i] : 0.f;
+            r.lin2 = i + 1 < H ? (float)lam_in[i + 1] : 0.f;
+            if (i + 1 < H)
+                for (int l = 0; l < h.k; ++l) {
+                    if (card(i + 1, 0) == card(i, l)) r.ma = 1.f;
+                    if (h.k == 2 && card(i + 1, 1) == card(i, l)) r.mb = 1.f;
+                }
+            std::memcpy(blk + 32 * k, &r, sizeof(r));
+            TmaFinRec f{};
+            f.oa1 = r.oa1;
+            f.ob1 = r.ob1;
+            f.oa2 = r.oa2;
+            f.ob2 = r.ob2;
+            f.lout1 = i < H ? (float)lam_out[i] : 0.f;
+            f.lout2 = i + 1 < H ? (float)lam_out[i + 1] : 0.f;
+            fin[k] = f;
+            uint32_t bits = 0;
+            for (int e = 0; e < 2; ++e) {
+                const int hi = i + e;
+                if (hi >= H) continue;
+                for (int d = 1; d <= 3; ++d) {
+                    const int q = hi - d;
+                    if (q < h.group_lo[hi]) break;
+                    if (share(hi, q)) continue;
+                    bits |= 1u << (e ? 4 + d : 1 + d);
+                }
+            }
+            tw[k / 4] |= bits << (8 * (k & 3));
         }
+        std::memcpy(blk + 256, tw, sizeof(tw));
     }
     return "";
 }
+
+}  // namespace kps
+
+namespace kps {
 
 TmaParams *tma_create(const HostGame &h, const double *lam_in, const double *lam_out, int n_out, int n_in,
                       const int *fcol, const int *scol, const float *fcoef, const float *scoef,
@@ -687,49 +783,74 @@ TmaParams *tma_create(const HostGame &h, const double *lam_in, const double *lam
         *why = "host allocation";
         return nullptr;
     }
-    std::string w = tma_prepare(h, lam_in, lam_out, *p);
+    std::string w;
+    try {
+        w = tma_prepare(h, lam_in, lam_out, *p);
+    } catch (const std::bad_alloc &) {
+        w = "host allocation";
+    }
     for (int r = 0; r < n_out && w.empty(); ++r)
         if (hfcol[r] < 0 && hscol[r] < 0) w = "an output sequence without terminals";
-    if (w.empty() && std::max<size_t>(tma_smem_bytes(p->nc, p->extra), 80 * 1024) > (size_t)max_dyn_smem())
+    if (w.empty() && std::max<size_t>(tma_smem_bytes(p->a.nc, p->a.extra), 80 * 1024) > (size_t)max_dyn_smem())
         w = "shared memory";
     if (!w.empty()) {
         delete p;
         *why = w;
         return nullptr;
     }
-    p->n_out = n_out;
-    p->n_in = n_in;
-    p->fcol = fcol;
-    p->scol = scol;
-    p->fcoef = fcoef;
-    p->scoef = scoef;
-    p->err = nullptr;
+    p->a.n_out = n_out;
+    p->a.n_in = n_in;
+    p->a.fcol = fcol;
+    p->a.scol = scol;
+    p->a.fcoef = fcoef;
+    p->a.scoef = scoef;
+    p->a.err = nullptr;
     return p;
 }
 
-void tma_destroy(TmaParams *p) { delete p; }
+void tma_destroy(TmaParams *p) {
+    if (!p) return;
+    if (p->dev) cudaFree(p->dev);
+    delete p;
+}
 
 cudaError_t launch_tma_scan(TmaParams *pp, const float *vin, float *vout, int batch, cudaStream_t stream) {
     TmaParams &p = *pp;
-    p.batch = batch;
-    p.nbb = (batch + 31) / 32;
-    cudaError_t e = encode3(&p.tin, vin, p.H, p.n_in, batch, p.hs);
-    if (e == cudaSuccess) e = encode3(&p.tout, vout, p.hs, p.n_out, batch, p.hs);
-    if (e != cudaSuccess) return e;
-    if (!p.err) {
-        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p.err), g_tma_err);
+    TmaArgs &A = p.a;
+    cudaError_t e;
+    if (!p.dev) {
+        // the record tables go to the device on the first product
+        e = cudaMalloc(&p.dev, p.host.size());
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(p.dev, p.host.data(), p.host.size(), cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) {
+            cudaFree(p.dev);
+            p.dev = nullptr;
+            return e;
+        }
+        A.rscan = static_cast<const unsigned char *>(p.dev);
+        A.rfin = reinterpret_cast<const TmaFinRec *>(static_cast<const unsigned char *>(p.dev) +
+                                                     (size_t)A.nbox * kScanBlock);
+        cudaGetDevice(&p.device);
+        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&A.err), g_tma_err);
         if (e != cudaSuccess) return e;
     }
+    A.batch = batch;
+    A.nbb = (batch + 31) / 32;
+    e = encode3(&A.tin, vin, A.H, A.n_in, batch, A.hs);
+    if (e == cudaSuccess) e = encode3(&A.tout, vout, A.hs, A.n_out, batch, A.hs);
+    if (e != cudaSuccess) return e;
     // at least 80 KB: never more than two CTAs per SM, so that their tensor
     // memory (256 columns each) always fits
-    const size_t smem = std::max<size_t>(tma_smem_bytes(p.nc, p.extra), 80 * 1024);
-    const long long blocks = (long long)p.n_out * p.nbb;
+    const size_t smem = std::max<size_t>(tma_smem_bytes(A.nc, A.extra), 80 * 1024);
+    const long long blocks = (long long)A.n_out * A.nbb;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    auto fn = p.k == 1 ? tma_scan_kernel<1> : tma_scan_kernel<2>;
+    auto fn = A.k == 1 ? tma_scan_kernel<1> : tma_scan_kernel<2>;
     e = ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem);
     if (e != cudaSuccess) return e;
-    fn<<<(unsigned)blocks, 32 * kTmaWarps, smem, stream>>>(p);
+    fn<<<(unsigned)blocks, 32 * kTmaWarps, smem, stream>>>(A);
     return cudaGetLastError();
 }
 
