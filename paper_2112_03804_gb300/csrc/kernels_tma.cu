@@ -264,8 +264,9 @@ struct Ctx {
     bool ok;                   // no wait gave up
 };
 
+// Scan and combination of one column kind; returns this warp's C.
 template <int KIND, int K2>
-__device__ __forceinline__ void tma_body(const TmaArgs &P, Ctx &c) {
+__device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
     constexpr bool HF = (KIND & kKindF) != 0, HS = (KIND & kKindS) != 0, FS = KIND == kKindFS;
     constexpr int NS = FS ? 3 : 6;                    // ring slots
     constexpr int SLOT = FS ? 4096 : 2048;            // bytes per slot
@@ -402,35 +403,12 @@ __device__ __forceinline__ void tma_body(const TmaArgs &P, Ctx &c) {
             if (HS) {
                 // t = 2 Lo_ord - TB (b units); partial = w + S t, the w only
                 // for two-card hands (see K_F)
-                float t1 = 2.f * (G - (sa1.x + sb1.x));
+                const float t1 = 2.f * (G - (sa1.x + sb1.x));
                 const float g1 = G + b1;
-                float t2 = 2.f * (g1 - (sa2.x + sb2.x));
+                const float t2 = 2.f * (g1 - (sa2.x + sb2.x));
                 G = g1 + b2;
-                const uint32_t tb = ((i / 2 < 4 ? tw0 : tw1) >> (8 * ((i / 2) & 3))) & 0xfcu;
-                if (tb) {
-                    // tie corrections: TB for each hand, TA into the
-                    // earlier partner's partial result
-                    auto bat = [&](int j) { return j >= 0 ? bv[j] : (j == -1 ? bq1 : j == -2 ? bq2 : bq3); };
-                    auto pat = [&](int j) -> float & { return j >= 0 ? p[j] : pp[16 + j]; };
-#pragma unroll
-                    for (int d = 1; d <= 3; ++d)
-                        if (tb & (1u << (1 + d))) t1 -= bat(i - d);
-#pragma unroll
-                    for (int d = 2; d <= 3; ++d)
-                        if (tb & (1u << (4 + d))) t2 -= bat(i + 1 - d);
-                    if (tb & (1u << 5)) t2 -= b1;
-                    p[i] = (K2 == 2 ? w1 : 0.f) + S * t1;
-                    p[i + 1] = (K2 == 2 ? w2 : 0.f) + S * t2;
-#pragma unroll
-                    for (int d = 1; d <= 3; ++d)
-                        if (tb & (1u << (1 + d))) pat(i - d) += S * b1;
-#pragma unroll
-                    for (int d = 1; d <= 3; ++d)
-                        if (tb & (1u << (4 + d))) pat(i + 1 - d) += S * b2;
-                } else {
-                    p[i] = fmaf(S, t1, K2 == 2 ? w1 : 0.f);
-                    p[i + 1] = fmaf(S, t2, K2 == 2 ? w2 : 0.f);
-                }
+                p[i] = fmaf(S, t1, K2 == 2 ? w1 : 0.f);
+                p[i + 1] = fmaf(S, t2, K2 == 2 ? w2 : 0.f);
                 if (!HF && K2 == 2) {
                     // showdown only: w = -S b
                     p[i] = fmaf(-S, b1, p[i]);
@@ -452,6 +430,33 @@ __device__ __forceinline__ void tma_body(const TmaArgs &P, Ctx &c) {
                 if (K2 == 2) *reinterpret_cast<float *>(B1) = sb1.x + d1;
                 *reinterpret_cast<float *>(A2) = sa2.x + d2;
                 if (K2 == 2) *reinterpret_cast<float *>(B2) = sb2.x + d2;
+            }
+        }
+        // tie corrections of the box (partial = w + S (2 Lo_ord - TB + TA)):
+        // TB leaves each tied hand's partial, TA enters the earlier
+        // partner's; partners before the box are the previous box's last
+        // three hands (their partials are stored one box late)
+        if (HS && (tw0 | tw1)) {
+            auto bat = [&](int j) { return j >= 0 ? bv[j] : (j == -1 ? bq1 : j == -2 ? bq2 : bq3); };
+            auto pat = [&](int j) -> float & { return j >= 0 ? p[j] : pp[16 + j]; };
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t tb = ((k < 4 ? tw0 : tw1) >> (8 * (k & 3))) & 0xfcu;
+                if (tb) {
+                    const int i = 2 * k;
+#pragma unroll
+                    for (int d = 1; d <= 3; ++d)
+                        if (tb & (1u << (1 + d))) {
+                            p[i] = fmaf(-S, bat(i - d), p[i]);
+                            pat(i - d) = fmaf(S, bv[i], pat(i - d));
+                        }
+#pragma unroll
+                    for (int d = 1; d <= 3; ++d)
+                        if (tb & (1u << (4 + d))) {
+                            p[i + 1] = fmaf(-S, bat(i + 1 - d), p[i + 1]);
+                            pat(i + 1 - d) = fmaf(S, bv[i + 1], pat(i + 1 - d));
+                        }
+                }
             }
         }
         // every lane has used the slot's values: refill it
@@ -532,9 +537,17 @@ __device__ __forceinline__ void tma_body(const TmaArgs &P, Ctx &c) {
     }
     __syncthreads();
 
-    // ---- finishing pass: out = lambda_out (partial + C - Q[c1] - Q[c2]),
-    // staged in swizzled boxes (the rest of the ring, 2 KB each) and stored
-    // by TMA
+    return Cw;
+}
+
+// Finishing pass (the same for every column kind): out = lambda_out
+// (partial + C - Q[c1] - Q[c2]), staged in swizzled boxes (the rest of the
+// ring, 2 KB each) and stored by TMA.
+template <int K2>
+__device__ __forceinline__ void tma_finish(const TmaArgs &P, const Ctx &c, float Cw) {
+    const int lane = c.lane, nc = P.nc, nb = c.nb, z0 = 32 * c.bb;
+    unsigned char *ring = c.sm + ring_off(c.warp);
+    const float *xpart = reinterpret_cast<const float *>(c.sm + extra_off(c.warp, nc, P.extra));
     const unsigned char *qb = ring + 4 * lane;
     const int qbytes = (nc * 128 + 1023) & ~1023;
     const int nbuf = (kRingBytes - qbytes) / 2048;
@@ -621,9 +634,11 @@ __global__ void __launch_bounds__(128, 2) tma_scan_kernel(const __grid_constant_
     const uint32_t tbase = *tslot;
     c.tmem = tbase + ((uint32_t)(32 * c.warp) << 16);
     const int kind = (c.rf >= 0 ? kKindF : 0) | (c.rs >= 0 ? kKindS : 0);
-    if (kind == kKindFS) tma_body<kKindFS, K2>(P, c);
-    else if (kind == kKindF) tma_body<kKindF, K2>(P, c);
-    else tma_body<kKindS, K2>(P, c);
+    float Cw;
+    if (kind == kKindFS) Cw = tma_scan<kKindFS, K2>(P, c);
+    else if (kind == kKindF) Cw = tma_scan<kKindF, K2>(P, c);
+    else Cw = tma_scan<kKindS, K2>(P, c);
+    tma_finish<K2>(P, c, Cw);
     if (!c.ok && c.lane == 0) atomicExch(P.err, 1u);
     tm_fence_before();
     __syncthreads();
