@@ -1106,9 +1106,26 @@ double orc_rmplus(const orc_game *g, int iters, const double *beh1_0, const doub
     return orc_rmplus_warm(g, iters, beh1_0, beh2_0, 0.0, 0, avg_beh1, avg_beh2, trace, trace_every);
 }
 
+static double rmplus_loop(const orc_game *g, int iters, const double *beh1_0, const double *beh2_0,
+                          double kappa, int t0, double eps, double *avg_beh1, double *avg_beh2,
+                          double *trace, int trace_every);
+
 double orc_rmplus_warm(const orc_game *g, int iters, const double *beh1_0, const double *beh2_0,
                        double kappa, int t0, double *avg_beh1, double *avg_beh2, double *trace,
                        int trace_every)
+{
+    return rmplus_loop(g, iters, beh1_0, beh2_0, kappa, t0, ORC_REGRET_EPS, avg_beh1, avg_beh2, trace,
+                       trace_every);
+}
+
+double orc_rmplus_eps(const orc_game *g, int iters, double eps, double *avg_beh1, double *avg_beh2)
+{
+    return rmplus_loop(g, iters, NULL, NULL, 0.0, 0, eps, avg_beh1, avg_beh2, NULL, 0);
+}
+
+static double rmplus_loop(const orc_game *g, int iters, const double *beh1_0, const double *beh2_0,
+                          double kappa, int t0, double eps, double *avg_beh1, double *avg_beh2,
+                          double *trace, int trace_every)
 {
     int H = g->H, n1 = g->n[0], n2 = g->n[1];
     size_t N1 = (size_t)n1 * H, N2 = (size_t)n2 * H;
@@ -1122,7 +1139,7 @@ double orc_rmplus_warm(const orc_game *g, int iters, const double *beh1_0, const
     if (beh2_0) memcpy(b2, beh2_0, N2 * sizeof(double)); else uniform_beh(g, 1, b2);
     orc_seqform(g, 0, b1, x);
     orc_seqform(g, 1, b2, y);
-    const double th1 = orc_regret_floor(g, 0, ORC_REGRET_EPS), th2 = orc_regret_floor(g, 1, ORC_REGRET_EPS);
+    const double th1 = orc_regret_floor(g, 0, eps), th2 = orc_regret_floor(g, 1, eps);
     /* warm start: regrets proportional to the initial strategy, which then
      * counts as played for iterations 1..t0 in the linear average */
     const double r1 = kappa * orc_regret_floor(g, 0, 1.0), r2 = kappa * orc_regret_floor(g, 1, 1.0);

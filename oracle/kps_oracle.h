@@ -151,6 +151,11 @@ double orc_rmplus_warm(const orc_game *g, int iters, const double *beh1_0, const
                        double kappa, int t0, double *avg_beh1, double *avg_beh2, double *trace,
                        int trace_every);
 
+/* orc_rmplus from uniform strategies with the noise floor eps * V_p of
+ * regret matching given explicitly (eps = 0: textbook RM+, uniform only at
+ * an exact zero regret sum). */
+double orc_rmplus_eps(const orc_game *g, int iters, double eps, double *avg_beh1, double *avg_beh2);
+
 /* Discounted CFR (the solver the paper runs, Sec. 5; Brown & Sandholm's
  * DCFR): alternating updates from uniform strategies; on iteration t the
  * instantaneous regret q - v is added and a cumulative regret is multiplied

@@ -67,6 +67,8 @@ def lib():
         L.orc_regret_floor.restype = C.c_double
         L.orc_rmplus_warm.argtypes = [P, C.c_int, P, P, C.c_double, C.c_int, P, P, P, C.c_int]
         L.orc_rmplus_warm.restype = C.c_double
+        L.orc_rmplus_eps.argtypes = [P, C.c_int, C.c_double, P, P]
+        L.orc_rmplus_eps.restype = C.c_double
         L.orc_dcfr.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, P, P, P, C.c_int]
         L.orc_dcfr.restype = C.c_double
         L.orc_beta.argtypes = [P]
@@ -256,6 +258,14 @@ class OracleGame:
         e = lib().orc_rmplus_warm(self._g, iters, _p(b1), _p(b2), kappa, t0, _p(avg1), _p(avg2), _p(trace),
                                   trace_every)
         return e, avg1, avg2, trace[:iters]
+
+    def rmplus_eps(self, iters: int, eps: float):
+        """RM+ from uniform strategies with the regret-matching noise floor
+        eps * V_p (eps = 0: textbook RM+); returns (expl, avg1, avg2)."""
+        avg1 = np.zeros((self.n1, self.H))
+        avg2 = np.zeros((self.n2, self.H))
+        e = lib().orc_rmplus_eps(self._g, iters, float(eps), _p(avg1), _p(avg2))
+        return e, avg1, avg2
 
     def dcfr(self, iters: int, alpha: float = 1.5, beta: float = 0.0, gamma: float = 2.0, trace_every: int = 0):
         """Discounted CFR from uniform strategies (see orc_dcfr)."""
