@@ -304,8 +304,39 @@ kps_status kps_solver_warm_start(kps_solver *solver, const float *beh1, const fl
  * reset / warm start.  Errors: KPS_EINVAL. */
 kps_status kps_solver_set_method(kps_solver *solver, int32_t method, double alpha, double beta, double gamma);
 /* Runs `iters` iterations as one CUDA graph (captured on first use of each
- * count), asynchronous on `stream`. */
+ * count), asynchronous on `stream`, then queues a check of the state those
+ * iterations leave: every regret, weighted strategy sum and current
+ * strategy entry of both players must be finite.  The check's result is read back asynchronously; a call
+ * finds it once it has landed (KPS_ENUMERIC from that call on, and from
+ * every later step, until kps_solver_reset, kps_solver_warm_start or
+ * kps_solver_load), and kps_solver_status waits for it.  A NaN or an
+ * infinity in the state (a non-finite input strategy, belief or payoff)
+ * would otherwise be carried into the averages and the exploitability. */
 kps_status kps_solver_step(kps_solver *solver, int32_t iters, void *stream);
+/* Waits for the last step's non-finite check: KPS_OK, or KPS_ENUMERIC when
+ * a regret, strategy-sum or strategy entry is NaN or infinite. */
+kps_status kps_solver_status(kps_solver *solver);
+
+/* ---- Checkpoint and resume ----------------------------------------------
+ * A solver's whole iteration state goes to / comes from a caller-owned host
+ * buffer of kps_solver_state_bytes bytes: a header (format version, storage
+ * type, method and DCFR parameters, warm-start parameters, iteration count,
+ * weight sum, a signature of the batch's games) followed, per player, by
+ * the regrets and the weighted strategy sums (FP32, FP64 for KPS_F64), the
+ * current sequence-form strategy (storage type) and the initial behavioural
+ * strategy (FP32).  Iterations run after kps_solver_load are the ones an
+ * uninterrupted solver would have run, bit for bit (Sec. 5's solver is a
+ * long iterative run; this is how it survives a restart).
+ *   kps_solver_save synchronises `stream` and fills `host`;
+ *   kps_solver_load needs a solver created on a batch of the same games
+ *   (same hands and trees) with the same storage type, synchronises
+ *   `stream`, restores the method saved (kps_solver_set_method) and clears
+ *   the non-finite report.
+ * Errors: KPS_EINVAL (NULL, buffer too small, not a checkpoint, another
+ * storage type or batch), KPS_ECUDA. */
+kps_status kps_solver_state_bytes(const kps_solver *solver, int64_t *bytes);
+kps_status kps_solver_save(kps_solver *solver, void *host, int64_t bytes, void *stream);
+kps_status kps_solver_load(kps_solver *solver, const void *host, int64_t bytes, void *stream);
 /* Iterations run since the last reset (host count). */
 kps_status kps_solver_iterations(const kps_solver *solver, int64_t *iters);
 /* FP64 average strategies (device, batch player layouts; either may be
@@ -394,6 +425,17 @@ kps_status kps_mlp_gradients(kps_mlp *mlp, const float *X, int32_t rows, const i
                              const float *w, float wsum, float *loss, void *stream);
 /* One Adam step with the last gradients (FP32 master weights, then BF16). */
 kps_status kps_mlp_adam(kps_mlp *mlp, float lr, float beta1, float beta2, float eps, void *stream);
+/* Checkpoint of a network in a caller-owned host buffer of
+ * kps_mlp_state_bytes bytes: a header (format version, layer sizes, Adam's
+ * step count) then the FP32 parameters and Adam's first and second moments,
+ * so that training resumed after kps_mlp_load takes the same steps, bit for
+ * bit, as training that never stopped.  Both calls synchronise the device.
+ * kps_mlp_load needs a network of the same layer sizes and rebuilds the
+ * BF16 weight copy.  Errors: KPS_EINVAL (NULL, buffer too small, not a
+ * checkpoint, other layer sizes), KPS_ECUDA. */
+kps_status kps_mlp_state_bytes(const kps_mlp *mlp, int64_t *bytes);
+kps_status kps_mlp_save(const kps_mlp *mlp, void *host, int64_t bytes);
+kps_status kps_mlp_load(kps_mlp *mlp, const void *host, int64_t bytes);
 
 /* A * y for BF16 or FP16 vectors without any device allocation.  The paper
  * has no counterpart: this is a service for callers that must not allocate

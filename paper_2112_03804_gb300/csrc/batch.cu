@@ -411,6 +411,10 @@ kps_status kps_batch_shape_set(kps_batch *b, kps_dtype dt, const kps_batch_shape
     } else if (nw < tmem_min_warps(b)) {
         return fail(KPS_ENOTSUP, "warp count leaves a hand chunk too long for tensor memory");
     }
+    // a shape the multi-game kernel cannot launch (shared memory, registers)
+    const int per = dt == KPS_F64 ? kps::vec_multi_ctas_per_sm(storage_of(dt), b->k, maxnc, nw)
+                                  : kps::tmem_multi_ctas_per_sm(storage_of(dt), b->k, maxnc, nw);
+    if (per < 1) return fail(KPS_ENOTSUP, "warp count needs too much shared memory or too many registers");
     BatchShape s = cur;
     s.nw = nw;
     s.grid = shape->grid;

@@ -659,7 +659,8 @@ int ctas_t(size_t smem, int nw) {
     // this kernel at every size, while two 4-warp CTAs do run side by side
     // (measured), so it is not used.
     auto fn = tmem_multi_kernel<S, K2, SP>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    // raise the kernel's limit if needed (never lower it: another launch may need more)
+    if (ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem) != cudaSuccess) return 0;
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 0;
     int dev = 0, sm_smem = 0, sm_regs = 0, sm_threads = 0;

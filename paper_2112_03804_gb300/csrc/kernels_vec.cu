@@ -576,7 +576,8 @@ cudaError_t launch_multi_t(const MultiParams &m, size_t smem, int grid, cudaStre
 template <typename S, int K2>
 int ctas_t(size_t smem, int nw) {
     auto fn = vec_multi_kernel<S, K2>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    // raise the kernel's limit if needed (never lower it: another launch may need more)
+    if (ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * nw, smem) != cudaSuccess) return 0;
     return n;

@@ -367,6 +367,69 @@ kps_status kps_mlp_set(kps_mlp *m, const float *host) {
     return KPS_OK;
 }
 
+// Checkpoint of a network (kps_mlp_save / kps_mlp_load): this header, then
+// the FP32 parameters and Adam's first and second moments.
+struct MlpCkpt {
+    char magic[8];
+    int32_t version, din, width, dout;
+    int64_t step, n;
+};
+static const char kMlpMagic[8] = {'K', 'P', 'S', 'M', 'L', 'P', '0', '1'};
+
+kps_status kps_mlp_state_bytes(const kps_mlp *m, int64_t *bytes) {
+    if (!m || !bytes) return fail(KPS_EINVAL, "NULL argument");
+    *bytes = (int64_t)sizeof(MlpCkpt) + 3 * 4 * m->off[6];
+    return KPS_OK;
+}
+
+kps_status kps_mlp_save(const kps_mlp *m, void *host, int64_t bytes) {
+    if (!m || !host) return fail(KPS_EINVAL, "NULL argument");
+    const long long n = m->off[6];
+    if (bytes < (int64_t)sizeof(MlpCkpt) + 12 * n) return fail(KPS_EINVAL, "buffer smaller than kps_mlp_state_bytes");
+    MlpCkpt h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kMlpMagic, 8);
+    h.version = 1;
+    h.din = m->din;
+    h.width = m->width;
+    h.dout = m->dout;
+    h.step = m->step;
+    h.n = n;
+    unsigned char *dst = static_cast<unsigned char *>(host);
+    std::memcpy(dst, &h, sizeof(h));
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(dst + sizeof(h), m->p, 4 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(dst + sizeof(h) + 4 * n, m->m, 4 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(dst + sizeof(h) + 8 * n, m->v, 4 * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "saving the network");
+    return KPS_OK;
+}
+
+kps_status kps_mlp_load(kps_mlp *m, const void *host, int64_t bytes) {
+    if (!m || !host) return fail(KPS_EINVAL, "NULL argument");
+    if (bytes < (int64_t)sizeof(MlpCkpt)) return fail(KPS_EINVAL, "buffer too small for a checkpoint");
+    MlpCkpt h;
+    std::memcpy(&h, host, sizeof(h));
+    if (std::memcmp(h.magic, kMlpMagic, 8) != 0 || h.version != 1) return fail(KPS_EINVAL, "not a network checkpoint");
+    if (h.din != m->din || h.width != m->width || h.dout != m->dout || h.n != m->off[6])
+        return fail(KPS_EINVAL, "checkpoint of a network with other layer sizes");
+    const long long n = m->off[6];
+    if (bytes < (int64_t)sizeof(MlpCkpt) + 12 * n) return fail(KPS_EINVAL, "checkpoint truncated");
+    if (h.step < 0 || h.step > 0x7fffffffLL) return fail(KPS_EINVAL, "bad step count in the checkpoint");
+    const unsigned char *src = static_cast<const unsigned char *>(host) + sizeof(h);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(m->p, src, 4 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->m, src + 4 * n, 4 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->v, src + 8 * n, 4 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        to_bf16_kernel<<<(unsigned)((n + 255) / 256), 256>>>(n, m->p, m->ph);
+        e = cudaDeviceSynchronize();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "loading the network");
+    m->step = (int)h.step;
+    return KPS_OK;
+}
+
 kps_status kps_mlp_forward(kps_mlp *m, const float *X, int32_t Q, const int32_t *nact, float *P, void *stream) {
     kps_status st = check_rows(m, X, Q);
     if (st != KPS_OK) return st;

@@ -391,6 +391,12 @@ struct kps_solver {
     cudaStream_t cap = nullptr;     // capture stream
     std::map<int, cudaGraphExec_t> graphs;
     std::vector<void *> allocs;
+    // non-finite check after every kps_solver_step: device flag, its pinned
+    // host copy and the event that tells when the copy has landed
+    unsigned int *bad = nullptr;
+    unsigned int *bad_host = nullptr;
+    cudaEvent_t bad_ev = nullptr;
+    bool check_pending = false;
 };
 
 namespace {
@@ -425,14 +431,8 @@ UpdateArgs<S, C> make_args(kps_solver *s, int p) {
 // Raises a kernel's dynamic shared-memory limit once per size (never
 // inside a stream capture: the solver warms every kernel up first).
 cudaError_t smem_limit(const void *kernel, size_t smem) {
-    static std::mutex mu;
-    static std::map<const void *, size_t> done;
-    std::lock_guard<std::mutex> lock(mu);
-    size_t &have = done[kernel];
-    if (smem <= 48 * 1024 || smem <= have) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) have = smem;
-    return e;
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return kps::ensure_dyn_smem(kernel, smem);
 }
 
 template <typename S, typename C, typename K>
@@ -496,7 +496,75 @@ kps_status one_iteration(kps_solver *s, cudaStream_t st) {
     return KPS_OK;
 }
 
+// Sets *bad when a regret, a weighted strategy sum or a current strategy
+// entry of a player is not finite (NaN or infinite): a product or an update
+// has gone wrong, and the averages and exploitability carry it from then on
+// (RM+'s max(0, .) turns a NaN regret into 0, so the regrets alone can look
+// clean while the averages are not).
+template <typename S, typename C>
+__global__ void nonfinite_kernel(const C *regret, const C *xsum, const S *x, long long n, unsigned int *bad) {
+    bool ok = true;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        ok = ok && isfinite((double)regret[i]) && isfinite((double)xsum[i]) && isfinite((double)Cv<S>::ld(x + i));
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(bad, 1u);
+}
+
+template <typename S, typename C>
+cudaError_t nonfinite_t(kps_solver *s, int p, cudaStream_t st) {
+    const long long n = s->batch->off[p].back();
+    const int blocks = (int)std::min<long long>(1024, (n + 255) / 256);
+    if (blocks <= 0) return cudaSuccess;
+    nonfinite_kernel<S, C><<<blocks, 256, 0, st>>>(static_cast<const C *>(s->regret[p]),
+                                                    static_cast<const C *>(s->xsum[p]),
+                                                    static_cast<const S *>(s->x[p]), n, s->bad);
+    return cudaGetLastError();
+}
+
+// Checkpoint of a solver (kps_solver_save / kps_solver_load): this header,
+// then per player its regrets and its weighted strategy sums (compute
+// type), its current strategy (storage type) and its initial behavioural
+// strategy (FP32).
+struct SolverCkpt {
+    char magic[8];
+    int32_t version, dtype, method, has_beh;
+    double alpha, beta, gamma, kappa, w0, wsum;
+    int64_t iter, init_iter;
+    int64_t len[2];
+    int64_t ngames;
+    uint64_t signature;
+};
+constexpr char kCkptMagic[8] = {'K', 'P', 'S', 'S', 'O', 'L', 'V', '1'};
+
+// Shape signature of a batch: games, hands and sequences (FNV-1a).
+uint64_t batch_signature(const kps_batch *b) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](int64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (uint64_t)((v >> (8 * i)) & 0xff);
+            h *= 1099511628211ull;
+        }
+    };
+    mix((int64_t)b->games.size());
+    for (const kps_game *g : b->games) {
+        mix(g->host.H);
+        mix(g->host.n[0]);
+        mix(g->host.n[1]);
+        mix(g->host.nodes[0]);
+        mix(g->host.nodes[1]);
+    }
+    return h;
+}
+
+size_t ckpt_bytes(const kps_solver *s) {
+    const size_t es = elem_size(s->dt), csz = compute_size(s->dt);
+    size_t n = sizeof(SolverCkpt);
+    for (int p = 0; p < 2; ++p) n += (size_t)s->batch->off[p].back() * (2 * csz + es + 4);
+    return n;
+}
+
 void free_solver(kps_solver *s) {
+    if (s->bad_ev) cudaEventDestroy(s->bad_ev);
+    if (s->bad_host) cudaFreeHost(s->bad_host);
     for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
     if (s->dtab) cudaFree(s->dtab);
     for (void *p : s->allocs) cudaFree(p);
@@ -648,6 +716,14 @@ kps_status kps_solver_create(kps_batch *b, kps_dtype dt, kps_solver **out) {
     }
     e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) { free_solver(s); return cuda_fail(e, "capture stream"); }
+    if (!alloc(4, reinterpret_cast<void **>(&s->bad)) ||
+        cudaMallocHost(reinterpret_cast<void **>(&s->bad_host), 4) != cudaSuccess) {
+        free_solver(s);
+        return fail(KPS_ENOMEM, "non-finite flag");
+    }
+    *s->bad_host = 0;
+    e = cudaEventCreateWithFlags(&s->bad_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) { free_solver(s); return cuda_fail(e, "non-finite event"); }
     // launch tables of the products the solver uses, built before any capture
     for (kps_dtype d : {dt, KPS_F64}) {
         BatchShape sh;
@@ -685,6 +761,10 @@ kps_status kps_solver_warm_start(kps_solver *s, const float *beh1, const float *
     if (!(kappa >= 0.0) || t0 < 0) return fail(KPS_EINVAL, "kappa and t0 must be >= 0");
     cudaStream_t st = static_cast<cudaStream_t>(stream_ptr);
     const size_t es = elem_size(s->dt);
+    // a fresh start clears the non-finite report (after any check in flight)
+    if (s->check_pending) cudaEventSynchronize(s->bad_ev);
+    s->check_pending = false;
+    if (s->bad_host) *s->bad_host = 0;
     s->has_beh = beh1 ? 1 : 0;
     s->kappa = kappa;
     double w0 = 0.0;
@@ -747,6 +827,13 @@ kps_status kps_solver_step(kps_solver *s, int32_t iters, void *stream_ptr) {
     if (!s) return fail(KPS_EINVAL, "solver is NULL");
     if (iters < 0) return fail(KPS_EINVAL, "iters must be >= 0");
     if (iters == 0) return KPS_OK;
+    // the check queued by an earlier call, if its result has landed
+    if (s->check_pending && cudaEventQuery(s->bad_ev) == cudaSuccess) {
+        s->check_pending = false;
+        if (*s->bad_host) return fail(KPS_ENUMERIC, "a regret or strategy entry is not finite (NaN or infinite)");
+    } else if (!s->check_pending && *s->bad_host) {
+        return fail(KPS_ENUMERIC, "a regret or strategy entry is not finite (NaN or infinite)");
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream_ptr);
     kps_status r0 = ensure_dtab(s, s->iters_host + iters, st);
     if (r0 != KPS_OK) return r0;
@@ -772,6 +859,123 @@ kps_status kps_solver_step(kps_solver *s, int32_t iters, void *stream_ptr) {
     cudaError_t e = cudaGraphLaunch(it->second, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the iteration graph");
     s->iters_host += iters;
+    // non-finite check of the state the iterations left (read back
+    // asynchronously; reported by the next step or by kps_solver_status)
+    e = cudaMemsetAsync(s->bad, 0, 4, st);
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = KPS_DISPATCH(s->dt, nonfinite_t, s, p, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->bad_host, s->bad, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->bad_ev, st);
+    if (e != cudaSuccess) return cuda_fail(e, "non-finite check");
+    s->check_pending = true;
+    return KPS_OK;
+}
+
+kps_status kps_solver_status(kps_solver *s) {
+    if (!s) return fail(KPS_EINVAL, "solver is NULL");
+    if (s->check_pending) {
+        cudaError_t e = cudaEventSynchronize(s->bad_ev);
+        if (e != cudaSuccess) return cuda_fail(e, "waiting for the non-finite check");
+        s->check_pending = false;
+    }
+    if (*s->bad_host) return fail(KPS_ENUMERIC, "a regret or strategy entry is not finite (NaN or infinite)");
+    return KPS_OK;
+}
+
+kps_status kps_solver_state_bytes(const kps_solver *s, int64_t *bytes) {
+    if (!s || !bytes) return fail(KPS_EINVAL, "NULL argument");
+    *bytes = (int64_t)ckpt_bytes(s);
+    return KPS_OK;
+}
+
+kps_status kps_solver_save(kps_solver *s, void *host, int64_t bytes, void *stream_ptr) {
+    if (!s || !host) return fail(KPS_EINVAL, "NULL argument");
+    if (bytes < (int64_t)ckpt_bytes(s)) return fail(KPS_EINVAL, "buffer smaller than kps_solver_state_bytes");
+    cudaStream_t st = static_cast<cudaStream_t>(stream_ptr);
+    SolverCkpt h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.dtype = (int32_t)s->dt;
+    h.method = s->method;
+    h.has_beh = s->has_beh;
+    h.alpha = s->alpha;
+    h.beta = s->beta;
+    h.gamma = s->gamma;
+    h.kappa = s->kappa;
+    h.w0 = s->w0;
+    h.ngames = (int64_t)s->batch->games.size();
+    h.signature = batch_signature(s->batch);
+    long long it = 0, ii = 0;
+    double ws = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&it, s->iter, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ii, s->init_iter, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ws, s->wsum, 8, cudaMemcpyDeviceToHost, st);
+    unsigned char *dst = static_cast<unsigned char *>(host) + sizeof(SolverCkpt);
+    const size_t es = elem_size(s->dt), csz = compute_size(s->dt);
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+        const size_t len = (size_t)s->batch->off[p].back();
+        h.len[p] = (int64_t)len;
+        const void *src[4] = {s->regret[p], s->xsum[p], s->x[p], s->beh0[p]};
+        const size_t sz[4] = {len * csz, len * csz, len * es, len * 4};
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+            e = cudaMemcpyAsync(dst, src[k], sz[k], cudaMemcpyDeviceToHost, st);
+            dst += sz[k];
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "saving the solver state");
+    h.iter = it;
+    h.init_iter = ii;
+    h.wsum = ws;
+    std::memcpy(host, &h, sizeof(h));
+    return KPS_OK;
+}
+
+kps_status kps_solver_load(kps_solver *s, const void *host, int64_t bytes, void *stream_ptr) {
+    if (!s || !host) return fail(KPS_EINVAL, "NULL argument");
+    if (bytes < (int64_t)sizeof(SolverCkpt)) return fail(KPS_EINVAL, "buffer too small for a checkpoint");
+    SolverCkpt h;
+    std::memcpy(&h, host, sizeof(h));
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) return fail(KPS_EINVAL, "not a solver checkpoint");
+    if (h.dtype != (int32_t)s->dt) return fail(KPS_EINVAL, "checkpoint of a solver with another storage type");
+    if (h.ngames != (int64_t)s->batch->games.size() || h.signature != batch_signature(s->batch) ||
+        h.len[0] != s->batch->off[0].back() || h.len[1] != s->batch->off[1].back())
+        return fail(KPS_EINVAL, "checkpoint of another batch of games");
+    if (bytes < (int64_t)ckpt_bytes(s)) return fail(KPS_EINVAL, "checkpoint truncated");
+    if (h.method != 0 && h.method != 1) return fail(KPS_EINVAL, "bad method in the checkpoint");
+    if (h.iter < 0 || h.init_iter < 0) return fail(KPS_EINVAL, "bad iteration count in the checkpoint");
+    cudaStream_t st = static_cast<cudaStream_t>(stream_ptr);
+    // method and discount parameters as saved (captured graphs and the DCFR
+    // table are rebuilt for them)
+    if (h.method != s->method || (h.method == 1 && (h.alpha != s->alpha || h.beta != s->beta || h.gamma != s->gamma))) {
+        kps_status r = kps_solver_set_method(s, h.method, h.alpha, h.beta, h.gamma);
+        if (r != KPS_OK) return r;
+    }
+    cudaError_t e = cudaStreamSynchronize(st);   // work queued on the state has finished
+    const unsigned char *src = static_cast<const unsigned char *>(host) + sizeof(SolverCkpt);
+    const size_t es = elem_size(s->dt), csz = compute_size(s->dt);
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+        const size_t len = (size_t)h.len[p];
+        void *dst[4] = {s->regret[p], s->xsum[p], s->x[p], s->beh0[p]};
+        const size_t sz[4] = {len * csz, len * csz, len * es, len * 4};
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+            e = cudaMemcpyAsync(dst[k], src, sz[k], cudaMemcpyHostToDevice, st);
+            src += sz[k];
+        }
+    }
+    const long long it = h.iter, ii = h.init_iter;
+    const double ws = h.wsum;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->iter, &it, 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->init_iter, &ii, 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->wsum, &ws, 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "loading the solver state");
+    s->has_beh = h.has_beh;
+    s->kappa = h.kappa;
+    s->w0 = h.w0;
+    s->iters_host = h.iter;
+    s->check_pending = false;
+    *s->bad_host = 0;
     return KPS_OK;
 }
 

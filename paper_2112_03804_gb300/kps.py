@@ -80,13 +80,15 @@ EXPORTED = ["kps_sparsify", "kps_game_destroy", "kps_game_info", "kps_game_hands
             "kps_batch_create", "kps_batch_destroy", "kps_batch_offsets", "kps_batch_matvec_A",
             "kps_batch_matvec_AT", "kps_batch_tune", "kps_batch_shape_get", "kps_batch_shape_set", "kps_partition",
             "kps_solver_create", "kps_solver_destroy", "kps_solver_reset", "kps_solver_warm_start",
-            "kps_solver_set_method", "kps_solver_step",
+            "kps_solver_set_method", "kps_solver_step", "kps_solver_status", "kps_solver_state_bytes",
+            "kps_solver_save", "kps_solver_load",
             "kps_solver_iterations", "kps_solver_average", "kps_solver_strategy", "kps_solver_exploitability",
             "kps_solver_exploitability_estimate",
             "kps_warm_num_queries", "kps_warm_features", "kps_warm_targets", "kps_warm_scatter",
             "kps_warm_predict",
             "kps_mlp_create", "kps_mlp_destroy", "kps_mlp_num_params", "kps_mlp_get", "kps_mlp_set",
-            "kps_mlp_forward", "kps_mlp_gradients", "kps_mlp_adam",
+            "kps_mlp_forward", "kps_mlp_gradients", "kps_mlp_adam", "kps_mlp_state_bytes", "kps_mlp_save",
+            "kps_mlp_load",
             "kps_tb_create", "kps_tb_destroy", "kps_tb_sizes", "kps_tb_export", "kps_tb_matvec",
             "kps_last_error", "kps_version"]
 
@@ -125,6 +127,13 @@ def lib():
         L.kps_solver_destroy.argtypes = [P]
         L.kps_solver_reset.argtypes = [P, P, P, P]
         L.kps_solver_step.argtypes = [P, C.c_int32, P]
+        L.kps_solver_status.argtypes = [P]
+        L.kps_solver_state_bytes.argtypes = [P, C.POINTER(C.c_int64)]
+        L.kps_solver_save.argtypes = [P, P, C.c_int64, P]
+        L.kps_solver_load.argtypes = [P, P, C.c_int64, P]
+        L.kps_mlp_state_bytes.argtypes = [P, C.POINTER(C.c_int64)]
+        L.kps_mlp_save.argtypes = [P, P, C.c_int64]
+        L.kps_mlp_load.argtypes = [P, P, C.c_int64]
         L.kps_solver_iterations.argtypes = [P, C.POINTER(C.c_int64)]
         L.kps_solver_average.argtypes = [P, C.c_int32, P, P, P]
         L.kps_solver_exploitability.argtypes = [P, P, P, P, P]
@@ -500,6 +509,24 @@ class Solver:
     def exploitability(self, expl, br1=None, br2=None, stream=None):
         _check(lib().kps_solver_exploitability(self._h, _ptr(expl), _ptr(br1), _ptr(br2), _stream(stream)))
 
+    def status(self):
+        """kps_solver_status: raises KpsError(ENUMERIC) when the last step
+        left a NaN or an infinity in the regrets or strategies."""
+        _check(lib().kps_solver_status(self._h))
+
+    def save(self, stream=None) -> bytes:
+        """kps_solver_save: the solver's iteration state as bytes."""
+        n = C.c_int64()
+        _check(lib().kps_solver_state_bytes(self._h, C.byref(n)))
+        buf = (C.c_ubyte * n.value)()
+        _check(lib().kps_solver_save(self._h, C.cast(buf, C.c_void_p), n.value, _stream(stream)))
+        return bytes(buf)
+
+    def load(self, state: bytes, stream=None):
+        """kps_solver_load: resume from bytes written by save()."""
+        buf = (C.c_ubyte * len(state)).from_buffer_copy(state)
+        _check(lib().kps_solver_load(self._h, C.cast(buf, C.c_void_p), len(state), _stream(stream)))
+
 
 WARM_DIN = 1232
 WARM_DOUT = 12
@@ -575,6 +602,19 @@ class MLP:
 
     def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None):
         _check(lib().kps_mlp_adam(self._h, lr, beta1, beta2, eps, _stream(stream)))
+
+    def save(self) -> bytes:
+        """kps_mlp_save: parameters, Adam moments and step count as bytes."""
+        n = C.c_int64()
+        _check(lib().kps_mlp_state_bytes(self._h, C.byref(n)))
+        buf = (C.c_ubyte * n.value)()
+        _check(lib().kps_mlp_save(self._h, C.cast(buf, C.c_void_p), n.value))
+        return bytes(buf)
+
+    def load(self, state: bytes):
+        """kps_mlp_load: resume from bytes written by save()."""
+        buf = (C.c_ubyte * len(state)).from_buffer_copy(state)
+        _check(lib().kps_mlp_load(self._h, C.cast(buf, C.c_void_p), len(state)))
 
 
 def version() -> str:

@@ -282,3 +282,85 @@ def test_trained_network_saves_iterations():
     r = warmstart.compare(m, hb, kps.F32, 1e-3, kappa=0.02, t0=0, block=25, max_iters=2000)
     assert r["cold"]["max_expl"] < 1e-3 and r["warm"]["max_expl"] < 1e-3
     assert r["warm"]["iterations"] < r["cold"]["iterations"], r
+
+
+def test_served_predictor_matches_oracle():
+    """kps_warm_predict (the fused tensor-core predictor the solver is warm
+    started from) against oracle/mlp_oracle.forward on the same BF16
+    weights, at 2000 sampled queries of a river game and a micro game.  The
+    predictor rounds the layer-1 and layer-2 activations to BF16 (unit
+    roundoff u = 2^-8) and accumulates in FP32.  Two bounds, both derived
+    per query from the oracle's FP64 activations:
+    worst case (every rounding error at its maximum, the same sign):
+      |dA1_j| <= g1 (sum_i |X_i W1_ij| + |b1_j|),   g1 = 1232 * 2^-24
+      |dH1_j| <= |dA1_j| + u (|H1_j| + |dA1_j|)      (ReLU is 1-Lipschitz)
+      |dA2_j| <= sum_k |W2_kj| |dH1_k| + g2 sum_k (|H1_k| + |dH1_k|) |W2_kj|
+      |dH2_j| <= |dA2_j| + u (|H2_j| + |dA2_j|),     g2 = 2 * 256 * 2^-24
+      |dZ_a|  <= sum_j |W3_ja| |dH2_j| + g2 sum_j (|H2_j| + |dH2_j|) |W3_ja|
+    statistical (round-to-nearest errors independent, zero mean, variance
+    at most (u x)^2 / 3 for a rounded value x; six standard deviations):
+      var dA2_j = sum_k W2_kj^2 (u H1_k)^2 / 3,  var dH2_j = var dA2_j + (u H2_j)^2 / 3,
+      var dZ_a  = sum_j W3_ja^2 var dH2_j,        |dZ_a| <= 6 sqrt(var dZ_a) + the FP32 terms
+    and for the probabilities, with d = max over the node's actions of |dZ_a|:
+      |dP_a| <= P_a (exp(2 d) - 1) + 1e-6   (softmax; FP32 exponential).
+    Every entry must be within the worst-case bound and within the
+    statistical one (the latter is the tight check)."""
+    from paper_2112_03804_gb300 import warmstart
+    specs = [synth.river_spec(seed=31), synth.micro_spec(seed=4, ranks=4, suits=2, nboard=2)]
+    games = [kps.Game(s) for s in specs]
+    b = kps.Batch(games)
+    m = kps.MLP(seed=9)
+    p = m.get(0)
+    blocks = M.unpack(p.astype(np.float64), DIN, WIDTH, DOUT)
+    blocks[4] *= 8.0
+    blocks[5] = np.random.default_rng(2).normal(0, 1.0, size=DOUT)
+    m.set(M.pack(blocks).astype(np.float32))
+    fused = warmstart.predict(m, b)
+    nq = kps.warm_num_queries(b)
+    rng = np.random.default_rng(8)
+    idx_np = np.sort(rng.choice(nq, size=min(2000, nq), replace=False)).astype(np.int64)
+    idx = torch.from_numpy(idx_np).cuda()
+    n = len(idx_np)
+    X = torch.zeros(n, DIN, device="cuda")
+    nact = torch.zeros(n, dtype=torch.int32, device="cuda")
+    kps.warm_features(b, X, nact, qidx=idx)
+    torch.cuda.synchronize()
+    eff = _effective(m.get(0))
+    W1, b1, W2, b2, W3, b3 = M.unpack(eff, DIN, WIDTH, DOUT)
+    Xn, na = X.cpu().double().numpy(), nact.cpu().numpy()
+    P, (_, A1, H1, A2, H2, Z) = M.forward(eff, Xn, na, DIN, WIDTH, DOUT)
+    u, g1, g2 = 2.0 ** -8, 1232 * 2.0 ** -24, 2 * 256 * 2.0 ** -24
+    aW2, aW3 = np.abs(W2), np.abs(W3)
+    fp32_A1 = g1 * (np.abs(Xn) @ np.abs(W1) + np.abs(b1))
+    dH1 = fp32_A1 + u * (np.abs(H1) + fp32_A1)
+    dA2 = dH1 @ aW2 + g2 * ((np.abs(H1) + dH1) @ aW2)
+    dH2 = dA2 + u * (np.abs(H2) + dA2)
+    dZ_worst = dH2 @ aW3 + g2 * ((np.abs(H2) + dH2) @ aW3)
+    fp32_Z = g2 * ((np.abs(H2) + dH2) @ aW3) + (fp32_A1 @ aW2) @ aW3
+    var_A2 = ((u * H1) ** 2 / 3.0) @ (W2 ** 2)
+    var_H2 = var_A2 + (u * H2) ** 2 / 3.0
+    dZ_stat = 6.0 * np.sqrt(var_H2 @ (W3 ** 2)) + fp32_Z
+    mask_a = np.arange(DOUT)[None, :] < na[:, None]
+    off = [int(b.offsets(pl)[-1]) for pl in (0, 1)]
+    want = [torch.full((off[pl],), float("nan"), device="cuda") for pl in (0, 1)]
+    kps.warm_scatter(b, torch.from_numpy(P.astype(np.float32)).cuda(), want[0], want[1], qidx=idx)
+    bounds = {}
+    for name, dZ in (("worst", dZ_worst), ("stat", dZ_stat)):
+        delta = np.max(np.where(mask_a, dZ, 0.0), axis=1)
+        bound = P * np.expm1(2.0 * delta)[:, None] + 1e-6
+        tol = [torch.full((off[pl],), float("nan"), device="cuda") for pl in (0, 1)]
+        kps.warm_scatter(b, torch.from_numpy(bound.astype(np.float32)).cuda(), tol[0], tol[1], qidx=idx)
+        bounds[name] = (bound, tol)
+    torch.cuda.synchronize()
+    checked = 0
+    for pl in (0, 1):
+        w, f = want[pl].double().cpu().numpy(), fused[pl].double().cpu().numpy()
+        sel = ~np.isnan(w)
+        checked += int(sel.sum())
+        err = np.abs(f[sel] - w[sel])
+        for name in ("worst", "stat"):
+            t = bounds[name][1][pl].double().cpu().numpy()[sel]
+            assert np.all(err <= t), (name, pl, float(np.max(err - t)))
+    assert checked >= 2 * n
+    # the statistical bound is the tighter check
+    assert np.median(bounds["stat"][0][mask_a]) < 0.5 * np.median(bounds["worst"][0][mask_a])

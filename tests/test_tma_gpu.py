@@ -21,82 +21,15 @@ torch = pytest.importorskip("torch")
 
 from oracle.oracle import OracleGame
 from paper_2112_03804_gb300 import kps, synth
+from tests.dyadic import dyadic_river
 from tests.gpu_util import from_library, library_order, normwise_error, to_library
 
 pytestmark = pytest.mark.gpu
 
 
-def _hand_cards(spec):
-    """Card pairs of the canonical hand order (deck minus board, a < b)."""
-    left = [c for c in range(spec["ranks"] * spec["suits"]) if c not in set(spec["board"])]
-    return [(a, b) for i, a in enumerate(left) for b in left[i + 1:]]
-
-
-def _dyadic_beliefs(spec, seed):
-    """mu1 in {1, 2}, mu2 in {0, 1} with beta = sum over compatible pairs of
-    mu1 mu2 = 2^20, so lambda = mu / 2^10 is exact in FP32."""
-    cards = np.array(_hand_cards(spec))
-    H = len(cards)
-    ind = np.zeros((H, spec["ranks"] * spec["suits"]), dtype=np.int64)
-    ind[np.arange(H), cards[:, 0]] = 1
-    ind[np.arange(H), cards[:, 1]] = 1
-    compat = (ind @ ind.T) == 0
-    r = np.random.default_rng(seed)
-    mu1 = np.ones(H)
-    mu1[r.choice(H, 300, replace=False)] = 2.0
-    c1 = (compat * mu1[:, None]).sum(axis=0).astype(np.int64)   # per player-2 hand
-    rem = int(c1.sum()) - (1 << 20)
-    k = int(round(rem / c1.mean()))
-    out = list(r.choice(H, k, replace=False))
-    inside = np.zeros(H, dtype=bool)
-    inside[out] = True
-    for _ in range(10000):
-        diff = rem - int(c1[inside].sum())
-        if diff == 0:
-            break
-        # one swap that moves the removed sum towards the target
-        a = np.flatnonzero(inside)
-        b = np.flatnonzero(~inside)
-        gain = c1[b][None, :] - c1[a][:, None]
-        i, j = np.unravel_index(np.argmin(np.abs(gain - diff)), gain.shape)
-        if abs(int(gain[i, j]) - diff) >= abs(diff):
-            raise AssertionError("no improving swap")
-        inside[a[i]] = False
-        inside[b[j]] = True
-    assert int(c1[inside].sum()) == rem
-    mu2 = np.where(inside, 0.0, 1.0)
-    beta = float((compat * np.outer(mu1, mu2)).sum())
-    assert beta == float(1 << 20)
-    return mu1.tolist(), mu2.tolist()
-
-
-def _grouped_strengths(spec, seed):
-    """Strength order of the spec, then consecutive hands merged into tie
-    groups of 1 to 4 hands."""
-    s = np.asarray(spec["strength"])
-    order = np.lexsort((np.arange(len(s)), s))
-    r = np.random.default_rng(seed)
-    out = np.empty(len(s), dtype=np.int64)
-    pos, gid = 0, 0
-    while pos < len(s):
-        n = int(r.integers(1, 5))
-        out[order[pos:pos + n]] = gid
-        pos += n
-        gid += 1
-    return out.tolist()
-
-
-def _dyadic_river(seed, ties):
-    spec = synth.river_spec(seed=seed)
-    if ties:
-        spec["strength"] = _grouped_strengths(spec, seed + 100)
-    spec["mu1"], spec["mu2"] = _dyadic_beliefs(spec, seed + 200)
-    return spec
-
-
 @pytest.mark.parametrize("ties", [False, True], ids=["river", "river_ties4"])
 def test_river_bit_exact(ties):
-    spec = _dyadic_river(seed=2, ties=ties)
+    spec = dyadic_river(seed=2, ties=ties)
     og, g = OracleGame(spec), kps.Game(spec)
     assert og.beta == float(1 << 20)
     order = library_order(spec["strength"])
