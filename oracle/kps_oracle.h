@@ -173,6 +173,54 @@ double orc_exploitability(const orc_game *g, const double *x, const double *y,
 /* x^T A y for sequence-form vectors. */
 double orc_value(const orc_game *g, const double *x, const double *y);
 
+/* ---- Turn endgames (kps_turn_oracle.c; end of Sec. 3) --------------------
+ * The turn betting round, then at every ending that is not a fold a chance
+ * node over the river card and the river betting round.  Hands over the
+ * deck minus the board (canonical order); strength[r * H + h] is hand h's
+ * showdown strength with river card r (higher is stronger; entries for
+ * cards on the board or in the hand are not read).  Vectors are
+ * [sequence][hand]: the turn round's sequences, then one block per
+ * (ending, river card), endings in depth-first order, cards ascending. */
+typedef struct {
+    int ranks, suits, cards_per_hand;
+    int nboard;
+    int board[ORC_MAX_BOARD];
+    double stack[2], contrib0[2];
+    int nbet_t;                      /* turn round */
+    double bet_frac_t[ORC_MAX_BETS];
+    int raise_cap_t, allow_allin_t;
+    int nbet_r;                      /* river round */
+    double bet_frac_r[ORC_MAX_BETS];
+    int raise_cap_r, allow_allin_r;
+    const double *mu1, *mu2;         /* per hand; NULL = uniform */
+    const int *strength;             /* [ranks*suits][H] */
+} orc_turn_spec;
+
+typedef struct orc_turn orc_turn;
+
+/* NULL on invalid input or when a non-fold ending of the turn leaves a
+ * player all in (no river betting). */
+orc_turn *orc_turn_build(const orc_turn_spec *spec);
+void orc_turn_free(orc_turn *g);
+/* info[0..8] = H, n1, n2, T, turn endings, river blocks, turn sequences of
+ * player 1 and 2, cards left after the board. */
+void orc_turn_info(const orc_turn *g, int *info);
+double orc_turn_beta(const orc_turn *g);
+int orc_turn_disjoint(const orc_turn *g, int h1, int h2);
+/* Direct products: transpose 0: out = A v (v [batch][n2][H], out
+ * [batch][n1][H]); 1: out = A^T v. */
+void orc_turn_matvec(const orc_turn *g, const double *v, double *out, int batch, int transpose, int nthreads);
+/* Selected entries of the product (out[k] = entry (s[k], h[k]) of vector b[k]). */
+void orc_turn_entries(const orc_turn *g, const double *v, int nent, const int *b, const int *s, const int *h,
+                      int transpose, double *out);
+/* Expected payoff of player 1 by walking the whole tree (deal, turn round,
+ * river card, river round) with behavioural strategies [n_p][H]. */
+double orc_turn_bruteforce(const orc_turn *g, const double *beh1, const double *beh2);
+/* parent[s]; for every sequence the id of its node's first sequence and the
+ * node's action count (either array may be NULL). */
+void orc_turn_sequences(const orc_turn *g, int p, int *parent, int *node_of_seq, int *nact_of_seq);
+void orc_turn_seqform(const orc_turn *g, int p, const double *beh, double *x);
+
 #ifdef __cplusplus
 }
 #endif

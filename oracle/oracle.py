@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "kps_oracle.c")
+_SRC_TURN = os.path.join(_HERE, "kps_turn_oracle.c")
 _LIB = os.path.join(_HERE, "libkps_oracle.so")
 
 MAX_BETS = 8
@@ -29,10 +30,10 @@ MAX_BOARD = 8
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, OpenMP) next to its source."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "kps_oracle.h"))):
+            os.path.getmtime(_SRC), os.path.getmtime(_SRC_TURN), os.path.getmtime(os.path.join(_HERE, "kps_oracle.h"))):
         tmp = _LIB + ".tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC",
-                               "-Wall", "-Wno-unused-function", "-o", tmp, _SRC, "-lm"])
+                               "-Wall", "-Wno-unused-function", "-o", tmp, _SRC, _SRC_TURN, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -47,6 +48,18 @@ class _Spec(C.Structure):
                 ("strength", C.POINTER(C.c_int)),
                 ("use_menu", C.c_int), ("menu_nbet", (C.c_int * 5) * 2),
                 ("menu_frac", ((C.c_double * MAX_BETS) * 5) * 2)]
+
+
+class _TurnSpec(C.Structure):
+    _fields_ = [("ranks", C.c_int), ("suits", C.c_int), ("cards_per_hand", C.c_int),
+                ("nboard", C.c_int), ("board", C.c_int * MAX_BOARD),
+                ("stack", C.c_double * 2), ("contrib0", C.c_double * 2),
+                ("nbet_t", C.c_int), ("bet_frac_t", C.c_double * MAX_BETS),
+                ("raise_cap_t", C.c_int), ("allow_allin_t", C.c_int),
+                ("nbet_r", C.c_int), ("bet_frac_r", C.c_double * MAX_BETS),
+                ("raise_cap_r", C.c_int), ("allow_allin_r", C.c_int),
+                ("mu1", C.POINTER(C.c_double)), ("mu2", C.POINTER(C.c_double)),
+                ("strength", C.POINTER(C.c_int))]
 
 
 _lib = None
@@ -67,6 +80,18 @@ def lib():
         L.orc_regret_floor.restype = C.c_double
         L.orc_rmplus_warm.argtypes = [P, C.c_int, P, P, C.c_double, C.c_int, P, P, P, C.c_int]
         L.orc_rmplus_warm.restype = C.c_double
+        L.orc_turn_build.restype = P
+        L.orc_turn_build.argtypes = [C.POINTER(_TurnSpec)]
+        L.orc_turn_free.argtypes = [P]
+        L.orc_turn_info.argtypes = [P, P]
+        L.orc_turn_beta.restype = C.c_double
+        L.orc_turn_beta.argtypes = [P]
+        L.orc_turn_matvec.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int]
+        L.orc_turn_entries.argtypes = [P, P, C.c_int, P, P, P, C.c_int, P]
+        L.orc_turn_bruteforce.restype = C.c_double
+        L.orc_turn_bruteforce.argtypes = [P, P, P]
+        L.orc_turn_sequences.argtypes = [P, C.c_int, P, P, P]
+        L.orc_turn_seqform.argtypes = [P, C.c_int, P, P]
         L.orc_rmplus_eps.argtypes = [P, C.c_int, C.c_double, P, P]
         L.orc_rmplus_eps.restype = C.c_double
         L.orc_dcfr.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, P, P, P, C.c_int]
@@ -286,3 +311,85 @@ class OracleGame:
         x = np.ascontiguousarray(x, dtype=np.float64)
         y = np.ascontiguousarray(y, dtype=np.float64)
         return lib().orc_value(self._g, _p(x), _p(y))
+
+
+class OracleTurn:
+    """A turn endgame (turn round, river card, river round) built by the
+    oracle from a spec dict: ranks, suits, cards_per_hand, board (the turn
+    board), stack, contrib0, bet_frac_t / raise_cap_t / allow_allin_t (turn
+    round), bet_frac_r / raise_cap_r / allow_allin_r (river round), mu1 /
+    mu2 (per hand, optional) and strength [ranks*suits][H] (hand strength
+    with each river card).  Vectors are [sequence][hand] in the layout of
+    kps_oracle.h (turn sequences, then the (ending, river card) blocks)."""
+
+    def __init__(self, spec: dict):
+        L = lib()
+        s = _TurnSpec()
+        s.ranks, s.suits = int(spec["ranks"]), int(spec["suits"])
+        s.cards_per_hand = int(spec["cards_per_hand"])
+        board = list(spec["board"])
+        s.nboard = len(board)
+        for i, c in enumerate(board):
+            s.board[i] = int(c)
+        s.stack[0], s.stack[1] = [float(v) for v in spec["stack"]]
+        s.contrib0[0], s.contrib0[1] = [float(v) for v in spec["contrib0"]]
+        for tag in ("t", "r"):
+            fr = list(spec["bet_frac_" + tag])
+            setattr(s, "nbet_" + tag, len(fr))
+            arr = getattr(s, "bet_frac_" + tag)
+            for i, f in enumerate(fr):
+                arr[i] = float(f)
+            setattr(s, "raise_cap_" + tag, int(spec["raise_cap_" + tag]))
+            setattr(s, "allow_allin_" + tag, 1 if spec.get("allow_allin_" + tag, False) else 0)
+        self._strength = np.ascontiguousarray(spec["strength"], dtype=np.int32)
+        self._mu1 = None if spec.get("mu1") is None else np.ascontiguousarray(spec["mu1"], dtype=np.float64)
+        self._mu2 = None if spec.get("mu2") is None else np.ascontiguousarray(spec["mu2"], dtype=np.float64)
+        s.strength = self._strength.ctypes.data_as(C.POINTER(C.c_int))
+        s.mu1 = self._mu1.ctypes.data_as(C.POINTER(C.c_double)) if self._mu1 is not None else None
+        s.mu2 = self._mu2.ctypes.data_as(C.POINTER(C.c_double)) if self._mu2 is not None else None
+        self._g = L.orc_turn_build(C.byref(s))
+        if not self._g:
+            raise ValueError("oracle rejected the turn spec")
+        info = np.zeros(9, dtype=np.int32)
+        L.orc_turn_info(self._g, _p(info))
+        (self.H, self.n1, self.n2, self.T, self.endings, self.blocks, self.nturn1, self.nturn2,
+         self.N) = [int(v) for v in info]
+        self.beta = L.orc_turn_beta(self._g)
+
+    def __del__(self):
+        if getattr(self, "_g", None):
+            lib().orc_turn_free(self._g)
+            self._g = None
+
+    def sequences(self, p: int) -> dict:
+        n = self.n1 if p == 0 else self.n2
+        parent, node, nact = (np.zeros(n, np.int32) for _ in range(3))
+        lib().orc_turn_sequences(self._g, p, _p(parent), _p(node), _p(nact))
+        return dict(parent=parent, node=node, nact=nact)
+
+    def matvec(self, v: np.ndarray, transpose: bool = False, nthreads: int = 0) -> np.ndarray:
+        nin, nout = (self.n1, self.n2) if transpose else (self.n2, self.n1)
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, nin, self.H)
+        out = np.zeros((v.shape[0], nout, self.H))
+        lib().orc_turn_matvec(self._g, _p(v), _p(out), v.shape[0], 1 if transpose else 0, nthreads)
+        return out
+
+    def entries(self, v: np.ndarray, b, s, h, transpose: bool = False) -> np.ndarray:
+        nin = self.n1 if transpose else self.n2
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, nin, self.H)
+        b, s, h = (np.ascontiguousarray(a, dtype=np.int32) for a in (b, s, h))
+        out = np.zeros(len(b))
+        lib().orc_turn_entries(self._g, _p(v), len(b), _p(b), _p(s), _p(h), 1 if transpose else 0, _p(out))
+        return out
+
+    def bruteforce_value(self, beh1: np.ndarray, beh2: np.ndarray) -> float:
+        b1 = np.ascontiguousarray(beh1, dtype=np.float64)
+        b2 = np.ascontiguousarray(beh2, dtype=np.float64)
+        return lib().orc_turn_bruteforce(self._g, _p(b1), _p(b2))
+
+    def seqform(self, p: int, beh: np.ndarray) -> np.ndarray:
+        b = np.ascontiguousarray(beh, dtype=np.float64)
+        x = np.zeros_like(b)
+        lib().orc_turn_seqform(self._g, p, _p(b), _p(x))
+        return x
+

@@ -192,3 +192,27 @@ def simplex_vectors(nact_per_node, H: int, batch: int, seed: int, dtype=np.float
 def integer_vectors(n: int, H: int, batch: int, seed: int, lo: int = -3, hi: int = 4) -> np.ndarray:
     """Small-integer vectors for exact-arithmetic checks."""
     return _rng(seed).integers(lo, hi, size=(batch, n, H)).astype(np.float64)
+
+
+def turn_spec(seed: int = 2, ranks: int = 13, suits: int = 4, cards_per_hand: int = 2,
+              bet_frac_t=(1.0,), raise_cap_t: int = 2, bet_frac_r=(0.5, 1.0), raise_cap_r: int = 2,
+              stack: float = 200.0, contrib: float = 1.0, strength_top: int = HAND_RANKS,
+              beliefs: bool = True) -> dict:
+    """Turn endgame shape: a seeded 4-card board, hands over the remaining
+    cards (C(48,2) = 1128 for the full deck), a turn betting round, then a
+    river card and a river round.  strength[r][h]: hand h's showdown
+    strength with river card r, uniform integers in [0, strength_top) drawn
+    independently per card (ties occur); beliefs uniform in [0.5, 1.5)."""
+    r = _rng(seed)
+    ncard = ranks * suits
+    board = sorted(r.choice(ncard, size=4, replace=False).tolist())
+    H = num_hands(ranks, suits, 4, cards_per_hand)
+    strength = r.integers(0, strength_top, size=(ncard, H))
+    mu1 = r.uniform(0.5, 1.5, size=H) if beliefs else None
+    mu2 = r.uniform(0.5, 1.5, size=H) if beliefs else None
+    return dict(ranks=ranks, suits=suits, cards_per_hand=cards_per_hand, board=board,
+                stack=[stack, stack], contrib0=[contrib, contrib],
+                bet_frac_t=list(bet_frac_t), raise_cap_t=raise_cap_t, allow_allin_t=False,
+                bet_frac_r=list(bet_frac_r), raise_cap_r=raise_cap_r, allow_allin_r=False,
+                strength=strength, mu1=mu1, mu2=mu2)
+
