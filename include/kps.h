@@ -258,6 +258,75 @@ kps_status kps_batch_shape_set(kps_batch *batch, kps_dtype dt, const kps_batch_s
  * games need no communication; only per-game scalars are gathered). */
 kps_status kps_partition(const int64_t *weights, int32_t n, int32_t parts, int32_t *bounds);
 
+/* ---- Turn endgames (end of Sec. 3) -----------------------------------------
+ * A turn endgame: the turn betting round, then at every ending of that
+ * round that is not a fold the river card (public; uniform over the cards
+ * in neither hand nor on the board) and the river betting round.  The river
+ * card being public, the payoff matrix is block diagonal with one river
+ * block per (turn ending, river card), each a river game of Prop. 1 (the
+ * paper's remark after Prop. 1).  The library builds the turn round (its
+ * folds) and every block as Kronecker-form games and runs the products of
+ * all of them in one batched persistent launch.
+ *   - Hands: 1- or 2-card hands over the deck minus the turn board
+ *     (canonical order as for kps_game_spec), the same hand set in every
+ *     block; beliefs mu1, mu2 per canonical hand (NULL = 1).
+ *   - strength[r * H + h]: showdown strength of canonical hand h when the
+ *     river card is r (card id); higher wins; entries for cards on the
+ *     board or in the hand are not read.
+ *   - Betting in each round as for kps_game_spec, player 1 first in both;
+ *     the river starts from the turn ending's contributions with the chips
+ *     left behind.  An ending that leaves a player all in (no river betting)
+ *     is refused (KPS_ENOTSUP).
+ *   - Chance: pi(h1,h2) = mu1 mu2 / beta over disjoint hands (Sec. 3), the
+ *     river card with probability 1 / (N - 2k) (N cards left after the
+ *     board, k cards per hand); inside a block both factors are folded into
+ *     lambda = mu / sqrt(beta (N - 2k)).
+ * Vector layout: game after game as a kps_batch (kps_turn_offsets): game 0
+ * is the turn round (its sequences), games 1.. the blocks, endings in
+ * depth-first order of the turn round, river cards ascending; within a game
+ * [sequence][hs], hands in that game's library order (kps_turn_block gives
+ * the canonical index of every position: a block's order is its river
+ * strength order).  One vector per call.
+ * Errors: KPS_EINVAL (bad spec), KPS_ENOTSUP, KPS_ENOMEM, KPS_ECUDA. */
+typedef struct {
+    int32_t ranks, suits;              /* deck = ranks*suits <= 63 cards      */
+    int32_t cards_per_hand;            /* 1 or 2                              */
+    int32_t nboard;
+    int32_t board[KPS_MAX_BOARD];      /* the turn board                      */
+    double stack[2], contrib0[2];      /* at the start of the turn round      */
+    int32_t nbet_turn;
+    double bet_frac_turn[KPS_MAX_BETS];
+    int32_t raise_cap_turn, allow_allin_turn;
+    int32_t nbet_river;
+    double bet_frac_river[KPS_MAX_BETS];
+    int32_t raise_cap_river, allow_allin_river;
+    const double *mu1, *mu2;           /* per canonical hand; NULL = 1        */
+    const int32_t *strength;           /* [ranks*suits][H]                    */
+} kps_turn_spec;
+
+typedef struct kps_turn kps_turn;
+
+kps_status kps_turn_create(const kps_turn_spec *spec, kps_turn **out);
+kps_status kps_turn_destroy(kps_turn *turn);
+/* info[0..8] = H, hs, n1, n2 (all sequences of the layout), turn endings
+ * that are not folds, river blocks, games (blocks + 1), turn-round
+ * sequences of player 1 and of player 2. */
+kps_status kps_turn_info(const kps_turn *turn, int64_t *info);
+/* Element offsets of every game's part of a player's vector (games + 1). */
+kps_status kps_turn_offsets(const kps_turn *turn, int32_t player, int64_t *off);
+/* Game `block` (0 = the turn round): its turn ending and river card (-1 for
+ * the turn round) and the canonical index of each of its hand positions
+ * (any pointer may be NULL). */
+kps_status kps_turn_block(const kps_turn *turn, int32_t block, int32_t *ending, int32_t *river_card,
+                          int32_t *canon);
+/* out = A y (player-2 vector y, player-1 vector out) and out = A^T x, one
+ * vector each, device, 16-byte aligned; dtypes as kps_batch_matvec_A. */
+kps_status kps_turn_matvec_A(kps_turn *turn, const void *y, void *out, kps_dtype dt, void *stream);
+kps_status kps_turn_matvec_AT(kps_turn *turn, const void *x, void *out, kps_dtype dt, void *stream);
+/* The batch of games behind the turn endgame (owned by the turn object):
+ * launch shapes (kps_batch_tune / kps_batch_shape_set) apply to it. */
+kps_status kps_turn_batch(kps_turn *turn, kps_batch **batch);
+
 /* ---- First-order solver ---------------------------------------------------
  * Regret matching plus with alternating updates and linearly weighted
  * averages on every game of a batch, the gradients A y and -A^T x coming

@@ -549,13 +549,21 @@ kps_status matvec_host(kps_game *g, int dir, const void *vin, void *vout, int32_
 extern "C" {
 
 kps_status kps_sparsify(const kps_game_spec *spec, kps_game **out) {
+    return create_game(spec, nullptr, out);
+}
+
+}  // extern "C"
+
+namespace kps_abi {
+
+kps_status create_game(const kps_game_spec *spec, const kps::BuildOptions *opt, kps_game **out) {
     if (!out) return fail(KPS_EINVAL, "out is NULL");
     *out = nullptr;
     kps_game *g = new (std::nothrow) kps_game();
     if (!g) return fail(KPS_ENOMEM, "host allocation");
     try {
         kps_status code = KPS_OK;
-        std::string err = kps::build_game(spec, g->host, &code);
+        std::string err = kps::build_game(spec, g->host, &code, opt);
         if (err.empty()) err = split_rows(g), code = err.empty() ? KPS_OK : KPS_ENOTSUP;
         if (!err.empty()) {
             delete g;
@@ -572,6 +580,10 @@ kps_status kps_sparsify(const kps_game_spec *spec, kps_game **out) {
     g_last_error.clear();
     return KPS_OK;
 }
+
+}  // namespace kps_abi
+
+extern "C" {
 
 kps_status kps_game_destroy(kps_game *g) {
     if (!g) return KPS_OK;

@@ -81,6 +81,9 @@ struct kps_game {
 
 namespace kps_abi {
 
+// kps_sparsify with internal build options (NULL = none).
+kps_status create_game(const kps_game_spec *spec, const kps::BuildOptions *opt, kps_game **out);
+
 // Uploads the game's tables to the current device on first use.
 kps_status upload(kps_game *g, cudaStream_t stream);
 

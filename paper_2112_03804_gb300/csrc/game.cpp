@@ -311,7 +311,7 @@ std::string build_hands(HostGame &g, const double *mu1_canon, const double *mu2_
 
 }  // namespace
 
-std::string build_game(const kps_game_spec *spec, HostGame &g, kps_status *code) {
+std::string build_game(const kps_game_spec *spec, HostGame &g, kps_status *code, const BuildOptions *opt) {
     std::string err = validate(spec, code);
     if (!err.empty()) return err;
     g.spec = *spec;
@@ -326,12 +326,25 @@ std::string build_game(const kps_game_spec *spec, HostGame &g, kps_status *code)
     *code = KPS_EINVAL;
     err = build_hands(g, spec->mu1, spec->mu2, spec->strength);
     if (!err.empty()) return err;
+    if (opt && opt->beta > 0.0) {
+        if (!std::isfinite(opt->beta)) return "beta must be finite";
+        g.beta = opt->beta;
+        const double rs = 1.0 / std::sqrt(g.beta);
+        for (int p = 0; p < g.H; ++p) {
+            g.lam1[p] = g.mu1[p] * rs;
+            g.lam2[p] = g.mu2[p] * rs;
+        }
+    }
     err = build_tree(g);
     if (!err.empty()) {
         if (err == "betting tree too large") *code = KPS_ENOTSUP;
         return err;
     }
     build_pairs(g);
+    if (opt && opt->showdown_pays_zero)
+        for (PairCsr *csr : {&g.csr_A, &g.csr_AT})
+            for (size_t e = 0; e < csr->kind.size(); ++e)
+                if (csr->kind[e] == 1) csr->coef[e] = 0.0;
     *code = KPS_OK;
     return "";
 }

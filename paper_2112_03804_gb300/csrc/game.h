@@ -78,9 +78,19 @@ struct HostGame {
     int64_t counts[9] = {0};        // nnz A, Ahat, U, M, V, pp Ahat, U, M, V
 };
 
+// Internal build options for games that are parts of a larger game (the
+// river blocks of a turn endgame, its turn round): a chance normalisation
+// given from outside (lambda_i = mu_i / sqrt(beta)) instead of the game's
+// own, and showdowns that pay nothing (the round continues elsewhere).
+struct BuildOptions {
+    double beta = 0.0;             // > 0: use this beta
+    bool showdown_pays_zero = false;
+};
+
 // Builds the game; returns an empty string on success, else a message.
 // `code` receives KPS_EINVAL or KPS_ENOTSUP on failure.
-std::string build_game(const kps_game_spec *spec, HostGame &g, kps_status *code);
+std::string build_game(const kps_game_spec *spec, HostGame &g, kps_status *code,
+                       const BuildOptions *opt = nullptr);
 
 // Technique B sizes (Sec. 4) from the structure of the factors.
 void technique_b_counts(HostGame &g);

@@ -51,6 +51,18 @@ class GameSpec(C.Structure):
                 ("strength", C.POINTER(C.c_int32)), ("menu", C.POINTER(BetMenu))]
 
 
+class TurnSpec(C.Structure):
+    _fields_ = [("ranks", C.c_int32), ("suits", C.c_int32), ("cards_per_hand", C.c_int32),
+                ("nboard", C.c_int32), ("board", C.c_int32 * MAX_BOARD),
+                ("stack", C.c_double * 2), ("contrib0", C.c_double * 2),
+                ("nbet_turn", C.c_int32), ("bet_frac_turn", C.c_double * MAX_BETS),
+                ("raise_cap_turn", C.c_int32), ("allow_allin_turn", C.c_int32),
+                ("nbet_river", C.c_int32), ("bet_frac_river", C.c_double * MAX_BETS),
+                ("raise_cap_river", C.c_int32), ("allow_allin_river", C.c_int32),
+                ("mu1", C.POINTER(C.c_double)), ("mu2", C.POINTER(C.c_double)),
+                ("strength", C.POINTER(C.c_int32))]
+
+
 class Info(C.Structure):
     _fields_ = [("H", C.c_int32), ("hs", C.c_int32), ("n1", C.c_int32), ("n2", C.c_int32),
                 ("T", C.c_int32), ("T_fold", C.c_int32), ("T_showdown", C.c_int32),
@@ -89,6 +101,8 @@ EXPORTED = ["kps_sparsify", "kps_game_destroy", "kps_game_info", "kps_game_hands
             "kps_mlp_create", "kps_mlp_destroy", "kps_mlp_num_params", "kps_mlp_get", "kps_mlp_set",
             "kps_mlp_forward", "kps_mlp_gradients", "kps_mlp_adam", "kps_mlp_state_bytes", "kps_mlp_save",
             "kps_mlp_load",
+            "kps_turn_create", "kps_turn_destroy", "kps_turn_info", "kps_turn_offsets", "kps_turn_block",
+            "kps_turn_matvec_A", "kps_turn_matvec_AT", "kps_turn_batch",
             "kps_tb_create", "kps_tb_destroy", "kps_tb_sizes", "kps_tb_export", "kps_tb_matvec",
             "kps_last_error", "kps_version"]
 
@@ -128,6 +142,14 @@ def lib():
         L.kps_solver_reset.argtypes = [P, P, P, P]
         L.kps_solver_step.argtypes = [P, C.c_int32, P]
         L.kps_solver_status.argtypes = [P]
+        L.kps_turn_create.argtypes = [C.POINTER(TurnSpec), C.POINTER(C.c_void_p)]
+        L.kps_turn_destroy.argtypes = [P]
+        L.kps_turn_info.argtypes = [P, P]
+        L.kps_turn_offsets.argtypes = [P, C.c_int32, P]
+        L.kps_turn_block.argtypes = [P, C.c_int32, P, P, P]
+        L.kps_turn_matvec_A.argtypes = [P, P, P, C.c_int, P]
+        L.kps_turn_matvec_AT.argtypes = [P, P, P, C.c_int, P]
+        L.kps_turn_batch.argtypes = [P, C.POINTER(C.c_void_p)]
         L.kps_solver_state_bytes.argtypes = [P, C.POINTER(C.c_int64)]
         L.kps_solver_save.argtypes = [P, P, C.c_int64, P]
         L.kps_solver_load.argtypes = [P, P, C.c_int64, P]
@@ -457,6 +479,82 @@ def partition(weights, parts: int) -> np.ndarray:
     bounds = np.zeros(parts + 1, dtype=np.int32)
     _check(lib().kps_partition(w.ctypes.data if len(w) else None, len(w), parts, bounds.ctypes.data))
     return bounds
+
+
+class Turn:
+    """A turn endgame (``kps_turn_*``): the turn round's folds and one river
+    block per (turn ending, river card), run as one batched launch.  spec
+    keys as synth.turn_spec: ranks, suits, cards_per_hand, board, stack,
+    contrib0, bet_frac_t / raise_cap_t / allow_allin_t, bet_frac_r /
+    raise_cap_r / allow_allin_r, mu1, mu2, strength [ranks*suits][H]."""
+
+    def __init__(self, spec: dict):
+        s = TurnSpec()
+        s.ranks, s.suits = int(spec["ranks"]), int(spec["suits"])
+        s.cards_per_hand = int(spec["cards_per_hand"])
+        board = list(spec["board"])
+        if len(board) > MAX_BOARD:
+            raise ValueError("board too long")
+        s.nboard = len(board)
+        for i, c in enumerate(board):
+            s.board[i] = int(c)
+        s.stack[0], s.stack[1] = [float(v) for v in spec["stack"]]
+        s.contrib0[0], s.contrib0[1] = [float(v) for v in spec["contrib0"]]
+        for tag, name in (("t", "turn"), ("r", "river")):
+            fr = list(spec["bet_frac_" + tag])
+            if len(fr) > MAX_BETS:
+                raise ValueError("too many bet sizes")
+            setattr(s, "nbet_" + name, len(fr))
+            arr = getattr(s, "bet_frac_" + name)
+            for i, f in enumerate(fr):
+                arr[i] = float(f)
+            setattr(s, "raise_cap_" + name, int(spec["raise_cap_" + tag]))
+            setattr(s, "allow_allin_" + name, 1 if spec.get("allow_allin_" + tag, False) else 0)
+        self._strength = np.ascontiguousarray(spec["strength"], dtype=np.int32)
+        mu1, mu2 = spec.get("mu1"), spec.get("mu2")
+        self._mu1 = None if mu1 is None else np.ascontiguousarray(mu1, dtype=np.float64)
+        self._mu2 = None if mu2 is None else np.ascontiguousarray(mu2, dtype=np.float64)
+        s.strength = self._strength.ctypes.data_as(C.POINTER(C.c_int32))
+        s.mu1 = self._mu1.ctypes.data_as(C.POINTER(C.c_double)) if self._mu1 is not None else None
+        s.mu2 = self._mu2.ctypes.data_as(C.POINTER(C.c_double)) if self._mu2 is not None else None
+        h = C.c_void_p()
+        _check(lib().kps_turn_create(C.byref(s), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().kps_turn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        v = np.zeros(9, dtype=np.int64)
+        _check(lib().kps_turn_info(self._h, v.ctypes.data))
+        keys = ("H", "hs", "n1", "n2", "endings", "blocks", "games", "turn_n1", "turn_n2")
+        return {k: int(x) for k, x in zip(keys, v)}
+
+    def offsets(self, player: int) -> np.ndarray:
+        off = np.zeros(self.info()["games"] + 1, dtype=np.int64)
+        _check(lib().kps_turn_offsets(self._h, int(player), off.ctypes.data))
+        return off
+
+    def block(self, i: int):
+        """(ending, river card, canonical index of every hand position)."""
+        e, r = C.c_int32(), C.c_int32()
+        canon = np.zeros(self.info()["H"], dtype=np.int32)
+        _check(lib().kps_turn_block(self._h, int(i), C.byref(e), C.byref(r), canon.ctypes.data))
+        return e.value, r.value, canon
+
+    def matvec_A(self, y, out, dtype=None, stream=None):
+        _check(lib().kps_turn_matvec_A(self._h, _ptr(y), _ptr(out), _dtype_code(y, dtype), _stream(stream)))
+
+    def matvec_AT(self, x, out, dtype=None, stream=None):
+        _check(lib().kps_turn_matvec_AT(self._h, _ptr(x), _ptr(out), _dtype_code(x, dtype), _stream(stream)))
 
 
 class Solver:
