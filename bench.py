@@ -30,7 +30,7 @@ UNIT = "matvecs/s"
 BATCH = 1024
 WORKLOAD = "river endgame, 1081 hands, 43+43 sequences, 57 terminals, batch 1024, fp32"
 CSRC = os.path.join(ROOT, "paper_2112_03804_gb300", "csrc")
-KERNEL = "tmem_scan_kernel"
+KERNEL = "tma_scan_kernel"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -44,7 +44,8 @@ def _args():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--workload", default="matvec", choices=["matvec", "batch", "solver", "warmstart", "factors", "libratus", "libratus_solve"],
+    ap.add_argument("--workload", default="matvec", choices=["matvec", "batch", "solver", "warmstart", "factors", "libratus", "libratus_solve",
+                                                   "turn"],
                     help="matvec: the headline line; batch / solver / warmstart / factors / libratus: print "
                          "only that measurement")
     ap.add_argument("--games", type=int, default=4096, help="games of the batched workload")
@@ -69,7 +70,7 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("kernels.h", "kernels_tmem.cu")
+KERNEL_SOURCES = ("kernels.h", "scan_records.h", "scan_records.cpp", "kernels_tma.cu")
 
 
 def _kernel_hash():
@@ -275,6 +276,7 @@ def run_ours(args):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    ran = [g.kernel(0), g.kernel(1)]
     la = [e[0].elapsed_time(e[1]) for e in evs]
     lt = [e[1].elapsed_time(e[2]) for e in evs]
     # end to end through the host-buffer entry points (pinned host memory)
@@ -286,7 +288,7 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return
-    _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec)
+    _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec, ran)
     if dist:
         dist.destroy_process_group()
 
@@ -349,6 +351,51 @@ def measure_batch(ngames: int, steps: int, warmup: int, rank: int = 0):
             "launch_shape": {k: shape[k] for k in ("warps", "grid", "schedule")},
             "tuned_ms_per_pair": shape["ms_per_pair"], "cuda_graph": True,
             "l2": "inputs larger than L2" if alg > 2.6e8 else "inputs smaller than L2"}
+
+
+def measure_turn(steps: int = 10, warmup: int = 3, seed: int = 2):
+    """Products of a turn endgame (end of Sec. 3): the 52-card turn (4-card
+    board, 1128 hands), a turn round with one pot-size bet and at most two
+    aggressive actions, then 48 river cards and a river round with bets of
+    0.5 and 1.0 pot: one batched launch over the turn round and its river
+    blocks per product, FP32.  The inputs are smaller than L2, so L2 is
+    flushed (a 512 MB write) before every step, outside the timed events."""
+    import torch
+    from paper_2112_03804_gb300 import kps, synth
+    t = kps.Turn(synth.turn_spec(seed=seed))
+    inf = t.info()
+    off = [t.offsets(p) for p in (0, 1)]
+    gen = torch.Generator(device="cuda").manual_seed(9)
+    vec = {p: torch.rand(int(off[p][-1]), device="cuda", generator=gen) for p in (0, 1)}
+    out = {p: torch.empty(int(off[p][-1]), device="cuda") for p in (0, 1)}
+    stream = torch.cuda.current_stream()
+    shape = t.tune(kps.F32, stream)
+    flush = torch.empty(128 << 20, dtype=torch.float32, device="cuda")
+    for _ in range(max(warmup, 3)):
+        t.matvec_A(vec[1], out[0], stream=stream)
+        t.matvec_AT(vec[0], out[1], stream=stream)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t.matvec_A(vec[1], out[0], stream=stream)
+        t.matvec_AT(vec[0], out[1], stream=stream)
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in times)
+    # every game of the layout: one input read and one output written per product
+    alg = 8.0 * inf["hs"] * (inf["n1"] + inf["n2"])
+    peak, peak_kind = _peaks()
+    gbs = alg / (ms / 1e3) / 1e9
+    return {"workload": f"turn endgame: {inf['H']} hands, {inf['endings']} turn endings x 48 river cards = "
+                        f"{inf['blocks']} river blocks, {inf['n1']}+{inf['n2']} sequences, fp32, one vector",
+            "ms_per_step": ms, "turn_matvecs_per_s": 2 / (ms / 1e3), "alg_bytes_per_step": alg,
+            "achieved_gbs": gbs, "frac_of_peak": gbs / peak, "peak_source": peak_kind,
+            "launch_shape": {k: shape[k] for k in ("warps", "grid", "schedule")},
+            "l2": "flushed before every step (inputs smaller than L2)"}
 
 
 def measure_factors(batch: int = BATCH, steps: int = 3, warmup: int = 2):
@@ -605,7 +652,7 @@ def _e2e(g, y, x, oy, ox, stream, args, world):
             "d2h_bytes_per_step": int(oyh.numel() * 4 + oxh.numel() * 4)}
 
 
-def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec):
+def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec, ran):
     mv_per_step = 2 * BATCH
     value = mv_per_step * args.steps * world / (ms / 1e3)
     peak, peak_kind = _peaks()
@@ -613,7 +660,7 @@ def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec):
     avg_launch_s = statistics.mean(la + lt) / 1e3
     achieved = alg_bytes / avg_launch_s / 1e9
     kh = _kernel_hash()
-    traffic = _traffic(kh)
+    traffic = _traffic(kh) if ran == ["tma", "tma"] else None
     clk_sum = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -625,7 +672,7 @@ def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec):
                    "parallelism": f"dp{world}" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": KERNEL, "alg_bytes_per_launch": alg_bytes,
+                     "kernel": KERNEL, "kernel_paths": ran, "alg_bytes_per_launch": alg_bytes,
                      "launch_ms": {"A": statistics.mean(la), "AT": statistics.mean(lt)}},
         "clocks": clk_sum,
         "e2e": e2e,
@@ -638,7 +685,8 @@ def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec):
     if not args.no_secondary:
         for key, fn in (("batched", lambda: measure_batch(args.games, 10, 3)), ("solver", measure_solver),
                         ("technique_b", measure_factors), ("libratus", measure_libratus),
-                        ("libratus_solve", lambda: measure_libratus_solve(seeds=(2, 3)))):
+                        ("libratus_solve", lambda: measure_libratus_solve(seeds=(2, 3))),
+                        ("turn", measure_turn)):
             try:
                 line[key] = fn()
             except Exception as exc:   # reported, never silently dropped
@@ -670,6 +718,10 @@ def main():
         import torch
         torch.cuda.set_device(_dist()[2])
         print(json.dumps(measure_libratus()), flush=True)
+    elif args.workload == "turn":
+        import torch
+        torch.cuda.set_device(_dist()[2])
+        print(json.dumps(measure_turn(steps=args.steps, warmup=args.warmup)), flush=True)
     elif args.workload == "factors":
         import torch
         torch.cuda.set_device(_dist()[2])

@@ -46,6 +46,7 @@
 // frees its tensor memory.
 #include "kernels.h"
 #include "game.h"
+#include "scan_records.h"
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -61,28 +62,7 @@
 
 namespace kps {
 
-constexpr int kTmaBox = 16;        // hands per box
-constexpr int kTmaWarps = 4;       // chunks per CTA
 constexpr int kTmaMaxExtra = 2;    // boxes of a chunk past the 256 tensor-memory columns
-
-// Scan records of a pair of hands (2i, 2i+1 of the library order, padding
-// hands included): byte offsets of the hands' card rows in a warp's per-card
-// table (card * 128; one-card hands: ob unused), their input weights
-// lambda_in, and ma / mb = 1 when the first / second card of hand 2i+1 is a
-// card of hand 2i (else 0).  A box's block is its 8 pair records followed by
-// two tie words: byte 8j + (k - 4j) of word j (pair k) has
-//   bits 2-4  hand 2k has a compatible tied hand 1, 2, 3 positions before it
-//   bits 5-7  the same for hand 2k+1.
-struct alignas(16) TmaScanRec {
-    uint32_t oa1, ob1, oa2, ob2;
-    float lin1, lin2, ma, mb;
-};
-constexpr int kScanBlock = 8 * 32 + 16;   // bytes per box
-// Finishing records of a pair: the card offsets and the output weights.
-struct alignas(16) TmaFinRec {
-    uint32_t oa1, ob1, oa2, ob2;
-    float lout1, lout2, pad0, pad1;
-};
 
 // Kernel arguments (__grid_constant__).
 struct alignas(128) TmaArgs {
@@ -689,100 +669,18 @@ static size_t tma_smem_bytes(int nc, int extra) { return hdr_off(nc, extra) + kH
 // Chunks, records and eligibility of one direction; fills p.a (but the
 // tensor maps, pointers and batch) and p.host.  Empty string on success.
 static std::string tma_prepare(const HostGame &h, const double *lam_in, const double *lam_out, TmaParams &p) {
+    ScanRecords r;
+    const std::string why = build_scan_records(h, lam_in, lam_out, kTmaMaxExtra, &r);
+    if (!why.empty()) return why;
     TmaArgs &A = p.a;
-    if (h.k != 1 && h.k != 2) return "cards per hand";
-    const int nc = h.ncards + 1;
-    if (nc > 64) return "too many cards";
-    const int H = h.H, hs = h.hs;
-    const int nbox = (hs + kTmaBox - 1) / kTmaBox;
-    // tie groups: at most 4 hands (partners within 3 positions)
-    for (int i = 0; i < H; ++i)
-        if (h.group_hi[i] - h.group_lo[i] > 3) return "tie group longer than 4 hands";
-    // chunk boundaries at box boundaries that cut no tie group, as close to
-    // an even split as possible
-    auto clean = [&](int bx) { return bx <= 0 || bx >= nbox || 16 * bx >= H || h.group_lo[16 * bx] == 16 * bx; };
-    A.bchunk[0] = 0;
-    A.bchunk[kTmaWarps] = nbox;
-    for (int k = 1; k < kTmaWarps; ++k) {
-        const int ideal = (int)((long long)nbox * k / kTmaWarps);
-        int best = -1;
-        for (int d = 0; d <= 4 && best < 0; ++d) {
-            for (int s : {ideal - d, ideal + d})
-                if (best < 0 && s >= A.bchunk[k - 1] && s <= nbox && clean(s)) best = s;
-        }
-        if (best < 0) return "no chunk boundary free of tie groups";
-        A.bchunk[k] = best;
-    }
-    int extra = 0;
-    for (int k = 0; k < kTmaWarps; ++k) {
-        const int n = A.bchunk[k + 1] - A.bchunk[k];
-        if (n < 0) return "chunk order";
-        extra = std::max(extra, n - 16);
-    }
-    if (extra > kTmaMaxExtra) return "chunk longer than tensor memory and its shared-memory overflow";
-    A.H = H;
-    A.hs = hs;
-    A.nc = nc;
-    A.k = h.k;
-    A.nbox = nbox;
-    A.extra = extra;
-    // records: scan blocks, then finishing records
-    const size_t scan_bytes = (size_t)nbox * kScanBlock, fin_bytes = (size_t)nbox * 8 * sizeof(TmaFinRec);
-    p.host.assign(scan_bytes + fin_bytes, 0);
-    auto card = [&](int hand, int j) { return h.hand_slots[2 * hand + j]; };
-    auto off = [&](int hand, int j) -> uint32_t {
-        // padding hands use the spare card row (their weights are zero)
-        if (hand >= H || j >= h.k) return (uint32_t)h.ncards * 128u;
-        return (uint32_t)card(hand, j) * 128u;
-    };
-    auto share = [&](int x, int y) {   // any card of hand y in hand x
-        for (int j = 0; j < h.k; ++j)
-            for (int l = 0; l < h.k; ++l)
-                if (card(x, j) == card(y, l)) return true;
-        return false;
-    };
-    for (int bx = 0; bx < nbox; ++bx) {
-        unsigned char *blk = p.host.data() + (size_t)bx * kScanBlock;
-        TmaFinRec *fin = reinterpret_cast<TmaFinRec *>(p.host.data() + scan_bytes) + 8 * bx;
-        uint32_t tw[2] = {0u, 0u};
-        for (int k = 0; k < 8; ++k) {
-            const int i = 16 * bx + 2 * k;
-            TmaScanRec r{};
-            r.oa1 = off(i, 0);
-            r.ob1 = off(i, 1);
-            r.oa2 = off(i + 1, 0);
-            r.ob2 = off(i + 1, 1);
-            r.lin1 = i < H ? (float)lam_in[i] : 0.f;
-            r.lin2 = i + 1 < H ? (float)lam_in[i + 1] : 0.f;
-            if (i + 1 < H)
-                for (int l = 0; l < h.k; ++l) {
-                    if (card(i + 1, 0) == card(i, l)) r.ma = 1.f;
-                    if (h.k == 2 && card(i + 1, 1) == card(i, l)) r.mb = 1.f;
-                }
-            std::memcpy(blk + 32 * k, &r, sizeof(r));
-            TmaFinRec f{};
-            f.oa1 = r.oa1;
-            f.ob1 = r.ob1;
-            f.oa2 = r.oa2;
-            f.ob2 = r.ob2;
-            f.lout1 = i < H ? (float)lam_out[i] : 0.f;
-            f.lout2 = i + 1 < H ? (float)lam_out[i + 1] : 0.f;
-            fin[k] = f;
-            uint32_t bits = 0;
-            for (int e = 0; e < 2; ++e) {
-                const int hi = i + e;
-                if (hi >= H) continue;
-                for (int d = 1; d <= 3; ++d) {
-                    const int q = hi - d;
-                    if (q < h.group_lo[hi]) break;
-                    if (share(hi, q)) continue;
-                    bits |= 1u << (e ? 4 + d : 1 + d);
-                }
-            }
-            tw[k / 4] |= bits << (8 * (k & 3));
-        }
-        std::memcpy(blk + 256, tw, sizeof(tw));
-    }
+    A.H = r.H;
+    A.hs = r.hs;
+    A.nc = r.nc;
+    A.k = r.k;
+    A.nbox = r.nbox;
+    A.extra = r.extra;
+    for (int k = 0; k <= kTmaWarps; ++k) A.bchunk[k] = r.bchunk[k];
+    p.host = std::move(r.bytes);
     return "";
 }
 

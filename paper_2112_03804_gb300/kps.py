@@ -550,6 +550,14 @@ class Turn:
         _check(lib().kps_turn_block(self._h, int(i), C.byref(e), C.byref(r), canon.ctypes.data))
         return e.value, r.value, canon
 
+    def tune(self, dtype: int, stream=None) -> dict:
+        """Autotune the launch shape of the batch behind the turn endgame."""
+        b = C.c_void_p()
+        _check(lib().kps_turn_batch(self._h, C.byref(b)))
+        sh = BatchShape()
+        _check(lib().kps_batch_tune(b, dtype, _stream(stream), C.byref(sh)))
+        return sh.as_dict()
+
     def matvec_A(self, y, out, dtype=None, stream=None):
         _check(lib().kps_turn_matvec_A(self._h, _ptr(y), _ptr(out), _dtype_code(y, dtype), _stream(stream)))
 
