@@ -348,7 +348,7 @@ def measure_batch(ngames: int, steps: int, warmup: int, rank: int = 0):
         alg += 8.0 * inf["H"] * (inf["n1"] + inf["n2"])
     return {"workload": BATCH_WORKLOAD, "games": ngames, "matvecs_per_s": 2 * ngames / (ms / 1e3),
             "ms_per_step": ms, "alg_bytes_per_step": alg, "achieved_gbs": alg / (ms / 1e3) / 1e9,
-            "launch_shape": {k: shape[k] for k in ("warps", "grid", "schedule")},
+            "launch_shape": {k: shape[k] for k in ("kernel", "warps", "grid", "schedule")},
             "tuned_ms_per_pair": shape["ms_per_pair"], "cuda_graph": True,
             "l2": "inputs larger than L2" if alg > 2.6e8 else "inputs smaller than L2"}
 
@@ -394,7 +394,7 @@ def measure_turn(steps: int = 10, warmup: int = 3, seed: int = 2):
                         f"{inf['blocks']} river blocks, {inf['n1']}+{inf['n2']} sequences, fp32, one vector",
             "ms_per_step": ms, "turn_matvecs_per_s": 2 / (ms / 1e3), "alg_bytes_per_step": alg,
             "achieved_gbs": gbs, "frac_of_peak": gbs / peak, "peak_source": peak_kind,
-            "launch_shape": {k: shape[k] for k in ("warps", "grid", "schedule")},
+            "launch_shape": {k: shape[k] for k in ("kernel", "warps", "grid", "schedule")},
             "l2": "flushed before every step (inputs smaller than L2)"}
 
 

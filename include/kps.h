@@ -222,10 +222,21 @@ kps_status kps_matvec_AT_host(kps_game *game, const void *x, void *out, int32_t 
  * tuned) for that dtype. */
 typedef struct kps_batch kps_batch;
 
+/* Multi-game kernels (kps_batch_shape.kernel):
+ *   KPS_BATCH_TMEM    tensor-memory scan, 32-column tiles, 1-8 warps (every
+ *                     storage type; FP64 runs its vector-register variant);
+ *   KPS_BATCH_STAGED  FP32 only: 4 warps per CTA scan chunks of a game's
+ *                     hand order in 16-hand boxes staged by cp.async, with
+ *                     per-box hand records (games whose tie groups have at
+ *                     most 4 hands and whose chunks fit 24 boxes). */
+#define KPS_BATCH_TMEM 0
+#define KPS_BATCH_STAGED 1
+
 typedef struct {
     int32_t warps;        /* warps per CTA                                  */
     int32_t grid;         /* CTAs of the persistent launch                  */
     int32_t schedule;     /* 0 atomic ticket counter, 1 static stride       */
+    int32_t kernel;       /* KPS_BATCH_TMEM or KPS_BATCH_STAGED             */
     double ms_per_pair;   /* tuned time of one A and one A^T launch, or 0   */
 } kps_batch_shape;
 
@@ -239,15 +250,17 @@ kps_status kps_batch_offsets(const kps_batch *batch, int32_t player, int64_t *of
 /* out = A y per game (y: player-2 layout, out: player-1 layout) / A^T x. */
 kps_status kps_batch_matvec_A(kps_batch *batch, const void *y, void *out, kps_dtype dt, void *stream);
 kps_status kps_batch_matvec_AT(kps_batch *batch, const void *x, void *out, kps_dtype dt, void *stream);
-/* Autotuner: times every admissible launch shape (warps per CTA, CTAs per
- * SM, schedule) of an A and an A^T launch with CUDA events on `stream`,
+/* Autotuner: times every admissible launch shape (kernel, warps per CTA,
+ * CTAs per SM, schedule) of an A and an A^T launch with CUDA events on `stream`,
  * keeps the fastest for `dt` and reports it in *chosen (may be NULL).
  * Allocates temporary buffers; synchronises `stream`. */
 kps_status kps_batch_tune(kps_batch *batch, kps_dtype dt, void *stream, kps_batch_shape *chosen);
 /* The launch shape in use for `dt` (the default one if never tuned). */
 kps_status kps_batch_shape_get(kps_batch *batch, kps_dtype dt, kps_batch_shape *shape);
 /* Sets the launch shape for `dt` (ms_per_pair ignored).  Errors: KPS_EINVAL
- * (out of range), KPS_ENOTSUP (warp count the games do not fit). */
+ * (out of range), KPS_ENOTSUP (warp count the games do not fit; the staged
+ * kernel for another dtype than FP32, with other than 4 warps, more than 2
+ * CTAs per SM, or for games it does not take). */
 kps_status kps_batch_shape_set(kps_batch *batch, kps_dtype dt, const kps_batch_shape *shape);
 
 /* Splits items 0..n-1 (games, in order) into `parts` contiguous ranges

@@ -23,7 +23,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
               "-I" + INCLUDE] + ARCH
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-I" + INCLUDE]
 
-SOURCES = ["game.cpp", "scan_records.cpp", "abi.cu", "kernels.cu", "kernels_fast.cu", "kernels_vec.cu", "kernels_tmem.cu", "kernels_tma.cu", "batch.cu", "turn.cu", "solver.cu", "mlp.cu", "warm.cu", "tb.cu"]
+SOURCES = ["game.cpp", "scan_records.cpp", "kernels_amulti.cu", "abi.cu", "kernels.cu", "kernels_fast.cu", "kernels_vec.cu", "kernels_tmem.cu", "kernels_tma.cu", "batch.cu", "turn.cu", "solver.cu", "mlp.cu", "warm.cu", "tb.cu"]
 
 
 def _nvcc() -> str:

@@ -56,14 +56,79 @@ int tmem_min_warps(kps_batch *b) {
 
 }  // namespace
 
-// Launch table of one (direction, FP64 or not, warp count).
-kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t stream, const BatchTable **out) {
-    const auto key = std::make_tuple(dir, f64, nw);
-    auto it = b->tables.find(key);
-    if (it != b->tables.end()) {
-        *out = &it->second;
-        return KPS_OK;
+bool batch_staged_ready(kps_batch *b, cudaStream_t stream) {
+    if (b->am_state != 0) return b->am_state == 1;
+    b->am_state = -1;
+    const int ng = (int)b->games.size();
+    for (int dir = 0; dir < 2; ++dir) {
+        std::vector<kps::AmGameDesc> d(ng);
+        for (int i = 0; i < ng; ++i) {
+            const kps_game *g = b->games[i];
+            const kps::HostGame &h = g->host;
+            kps::AmGameDesc &x = d[i];
+            x.h = &h;
+            x.lam_in = dir == 0 ? h.lam2.data() : h.lam1.data();
+            x.lam_out = dir == 0 ? h.lam1.data() : h.lam2.data();
+            x.n_out = dir == 0 ? h.n[0] : h.n[1];
+            x.fcol = g->dev.fcol[dir];
+            x.scol = g->dev.scol[dir];
+            x.fcoef = g->dev.fcoef_f[dir];
+            x.scoef = g->dev.scoef_f[dir];
+            x.in_off = b->off[dir == 0 ? 1 : 0][i];
+            x.out_off = b->off[dir == 0 ? 0 : 1][i];
+        }
+        std::string why;
+        std::vector<char> taken;
+        b->am[dir] = kps::am_create(d, 2 * sm_count(), stream, &taken, &why);
+        bool ok = b->am[dir] != nullptr && kps::am_ctas_per_sm(b->am[dir]) >= 1;
+        if (ok && dir == 1) ok = b->am_rest.size() == taken.size();
+        for (int i = 0; ok && i < ng; ++i) {
+            if (dir == 0) b->am_rest.push_back(taken[i] ? 0 : 1);
+            else ok = b->am_rest[i] == (taken[i] ? 0 : 1);
+        }
+        if (!ok) {
+            for (int k = 0; k < 2; ++k) {
+                kps::am_destroy(b->am[k]);
+                b->am[k] = nullptr;
+            }
+            b->am_rest.clear();
+            return false;
+        }
     }
+    // the games left to the tensor-memory kernel, and its warp count for them
+    b->am_nrest = 0;
+    int lo = 0;
+    bool fit4 = true;
+    for (int i = 0; i < ng; ++i) {
+        if (!b->am_rest[i]) continue;
+        ++b->am_nrest;
+        const kps::HostGame &h = b->games[i]->host;
+        int w = 1;
+        while (w <= kps::kMaxWarps && !kps_abi::tmem_split_fits(h, w)) ++w;
+        lo = std::max(lo, w);
+        fit4 = fit4 && kps_abi::tmem_split_fits(h, 4);
+    }
+    if (b->am_nrest > 0) {
+        if (lo > kps::kMaxWarps || b->games[0]->host.ncards + 1 > 66) {
+            for (int k = 0; k < 2; ++k) {
+                kps::am_destroy(b->am[k]);
+                b->am[k] = nullptr;
+            }
+            b->am_rest.clear();
+            return false;
+        }
+        b->rest_nw = fit4 && lo <= 4 ? 4 : lo;
+    }
+    b->am_state = 1;
+    return true;
+}
+
+namespace {
+
+// Launch table of one (direction, FP64 or not, warp count) over every game,
+// or over the games with only[i] != 0.
+kps_status build_table(kps_batch *b, int dir, bool f64, int nw, const std::vector<char> *only, cudaStream_t stream,
+                       BatchTable *tb_out) {
     const int ng = (int)b->games.size();
     std::vector<kps::FastParams> fp(ng);
     std::vector<long long> tstart(ng + 1, 0), in_off(ng), out_off(ng);
@@ -71,6 +136,13 @@ kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t str
     int nc = 0;
     bool any_spill = false;
     for (int i = 0; i < ng; ++i) {
+        in_off[i] = b->off[dir == 0 ? 1 : 0][i];
+        out_off[i] = b->off[dir == 0 ? 0 : 1][i];
+        if (only && !(*only)[i]) {
+            std::memset(&fp[i], 0, sizeof(fp[i]));
+            tstart[i + 1] = tstart[i];
+            continue;
+        }
         kps_game *g = b->games[i];
         const kps::HostGame &h = g->host;
         const kps_game::Tiles *t = nullptr;
@@ -105,8 +177,6 @@ kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t str
         const int nt = (p.n_out + 31) / 32;
         tstart[i + 1] = tstart[i] + nt;
         for (int k = 0; k < nt; ++k) tgame.push_back(i);
-        in_off[i] = b->off[dir == 0 ? 1 : 0][i];
-        out_off[i] = b->off[dir == 0 ? 0 : 1][i];
     }
     if (tstart[ng] > 0x7fffffffLL) return fail(KPS_ENOTSUP, "too many column tiles in one batch");
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
@@ -141,7 +211,36 @@ kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t str
     tb.m.nc = nc;
     tb.m.spill = any_spill ? 1 : 0;
     tb.m.schedule = 0;
+    *tb_out = tb;
+    return KPS_OK;
+}
+
+}  // namespace
+
+kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t stream, const BatchTable **out) {
+    const auto key = std::make_tuple(dir, f64, nw);
+    auto it = b->tables.find(key);
+    if (it != b->tables.end()) {
+        *out = &it->second;
+        return KPS_OK;
+    }
+    BatchTable tb;
+    kps_status st = build_table(b, dir, f64, nw, nullptr, stream, &tb);
+    if (st != KPS_OK) return st;
     *out = &b->tables.emplace(key, tb).first->second;
+    return KPS_OK;
+}
+
+kps_status batch_rest_table(kps_batch *b, int dir, cudaStream_t stream, const BatchTable **out) {
+    auto it = b->rest_tables.find(dir);
+    if (it != b->rest_tables.end()) {
+        *out = &it->second;
+        return KPS_OK;
+    }
+    BatchTable tb;
+    kps_status st = build_table(b, dir, false, b->rest_nw, &b->am_rest, stream, &tb);
+    if (st != KPS_OK) return st;
+    *out = &b->rest_tables.emplace(dir, tb).first->second;
     return KPS_OK;
 }
 
@@ -165,6 +264,10 @@ kps_status batch_default_shape(kps_batch *b, kps_dtype dt, cudaStream_t stream, 
         while (s.nw > 1 && kps::vec_smem_bytes(storage, maxnc, s.nw) > (size_t)kps::max_dyn_smem()) --s.nw;
         s.nw = std::max(1, std::min(s.nw, (maxH + kps::kTile - 1) / kps::kTile));
         s.per_sm = std::max(1, kps::vec_multi_ctas_per_sm(storage, b->k, maxnc, s.nw));
+    } else if (dt == KPS_F32 && batch_staged_ready(b, stream)) {
+        s.kernel = KPS_BATCH_STAGED;
+        s.nw = 4;
+        s.per_sm = std::min(kps::am_ctas_per_sm(b->am[0]), kps::am_ctas_per_sm(b->am[1]));
     } else {
         if (maxnc > 66) return fail(KPS_ENOTSUP, "card count too large for the tensor-memory kernel");
         const int lo = tmem_min_warps(b);
@@ -203,6 +306,29 @@ kps_status batch_matvec(kps_batch *b, int dir, const void *vin, void *vout, kps_
     BatchShape s;
     kps_status st = batch_default_shape(b, dt, stream, &s);
     if (st != KPS_OK) return st;
+    if (s.kernel == KPS_BATCH_STAGED) {
+        cudaError_t e = cudaSuccess;
+        if (s.schedule == 0) e = cudaMemsetAsync(b->ticket, 0, sizeof(int), stream);
+        if (e != cudaSuccess) return cuda_fail(e, "clearing the work-item ticket");
+        e = kps::launch_async_multi(b->am[dir], static_cast<const float *>(vin), static_cast<float *>(vout), b->ticket,
+                                    s.schedule, s.grid, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "launching the staged batched payoff scan");
+        if (b->am_nrest > 0) {
+            // the games the staged kernel leaves: tensor-memory kernel, static stride
+            const BatchTable *t = nullptr;
+            st = batch_rest_table(b, dir, stream, &t);
+            if (st != KPS_OK) return st;
+            kps::MultiParams m = t->m;
+            m.vin = vin;
+            m.vout = vout;
+            m.schedule = 1;
+            const int per = std::max(1, kps::tmem_multi_ctas_per_sm(kps::kStoreF32, b->k, m.nc, m.nw));
+            const int grid = std::max(1, std::min(m.total_tiles, sm_count() * per));
+            e = kps::launch_tmem_multi(m, kps::kStoreF32, b->k, grid, stream);
+            if (e != cudaSuccess) return cuda_fail(e, "launching the batched payoff scan of the remaining games");
+        }
+        return KPS_OK;
+    }
     const BatchTable *t = nullptr;
     st = batch_table(b, dir, dt == KPS_F64, s.nw, stream, &t);
     if (st != KPS_OK) return st;
@@ -255,6 +381,8 @@ kps_status kps_batch_create(kps_game *const *games, int32_t n, kps_batch **out) 
 kps_status kps_batch_destroy(kps_batch *b) {
     if (!b) return KPS_OK;
     for (auto &kv : b->tables) cudaFree(kv.second.blob);
+    for (auto &kv : b->rest_tables) cudaFree(kv.second.blob);
+    for (int k = 0; k < 2; ++k) kps::am_destroy(b->am[k]);
     warm_free(b);
     if (b->ticket) cudaFree(b->ticket);
     delete b;
@@ -303,6 +431,19 @@ kps_status kps_batch_tune(kps_batch *b, kps_dtype dt, void *stream_ptr, kps_batc
             for (int mul = 1; mul <= per; mul = mul == per ? per + 1 : per) {
                 BatchShape s;
                 s.nw = nw;
+                s.per_sm = mul;
+                s.grid = sm_count() * mul;
+                s.schedule = sched;
+                cands.push_back(s);
+            }
+    }
+    if (dt == KPS_F32 && batch_staged_ready(b, stream)) {
+        const int per = std::min(kps::am_ctas_per_sm(b->am[0]), kps::am_ctas_per_sm(b->am[1]));
+        for (int sched = 0; sched < 2; ++sched)
+            for (int mul = 1; mul <= per; ++mul) {
+                BatchShape s;
+                s.kernel = KPS_BATCH_STAGED;
+                s.nw = 4;
                 s.per_sm = mul;
                 s.grid = sm_count() * mul;
                 s.schedule = sched;
@@ -376,6 +517,7 @@ kps_status kps_batch_tune(kps_batch *b, kps_dtype dt, void *stream_ptr, kps_batc
         chosen->warps = bs.nw;
         chosen->grid = bs.grid;
         chosen->schedule = bs.schedule;
+        chosen->kernel = bs.kernel;
         chosen->ms_per_pair = bs.ms;
     }
     return KPS_OK;
@@ -389,6 +531,7 @@ kps_status kps_batch_shape_get(kps_batch *b, kps_dtype dt, kps_batch_shape *shap
     shape->warps = s.nw;
     shape->grid = s.grid;
     shape->schedule = s.schedule;
+    shape->kernel = s.kernel;
     shape->ms_per_pair = s.ms;
     return KPS_OK;
 }
@@ -401,6 +544,22 @@ kps_status kps_batch_shape_set(kps_batch *b, kps_dtype dt, const kps_batch_shape
     if (st != KPS_OK) return st;
     if (shape->schedule != 0 && shape->schedule != 1) return fail(KPS_EINVAL, "schedule must be 0 or 1");
     if (shape->grid < 1) return fail(KPS_EINVAL, "grid must be >= 1");
+    if (shape->kernel != KPS_BATCH_TMEM && shape->kernel != KPS_BATCH_STAGED)
+        return fail(KPS_EINVAL, "kernel must be KPS_BATCH_TMEM or KPS_BATCH_STAGED");
+    if (shape->kernel == KPS_BATCH_STAGED) {
+        if (dt != KPS_F32) return fail(KPS_ENOTSUP, "the staged kernel takes FP32 vectors only");
+        if (shape->warps != 4) return fail(KPS_ENOTSUP, "the staged kernel runs 4 warps per CTA");
+        if (!batch_staged_ready(b, nullptr)) return fail(KPS_ENOTSUP, "a game of the batch does not fit the staged kernel");
+        if (shape->grid > kps::am_grid_cap(b->am[0])) return fail(KPS_ENOTSUP, "the staged kernel runs at most 2 CTAs per SM");
+        BatchShape s = cur;
+        s.kernel = KPS_BATCH_STAGED;
+        s.nw = 4;
+        s.grid = shape->grid;
+        s.schedule = shape->schedule;
+        s.ms = 0.0;
+        b->shape[(int)dt] = s;
+        return KPS_OK;
+    }
     const int nw = shape->warps;
     if (nw < 1 || nw > kps::kMaxWarps) return fail(KPS_EINVAL, "warps must be in 1..8");
     int maxnc = 0;
@@ -416,6 +575,7 @@ kps_status kps_batch_shape_set(kps_batch *b, kps_dtype dt, const kps_batch_shape
                                   : kps::tmem_multi_ctas_per_sm(storage_of(dt), b->k, maxnc, nw);
     if (per < 1) return fail(KPS_ENOTSUP, "warp count needs too much shared memory or too many registers");
     BatchShape s = cur;
+    s.kernel = KPS_BATCH_TMEM;
     s.nw = nw;
     s.grid = shape->grid;
     s.schedule = shape->schedule;

@@ -18,6 +18,7 @@ struct BatchShape {
     int per_sm = 1;     // CTAs per SM
     int grid = 0;       // CTAs of the persistent launch
     int schedule = 0;   // 0 ticket counter, 1 static stride
+    int kernel = 0;     // KPS_BATCH_TMEM or KPS_BATCH_STAGED
     double ms = 0.0;    // tuned time of one A and one A^T launch (0 = untuned)
 };
 
@@ -38,14 +39,26 @@ struct kps_batch {
     std::map<std::tuple<int, bool, int>, kps_abi::BatchTable> tables;
     std::map<int, kps_abi::BatchShape> shape;   // per dtype
     void *warm = nullptr;            // warm-start feature tables (warm.cu)
+    kps::AmPlan *am[2] = {nullptr, nullptr};   // staged FP32 kernel, per direction
+    int am_state = 0;                // 0 not tried, 1 built, -1 it takes no game
+    std::vector<char> am_rest;       // per game: 1 when the staged kernel leaves it to the tensor-memory one
+    int am_nrest = 0;
+    int rest_nw = 0;                 // warps of the tensor-memory launch over those games
+    std::map<int, kps_abi::BatchTable> rest_tables;   // per direction
 };
 
 namespace kps_abi {
 
 kps_status batch_table(kps_batch *b, int dir, bool f64, int nw, cudaStream_t stream, const BatchTable **out);
+// FP32 launch table of the tensor-memory kernel over the games the staged
+// kernel leaves (b->am_rest), b->rest_nw warps.
+kps_status batch_rest_table(kps_batch *b, int dir, cudaStream_t stream, const BatchTable **out);
 kps_status batch_default_shape(kps_batch *b, kps_dtype dt, cudaStream_t stream, BatchShape *out);
 // dir 0: out = A y per game (y player-2 layout, out player-1 layout); dir 1: A^T.
 kps_status batch_matvec(kps_batch *b, int dir, const void *vin, void *vout, kps_dtype dt, cudaStream_t stream);
+// Builds the staged kernel's plans on first use (host work, synchronises
+// `stream`); true when every game fits that kernel.
+bool batch_staged_ready(kps_batch *b, cudaStream_t stream);
 // Frees the warm-start tables of the batch (warm.cu).
 void warm_free(kps_batch *b);
 

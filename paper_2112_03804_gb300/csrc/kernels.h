@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
+#include <vector>
 #include <utility>
 
 namespace kps {
@@ -187,5 +188,32 @@ void tma_destroy(TmaParams *p);
 // One product: out (device, [batch][n_out][hs]) from vin ([batch][n_in][hs]),
 // both 16-byte aligned.
 cudaError_t launch_tma_scan(TmaParams *p, const float *vin, float *vout, int batch, cudaStream_t stream);
+
+// Staged multi-game path (FP32 storage, kernels_amulti.cu): one persistent
+// launch over (game, 32 output sequences) work items of a batch, one vector
+// per game; the warps of a CTA scan chunks of the game's hand order in
+// 16-hand boxes copied by cp.async.  One plan per direction.
+struct AmGameDesc {
+    const HostGame *h;
+    const double *lam_in, *lam_out;   // host, library order
+    int n_out;
+    const int *fcol, *scol;           // device tables of the direction
+    const float *fcoef, *scoef;
+    long long in_off, out_off;        // element offsets in the batch vectors
+};
+struct AmPlan;
+// Builds and uploads the plan (synchronises `stream`) for the games this
+// path takes ((*taken)[i] = 1; the others, e.g. with a tie group longer than
+// 4 hands, get no work items); nullptr when it takes none or on a failure,
+// *why set.  Scratch for `grid_cap` CTAs.
+AmPlan *am_create(const std::vector<AmGameDesc> &games, int grid_cap, cudaStream_t stream, std::vector<char> *taken,
+                  std::string *why);
+void am_destroy(AmPlan *p);
+int am_ctas_per_sm(const AmPlan *p);
+int am_grid_cap(const AmPlan *p);
+// One product over every game; ticket: a device counter cleared before the
+// launch when schedule == 0 (ticket), unused when 1 (static stride).
+cudaError_t launch_async_multi(AmPlan *p, const float *vin, float *vout, int *ticket, int schedule, int grid,
+                               cudaStream_t stream);
 
 }  // namespace kps

@@ -728,7 +728,7 @@ kps_status kps_solver_create(kps_batch *b, kps_dtype dt, kps_solver **out) {
     for (kps_dtype d : {dt, KPS_F64}) {
         BatchShape sh;
         kps_status st = batch_default_shape(b, d, nullptr, &sh);
-        for (int dir = 0; dir < 2 && st == KPS_OK; ++dir) {
+        for (int dir = 0; dir < 2 && st == KPS_OK && sh.kernel == KPS_BATCH_TMEM; ++dir) {
             const BatchTable *t = nullptr;
             st = batch_table(b, dir, d == KPS_F64, sh.nw, nullptr, &t);
         }

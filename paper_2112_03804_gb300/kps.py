@@ -78,7 +78,7 @@ class Info(C.Structure):
 
 
 class BatchShape(C.Structure):
-    _fields_ = [("warps", C.c_int32), ("grid", C.c_int32), ("schedule", C.c_int32),
+    _fields_ = [("warps", C.c_int32), ("grid", C.c_int32), ("schedule", C.c_int32), ("kernel", C.c_int32),
                 ("ms_per_pair", C.c_double)]
 
     def as_dict(self) -> dict:
@@ -411,6 +411,7 @@ class TechniqueB:
 
 
 STATIC_SCRATCH_FLOATS = 4194304
+BATCH_TMEM, BATCH_STAGED = 0, 1
 KERNEL_NAMES = {1: "tma", 2: "tmem", 3: "vec", 4: "fast", 5: "general"}
 
 
@@ -468,8 +469,9 @@ class Batch:
         _check(lib().kps_batch_shape_get(self._h, dtype, C.byref(sh)))
         return sh.as_dict()
 
-    def set_shape(self, dtype: int, warps: int, grid: int, schedule: int):
-        sh = BatchShape(warps, grid, schedule, 0.0)
+    def set_shape(self, dtype: int, warps: int, grid: int, schedule: int, kernel: int = 0):
+        """kernel: BATCH_TMEM (0) or BATCH_STAGED (1, FP32, 4 warps)."""
+        sh = BatchShape(warps, grid, schedule, kernel, 0.0)
         _check(lib().kps_batch_shape_set(self._h, dtype, C.byref(sh)))
 
 

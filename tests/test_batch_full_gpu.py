@@ -6,11 +6,13 @@
   entries of A y and of A^T x, each computed one by one by the FP64 oracle
   of its game, within the FP32 bound (normwise against that game's largest
   output, 1e-5).  Flop-size games (1176 hands) need the spill rows, so the
-  launch runs the spill instantiation.
+  launch runs the spill instantiation.  Checked with the tuned shape and
+  with each of the two batched kernels (the staged one's chunks of 18-19
+  boxes put their last boxes in its scratch area).
 * A batch of river-shaped games with dyadic lambda (beta = 2^20; tests/
   dyadic.py) and small-integer vectors, on every launch shape the batch
-  accepts (warps per CTA, one or two CTAs per SM, ticket or static
-  schedule; kps_batch_shape_set refuses the others): every
+  accepts (both kernels, warps per CTA, one or two CTAs per SM, ticket or
+  static schedule; kps_batch_shape_set refuses the others): every
   FP32 product is exact, so the batched kernels must equal the oracle bit
   for bit, chunks of 1081 to 1176 hands with their tensor-memory region and
   spill rows included.
@@ -52,13 +54,23 @@ def test_full_benchmark_batch_sampled_entries():
         flat, per[p] = _vectors(games, b, p, lambda i, g, inf: synth.simplex_vectors(
             g.sequences(p)["nact"], inf["H"], 1, seed=11 * i + p, dtype=np.float32)[0].astype(np.float64))
         vec[p] = torch.from_numpy(flat.astype(np.float32)).cuda()
-    out = {p: torch.full((int(b.offsets(p)[-1]),), float("nan"), device="cuda") for p in (0, 1)}
     shape = b.tune(kps.F32)
     assert shape["warps"] >= 1
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    # the tuned shape, then each kernel with two CTAs per SM
+    for kernel in (None, kps.BATCH_STAGED, kps.BATCH_TMEM):
+        if kernel is not None:
+            b.set_shape(kps.F32, 4, 2 * sms, 0, kernel)
+            assert b.shape(kps.F32)["kernel"] == kernel
+        _sampled_entries(specs, games, b, vec, per, seed=23 + (kernel or 0))
+
+
+def _sampled_entries(specs, games, b, vec, per, seed):
+    out = {p: torch.full((int(b.offsets(p)[-1]),), float("nan"), device="cuda") for p in (0, 1)}
     b.matvec_A(vec[1], out[0])
     b.matvec_AT(vec[0], out[1])
     torch.cuda.synchronize()
-    rng = np.random.default_rng(23)
+    rng = np.random.default_rng(seed)
     for direction in (0, 1):                     # 0: A y (player-1 rows), 1: A^T x
         res = out[direction].double().cpu().numpy()
         off = b.offsets(direction)
@@ -101,13 +113,14 @@ def test_dyadic_batch_bit_exact_every_shape():
             vcan[:, orders[i]] = per[1 - direction][i]
             want[direction].append((og.matvec_AT(vcan[None]) if direction == 1 else og.matvec_A(vcan[None]))[0])
     ran = 0
-    for warps in range(1, 9):
+    shapes = [(kps.BATCH_TMEM, w) for w in range(1, 9)] + [(kps.BATCH_STAGED, 4)]
+    for kernel, warps in shapes:
         for per_sm in (1, 2):
             for sched in (0, 1):
                 try:
-                    b.set_shape(kps.F32, warps=warps, grid=152 * per_sm, schedule=sched)
+                    b.set_shape(kps.F32, warps=warps, grid=152 * per_sm, schedule=sched, kernel=kernel)
                 except kps.KpsError as e:
-                    assert e.status == kps.ENOTSUP
+                    assert e.status == kps.ENOTSUP and kernel == kps.BATCH_TMEM
                     continue
                 out = {p: torch.full((int(b.offsets(p)[-1]),), float("nan"), device="cuda") for p in (0, 1)}
                 b.matvec_A(vec[1], out[0])
@@ -122,4 +135,4 @@ def test_dyadic_batch_bit_exact_every_shape():
                         got = from_library(res[off[i]:off[i + 1]].reshape(n_out, inf["hs"]), orders[i], inf["H"])
                         assert np.array_equal(got, want[direction][i]), (warps, per_sm, sched, direction, i)
                 ran += 1
-    assert ran >= 4
+    assert ran >= 8

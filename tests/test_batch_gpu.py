@@ -110,7 +110,7 @@ def test_every_warp_count_and_schedule(batch, schedule):
     tried = 0
     for w in range(1, 9):
         try:
-            b.set_shape(kps.F32, w, 3 if schedule else sms, schedule)
+            b.set_shape(kps.F32, w, 3 if schedule else sms, schedule, kps.BATCH_TMEM)
         except kps.KpsError as e:
             assert e.status == kps.ENOTSUP
             continue
@@ -118,7 +118,23 @@ def test_every_warp_count_and_schedule(batch, schedule):
         _check(batch, kps.F32, False)
         _check(batch, kps.F32, True)
     assert tried >= 2
-    b.set_shape(kps.F32, dflt["warps"], dflt["grid"], dflt["schedule"])
+    # the staged kernel takes 4 warps only, and FP32 only
+    for w in (3, 5):
+        with pytest.raises(kps.KpsError) as e:
+            b.set_shape(kps.F32, w, sms, schedule, kps.BATCH_STAGED)
+        assert e.value.status == kps.ENOTSUP
+    with pytest.raises(kps.KpsError) as e:
+        b.set_shape(kps.F64, 4, sms, schedule, kps.BATCH_STAGED)
+    assert e.value.status == kps.ENOTSUP
+    try:
+        b.set_shape(kps.F32, 4, 3 if schedule else 2 * sms, schedule, kps.BATCH_STAGED)
+    except kps.KpsError as e:
+        assert e.status == kps.ENOTSUP      # a game with a tie group over 4 hands
+    else:
+        assert b.shape(kps.F32)["kernel"] == kps.BATCH_STAGED
+        _check(batch, kps.F32, False)
+        _check(batch, kps.F32, True)
+    b.set_shape(kps.F32, dflt["warps"], dflt["grid"], dflt["schedule"], dflt["kernel"])
 
 
 def test_autotuner_picks_a_valid_shape(batch):
@@ -160,3 +176,28 @@ def test_misaligned_and_mixed_batches_rejected(batch):
     with pytest.raises(kps.KpsError) as e:
         b.matvec_A(y[1:], out)     # 4-byte offset: not 16-byte aligned
     assert e.value.status == kps.EINVAL
+
+
+def test_staged_kernel_leaves_long_ties_to_tensor_memory_kernel():
+    """A game with a tie group of 5 hands is not taken by the staged FP32
+    kernel: the batch's default FP32 product runs the staged kernel for the
+    other games and the tensor-memory kernel for that one, and every game
+    matches the oracle."""
+    tied = synth.river_spec(seed=2)
+    s = np.asarray(tied["strength"])
+    order = np.lexsort((np.arange(len(s)), s))
+    s = s.copy()
+    s[order[100:105]] = s[order[100]]
+    tied["strength"] = s.tolist()
+    specs = [synth.river_spec(seed=3), tied, synth.river_spec(seed=4, nboard=4)]
+    bt = {"specs": specs, "games": [kps.Game(x) for x in specs]}
+    bt["oracles"] = [OracleGame(x) for x in specs]
+    bt["orders"] = [library_order(x["strength"]) for x in specs]
+    bt["b"] = kps.Batch(bt["games"])
+    assert bt["b"].shape(kps.F32)["kernel"] == kps.BATCH_STAGED
+    bt["vec"] = {p: [synth.simplex_vectors(og.sequences(p)["nact"], og.H, 1, seed=40 * i + p)[0]
+                     for i, og in enumerate(bt["oracles"])] for p in (0, 1)}
+    bt["want"] = {0: [og.matvec_A(bt["vec"][1][i][None])[0] for i, og in enumerate(bt["oracles"])],
+                  1: [og.matvec_AT(bt["vec"][0][i][None])[0] for i, og in enumerate(bt["oracles"])]}
+    _check(bt, kps.F32, False)
+    _check(bt, kps.F32, True)
