@@ -284,11 +284,18 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = _e2e(g, y, x, oy, ox, stream, args, world)
 
+    # the batched workload, sharded over every rank
+    batched = None
+    if not args.no_secondary:
+        try:
+            batched = measure_batch(args.games, 10, 3, rank, world, dist, solve_iters=50)
+        except Exception as exc:   # reported, never silently dropped
+            batched = {"error": f"{type(exc).__name__}: {exc}"}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec, ran)
+    _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec, ran, batched)
     if dist:
         dist.destroy_process_group()
 
@@ -297,25 +304,36 @@ BATCH_WORKLOAD = ("uneven river endgames in one persistent launch: boards of 3-5
                   "hands), 13-209 terminals, one fp32 vector per game and player")
 
 
-def measure_batch(ngames: int, steps: int, warmup: int, rank: int = 0):
-    """Batched products over `ngames` uneven games (one A and one A^T launch
-    per step, captured in a CUDA graph), launch shape from the autotuner."""
+def measure_batch(ngames: int, steps: int, warmup: int, rank: int = 0, world: int = 1, dist=None,
+                  solve_iters: int = 0):
+    """Batched products over uneven games (one A and one A^T launch per
+    step, captured in a CUDA graph), launch shape from the autotuner.  With
+    `world` ranks the job is ngames * world games, split into contiguous
+    ranges by kps_partition (weights 4 H (n1 + n2) from the specs); each
+    rank builds and runs only its own games, the step time is the maximum
+    over ranks and nothing on the data path communicates.  With solve_iters
+    > 0 every rank then runs the batched FP32 solver on its games for that
+    many iterations and the per-game exploitabilities are gathered in game
+    order (the one collective)."""
     import torch
-    from paper_2112_03804_gb300 import kps, synth
-    specs = synth.batch_specs(seed=4 + 7919 * rank, n=ngames)
-    games = [kps.Game(sp) for sp in specs]
+    from paper_2112_03804_gb300 import kps, shard, synth
+    specs = synth.batch_specs(seed=4, n=ngames * world)
+    bounds = kps.partition(shard.spec_weights(specs), world)
+    lo, hi = int(bounds[rank]), int(bounds[rank + 1])
+    games = [kps.Game(specs[i]) for i in range(lo, hi)]
     b = kps.Batch(games)
     stream = torch.cuda.current_stream()
     off = [b.offsets(p) for p in (0, 1)]
     vec = {}
     for p in (0, 1):
         flat = np.zeros(int(off[p][-1]), dtype=np.float32)
-        for i, g in enumerate(games):
+        for j, g in enumerate(games):
             inf = g.info()
-            v = synth.simplex_vectors(g.sequences(p)["nact"], inf["H"], 1, seed=11 * i + p, dtype=np.float32)[0]
+            v = synth.simplex_vectors(g.sequences(p)["nact"], inf["H"], 1, seed=11 * (lo + j) + p,
+                                      dtype=np.float32)[0]
             w = np.zeros((v.shape[0], inf["hs"]), dtype=np.float32)
             w[:, :inf["H"]] = v
-            flat[off[p][i]:off[p][i + 1]] = w.reshape(-1)
+            flat[off[p][j]:off[p][j + 1]] = w.reshape(-1)
         vec[p] = torch.from_numpy(flat).cuda()
     out = {p: torch.empty(int(off[p][-1]), device="cuda") for p in (0, 1)}
     shape = b.tune(kps.F32, stream)
@@ -333,6 +351,9 @@ def measure_batch(ngames: int, steps: int, warmup: int, rank: int = 0):
     for _ in range(max(warmup, 3)):
         graph.replay()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(steps):
@@ -346,11 +367,35 @@ def measure_batch(ngames: int, steps: int, warmup: int, rank: int = 0):
     for g in games:
         inf = g.info()
         alg += 8.0 * inf["H"] * (inf["n1"] + inf["n2"])
-    return {"workload": BATCH_WORKLOAD, "games": ngames, "matvecs_per_s": 2 * ngames / (ms / 1e3),
-            "ms_per_step": ms, "alg_bytes_per_step": alg, "achieved_gbs": alg / (ms / 1e3) / 1e9,
-            "launch_shape": {k: shape[k] for k in ("kernel", "warps", "grid", "schedule")},
-            "tuned_ms_per_pair": shape["ms_per_pair"], "cuda_graph": True,
-            "l2": "inputs larger than L2" if alg > 2.6e8 else "inputs smaller than L2"}
+    if dist:
+        t = torch.tensor([ms, alg], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms, alg = float(tmax[0]), float(t[1])
+    total = ngames * world
+    res = {"workload": BATCH_WORKLOAD, "games": total, "n_gpus": world,
+           "matvecs_per_s": 2 * total / (ms / 1e3), "ms_per_step": ms, "alg_bytes_per_step": alg,
+           "achieved_gbs": alg / (ms / 1e3) / 1e9,
+           "launch_shape": {k: shape[k] for k in ("kernel", "warps", "grid", "schedule")},
+           "tuned_ms_per_pair": shape["ms_per_pair"], "cuda_graph": True,
+           "sharding": "contiguous game ranges by kps_partition (4 H (n1+n2) per game); no collective on the "
+                       "data path; step time = max over ranks",
+           "l2": "inputs larger than L2" if alg / world > 2.6e8 else "inputs smaller than L2"}
+    if solve_iters > 0:
+        s = kps.Solver(b, kps.F32)
+        s.step(solve_iters)
+        e = torch.zeros(len(games), dtype=torch.float64, device="cuda")
+        s.exploitability(e)
+        torch.cuda.synchronize()
+        local = e.cpu().numpy()
+        allv = shard.gather_scalars(local, np.diff(bounds)) if dist else local
+        res["solver"] = {"iters": solve_iters, "storage": "f32", "games": int(len(allv)),
+                         "expl_pot_mean": float(np.mean(allv)), "expl_pot_max": float(np.max(allv)),
+                         "gathered": "per-game exploitabilities, game order" + (
+                             " (all_gather over ranks)" if dist else "")}
+        s.close()
+    return res
 
 
 def measure_turn(steps: int = 10, warmup: int = 3, seed: int = 2):
@@ -647,12 +692,51 @@ def _e2e(g, y, x, oy, ox, stream, args, world):
         kps.matvec_A_host(g, yh.data_ptr(), oyh.data_ptr(), BATCH, kps.F32, stream)
         kps.matvec_AT_host(g, xh.data_ptr(), oxh.data_ptr(), BATCH, kps.F32, stream)
     e2e_dt = time.perf_counter() - t0
+    h2d = int(yh.numel() * 4 + xh.numel() * 4)
+    d2h = int(oyh.numel() * 4 + oxh.numel() * 4)
+    link = _host_link(yh, y, oyh, oy)
+    # the step moves h2d + d2h bytes over the link; copies in both directions
+    # overlap, so the bound is the concurrent rate
+    bound = mv_per_step / ((h2d + d2h) / (link["both_gbs"] * 1e9))
     return {"value": mv_per_step * ne * world / e2e_dt, "unit": UNIT,
-            "h2d_bytes_per_step": int(yh.numel() * 4 + xh.numel() * 4),
-            "d2h_bytes_per_step": int(oyh.numel() * 4 + oxh.numel() * 4)}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "host_link": dict(link, bound_matvecs_per_s=bound)}
 
 
-def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec, ran):
+def _host_link(hin, din, hout, dout, reps: int = 3):
+    """Pinned host <-> device copy rates (GB/s) measured with CUDA events:
+    host to device alone, device to host alone, and both at once on two
+    streams (what the end-to-end step overlaps)."""
+    import torch
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fn):
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            best = dt if best is None else min(best, dt)
+        return best
+
+    n = hin.numel() * 4
+    t_h2d = timed(lambda: din.copy_(hin, non_blocking=True))
+    t_d2h = timed(lambda: hout.copy_(dout, non_blocking=True))
+
+    def both():
+        with torch.cuda.stream(s1):
+            din.copy_(hin, non_blocking=True)
+        with torch.cuda.stream(s2):
+            hout.copy_(dout, non_blocking=True)
+
+    t_both = timed(both)
+    return {"h2d_gbs": n / t_h2d / 1e9, "d2h_gbs": hout.numel() * 4 / t_d2h / 1e9,
+            "both_gbs": (n + hout.numel() * 4) / t_both / 1e9, "bytes_per_copy": int(n)}
+
+
+def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec, ran, batched=None):
     mv_per_step = 2 * BATCH
     value = mv_per_step * args.steps * world / (ms / 1e3)
     peak, peak_kind = _peaks()
@@ -683,7 +767,8 @@ def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec, ran):
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_seconds)
     if not args.no_secondary:
-        for key, fn in (("batched", lambda: measure_batch(args.games, 10, 3)), ("solver", measure_solver),
+        line["batched"] = batched
+        for key, fn in (("solver", measure_solver),
                         ("technique_b", measure_factors), ("libratus", measure_libratus),
                         ("libratus_solve", lambda: measure_libratus_solve(seeds=(2, 3))),
                         ("turn", measure_turn)):
@@ -700,8 +785,17 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         import torch
-        torch.cuda.set_device(_dist()[2])
-        print(json.dumps(measure_batch(args.games, args.steps, args.warmup)), flush=True)
+        rank, world, local = _dist()
+        torch.cuda.set_device(local)
+        dist = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+        res = measure_batch(args.games, args.steps, args.warmup, rank, world, dist)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        if dist:
+            dist.destroy_process_group()
     elif args.workload == "warmstart":
         import torch
         torch.cuda.set_device(_dist()[2])

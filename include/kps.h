@@ -606,6 +606,17 @@ kps_status kps_tb_matvec(kps_tb *tb, const void *y, void *out, int32_t batch, kp
 /* Thread-local description of the last failure ("" if none). */
 const char *kps_last_error(void);
 
+/* Synchronises `stream` and reports device-side failures of the launches
+ * since the previous call: KPS_ETIMEOUT when a bounded wait of the
+ * TMA-staged kernel (an mbarrier its copies complete; limit 2 s) gave up,
+ * in which case the products of those launches are not valid (the flag is
+ * then cleared and the context stays usable); KPS_ECUDA on a CUDA error.
+ * The wait limit turns a copy that never completes into this status
+ * instead of a hang.  Test hook: with the environment variable
+ * KPS_TEST_STALL_WAIT=1 at launch, one barrier per CTA of that kernel
+ * expects 16 bytes more than its copies bring, so its wait runs out. */
+kps_status kps_device_status(void *stream);
+
 /* Library version string. */
 const char *kps_version(void);
 

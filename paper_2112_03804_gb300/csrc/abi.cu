@@ -796,6 +796,18 @@ kps_status kps_matvec_A_static_scratch(kps_game *g, const void *y, void *out, in
 
 const char *kps_last_error(void) { return g_last_error.c_str(); }
 
+kps_status kps_device_status(void *stream) {
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "synchronising the stream");
+    bool set = false;
+    e = kps::tma_take_error(&set);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device wait flag");
+    if (set)
+        return fail(KPS_ETIMEOUT, "a bounded wait of the TMA-staged kernel gave up: products since the last check "
+                                  "are not valid");
+    return KPS_OK;
+}
+
 const char *kps_version(void) { return "kps 0.1.0 (sm_103a)"; }
 
 }  // extern "C"

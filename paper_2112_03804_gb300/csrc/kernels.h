@@ -188,6 +188,9 @@ void tma_destroy(TmaParams *p);
 // One product: out (device, [batch][n_out][hs]) from vin ([batch][n_in][hs]),
 // both 16-byte aligned.
 cudaError_t launch_tma_scan(TmaParams *p, const float *vin, float *vout, int batch, cudaStream_t stream);
+// Reads and clears the flag the TMA-staged kernel sets when a bounded wait
+// gives up (synchronises the device).
+cudaError_t tma_take_error(bool *set);
 
 // Staged multi-game path (FP32 storage, kernels_amulti.cu): one persistent
 // launch over (game, 32 output sequences) work items of a batch, one vector

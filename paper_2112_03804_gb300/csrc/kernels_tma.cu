@@ -41,9 +41,10 @@
 // C = Tot + 2 S G_before, written into a swizzled box and stored with one
 // cp.async.bulk.tensor per box.  No atomics: results are bit-reproducible.
 //
-// Waits are bounded: a wait that gives up sets *err, the CTA runs to its end
-// without waiting again, waits (bounded) for its copies still in flight and
-// frees its tensor memory.
+// Waits are bounded: a wait that gives up sets *err; the warp scans no
+// further box, the CTA runs to its end without waiting again (its results
+// are not valid), waits (bounded) for its copies still in flight and frees
+// its tensor memory.
 #include "kernels.h"
 #include "game.h"
 #include "scan_records.h"
@@ -54,6 +55,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -69,6 +71,7 @@ struct alignas(128) TmaArgs {
     CUtensorMap tin;               // input  [batch][n_in][H]  fp32, box 16 x 1 x 32, 64-byte swizzle
     CUtensorMap tout;              // output [batch][n_out][hs] fp32, same box
     int H, hs, nc, k, n_out, n_in, batch, nbb, nbox, extra;
+    int stall_test;                // test hook: warp 0's first box expects 16 bytes that never come
     int bchunk[kTmaWarps + 1];     // warp k scans boxes [bchunk[k], bchunk[k+1])
     const int *fcol, *scol;        // per output sequence: its fold / showdown input sequence or -1
     const float *fcoef, *scoef;    // and the payoffs
@@ -276,7 +279,7 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
         const uint32_t bar = bar0 + 8u * (uint32_t)sl;
         const uint32_t dst = ring_s + (uint32_t)(sl * SLOT);
         const int x = kTmaBox * (c.b0 + m);
-        mbar_expect_tx(bar, (uint32_t)(SLOT + kScanBlock));
+        mbar_expect_tx(bar, (uint32_t)(SLOT + kScanBlock) + (P.stall_test && m == 0 && warp == 0 ? 16u : 0u));
         if (HF) tma_load3(dst, &P.tin, x, c.rf, z0, bar);
         if (HS) tma_load3(dst + (HF ? 2048u : 0u), &P.tin, x, c.rs, z0, bar);
         bulk_load(rring_s + (uint32_t)(sl * kScanBlock), P.rscan + (size_t)(c.b0 + m) * kScanBlock, kScanBlock, bar);
@@ -311,6 +314,9 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
             c.ok = __all_sync(kFull, got);
             if (c.ok) nwaited = m + 1;
         }
+        // after a wait gave up, the slot's records (shared-memory offsets)
+        // may never have arrived: scan no further
+        if (!c.ok) break;
         const unsigned char *slot = ring + sl * SLOT;
         float yf[16], ys[16];
 #pragma unroll
@@ -721,6 +727,14 @@ TmaParams *tma_create(const HostGame &h, const double *lam_in, const double *lam
     return p;
 }
 
+cudaError_t tma_take_error(bool *set) {
+    unsigned int v = 0, zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_tma_err, sizeof(v));
+    if (e == cudaSuccess && v) e = cudaMemcpyToSymbol(g_tma_err, &zero, sizeof(zero));
+    *set = v != 0;
+    return e;
+}
+
 void tma_destroy(TmaParams *p) {
     if (!p) return;
     if (p->dev) cudaFree(p->dev);
@@ -751,6 +765,10 @@ cudaError_t launch_tma_scan(TmaParams *pp, const float *vin, float *vout, int ba
     }
     A.batch = batch;
     A.nbb = (batch + 31) / 32;
+    // test hook (KPS_TEST_STALL_WAIT=1): one barrier per CTA never completes,
+    // so that its bounded wait gives up and sets the error flag
+    const char *st = std::getenv("KPS_TEST_STALL_WAIT");
+    A.stall_test = st && std::atoi(st) > 0 ? 1 : 0;
     e = encode3(&A.tin, vin, A.H, A.n_in, batch, A.hs);
     if (e == cudaSuccess) e = encode3(&A.tout, vout, A.hs, A.n_out, batch, A.hs);
     if (e != cudaSuccess) return e;

@@ -102,7 +102,7 @@ EXPORTED = ["kps_sparsify", "kps_game_destroy", "kps_game_info", "kps_game_hands
             "kps_mlp_forward", "kps_mlp_gradients", "kps_mlp_adam", "kps_mlp_state_bytes", "kps_mlp_save",
             "kps_mlp_load",
             "kps_turn_create", "kps_turn_destroy", "kps_turn_info", "kps_turn_offsets", "kps_turn_block",
-            "kps_turn_matvec_A", "kps_turn_matvec_AT", "kps_turn_batch",
+            "kps_turn_matvec_A", "kps_turn_matvec_AT", "kps_turn_batch", "kps_device_status",
             "kps_tb_create", "kps_tb_destroy", "kps_tb_sizes", "kps_tb_export", "kps_tb_matvec",
             "kps_last_error", "kps_version"]
 
@@ -150,6 +150,7 @@ def lib():
         L.kps_turn_matvec_A.argtypes = [P, P, P, C.c_int, P]
         L.kps_turn_matvec_AT.argtypes = [P, P, P, C.c_int, P]
         L.kps_turn_batch.argtypes = [P, C.POINTER(C.c_void_p)]
+        L.kps_device_status.argtypes = [P]
         L.kps_solver_state_bytes.argtypes = [P, C.POINTER(C.c_int64)]
         L.kps_solver_save.argtypes = [P, P, C.c_int64, P]
         L.kps_solver_load.argtypes = [P, P, C.c_int64, P]
@@ -473,6 +474,12 @@ class Batch:
         """kernel: BATCH_TMEM (0) or BATCH_STAGED (1, FP32, 4 warps)."""
         sh = BatchShape(warps, grid, schedule, kernel, 0.0)
         _check(lib().kps_batch_shape_set(self._h, dtype, C.byref(sh)))
+
+
+def device_status(stream=None):
+    """Synchronises `stream`; raises KpsError(ETIMEOUT) when a bounded
+    device wait gave up since the last call (``kps_device_status``)."""
+    _check(lib().kps_device_status(_stream(stream)))
 
 
 def partition(weights, parts: int) -> np.ndarray:

@@ -19,6 +19,31 @@ def game_weights(games) -> np.ndarray:
     return np.array([4 * g.info()["H"] * (g.info()["n1"] + g.info()["n2"]) for g in games], dtype=np.int64)
 
 
+def spec_weights(specs) -> np.ndarray:
+    """The same weights, 4 * H * (n1 + n2), from the specs alone (no game is
+    built): H from the deck, board and hand size, n1 + n2 from one game on a
+    6-card deck per distinct betting configuration (stacks, contributions,
+    bet sizes, raise cap, all-in, menu), since the betting tree does not
+    depend on the cards."""
+    from . import synth
+    trees = {}
+    out = np.zeros(len(specs), dtype=np.int64)
+    for i, s in enumerate(specs):
+        menu = s.get("menu")
+        key = (tuple(float(v) for v in s["stack"]), tuple(float(v) for v in s["contrib0"]),
+               tuple(float(v) for v in s.get("bet_frac", [])), int(s.get("raise_cap", -1)),
+               bool(s.get("allow_allin", False)), repr(menu))
+        if key not in trees:
+            probe = dict(ranks=3, suits=2, cards_per_hand=1, board=[], stack=list(key[0]), contrib0=list(key[1]),
+                         bet_frac=list(key[2]), raise_cap=key[3], allow_allin=key[4], menu=menu,
+                         strength=[0, 1, 2, 3, 4, 5])
+            inf = kps.Game(probe).info()
+            trees[key] = inf["n1"] + inf["n2"]
+        H = synth.num_hands(int(s["ranks"]), int(s["suits"]), len(s.get("board", [])), int(s["cards_per_hand"]))
+        out[i] = 4 * H * trees[key]
+    return out
+
+
 def my_range(weights, rank: int, world: int):
     """[lo, hi) of this rank's games."""
     b = kps.partition(weights, world)

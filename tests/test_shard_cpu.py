@@ -74,3 +74,48 @@ def test_gloo_two_ranks_gather_in_game_order():
     assert lo0 == 0 and hi0 == lo1 and hi1 == 11 and hi0 > 0
     want = [kps.Game(s).info()["nnz_A"] for s in specs]
     assert v0 == want and v1 == want
+
+
+def _solve_worker(rank, world, port, specs, iters, q):
+    import torch.distributed as dist
+    from oracle.oracle import OracleGame
+    from paper_2112_03804_gb300 import shard
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = shard.spec_weights(specs)                 # no game built for the split
+        b = kps.partition(w, world)
+        lo, hi = int(b[rank]), int(b[rank + 1])
+        # each rank solves only its own games (RM+, the FP64 oracle) ...
+        local = [OracleGame(specs[i]).rmplus(iters)[0] for i in range(lo, hi)]
+        # ... and the per-game exploitabilities are the one collective
+        allv = shard.gather_scalars(local, np.diff(b))
+        q.put((rank, lo, hi, allv.tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_ranks_solve_their_games_and_gather_exploitabilities():
+    import socket
+    import torch.multiprocessing as mp
+    from oracle.oracle import OracleGame
+    specs = [synth.micro_spec(seed=20 + k, ranks=4 + k % 2, nboard=2 + k % 2) for k in range(7)]
+    iters = 60
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_solve_worker, args=(r, 2, port, specs, iters, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, lo0, hi0, v0), (_, lo1, hi1, v1) = res
+    assert lo0 == 0 and hi0 == lo1 and hi1 == len(specs) and 0 < hi0 < len(specs)
+    want = [OracleGame(s).rmplus(iters)[0] for s in specs]
+    assert v0 == v1
+    assert v0 == want                      # same games, same arithmetic: bit for bit
+    assert all(v > 0 for v in want)
