@@ -479,7 +479,8 @@ typedef struct kps_mlp kps_mlp;
 /* The network's behavioural strategy at EVERY query of the batch, written
  * into beh1 / beh2 (device FP32, batch layouts) in one fused pass: the first
  * layer from its game, node and hand parts (the game and node parts computed
- * once per game / node), layers 2 and 3 on the tensor cores with BF16
+ * once per game / node), layers 2 and 3 on the tensor cores (tcgen05.mma,
+ * BF16 operands, FP32 accumulators in tensor memory) with BF16
  * activations, the masked softmax, the scatter.  Needs din = KPS_WARM_DIN,
  * width 256, dout <= 16 (KPS_ENOTSUP otherwise).  Allocates temporaries and
  * synchronises `stream`.  Agrees with kps_warm_features + kps_mlp_forward +

@@ -12,6 +12,7 @@
 
 #include "../../include/kps.h"
 #include "abi_internal.h"
+#include "batch_internal.h"
 #include "game.h"
 #include "kernels.h"
 
@@ -799,12 +800,16 @@ const char *kps_last_error(void) { return g_last_error.c_str(); }
 kps_status kps_device_status(void *stream) {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "synchronising the stream");
-    bool set = false;
+    bool set = false, pset = false;
     e = kps::tma_take_error(&set);
-    if (e != cudaSuccess) return cuda_fail(e, "reading the device wait flag");
+    if (e == cudaSuccess) e = predict_take_error(&pset);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device wait flags");
     if (set)
         return fail(KPS_ETIMEOUT, "a bounded wait of the TMA-staged kernel gave up: products since the last check "
                                   "are not valid");
+    if (pset)
+        return fail(KPS_ETIMEOUT, "a bounded wait of the warm-start predictor gave up: its predictions since the "
+                                  "last check are not valid");
     return KPS_OK;
 }
 

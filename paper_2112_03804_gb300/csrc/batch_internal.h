@@ -59,6 +59,9 @@ kps_status batch_matvec(kps_batch *b, int dir, const void *vin, void *vout, kps_
 // Builds the staged kernel's plans on first use (host work, synchronises
 // `stream`); true when every game fits that kernel.
 bool batch_staged_ready(kps_batch *b, cudaStream_t stream);
+// Reads and clears the flag the warm-start predictor sets when a bounded
+// wait gives up (warm.cu; synchronises the device).
+cudaError_t predict_take_error(bool *set);
 // Frees the warm-start tables of the batch (warm.cu).
 void warm_free(kps_batch *b);
 

@@ -164,13 +164,26 @@ __global__ void game_part_kernel(const WarmDev d, float *Gf) {
 
 // ---- fused inference ---------------------------------------------------
 // Layer 1 from its three parts (game and node parts precomputed, the hand
-// part from five rows of W1), layers 2 and 3 on the tensor cores
-// (mma.sync m16n8k16, BF16 operands, FP32 accumulation) with W2^T and W3^T
-// resident in shared memory, activations in shared memory as BF16, then the
-// masked softmax, written straight into the behavioural strategies.
-constexpr int kPR = 128;            // queries per tile (8 warps x 16 rows)
+// part from five rows of W1), layers 2 and 3 on the fifth-generation tensor
+// cores: tcgen05.mma (kind::f16, BF16 operands, FP32 accumulation in tensor
+// memory) for a tile of 128 queries, M = 128, N = 256 (layer 2) and N = 16
+// (layer 3, logits padded), K = 256 in 16 steps of 16.  Both operands are
+// K-major in shared memory without swizzle, in 8-row x 16-byte core
+// matrices: element (r, k) of an operand with K = 256 sits at byte
+//   (r / 8) * 4096 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
+// so core matrices adjacent in K are 128 bytes apart and 8-row groups 4096
+// bytes apart (the descriptors' leading and stride byte offsets).  W2 and W3
+// stay resident in shared memory; the activations of layer 1 are written in
+// that layout, read back from tensor memory after layer 2 (bias, ReLU,
+// BF16) into the same buffer for layer 3, whose 16 logits per row go to the
+// masked softmax, written straight into the behavioural strategies.  One
+// thread issues the MMAs; tcgen05.commit arrives on an mbarrier that the
+// others wait on (bounded: 2 s, then the error flag read by
+// kps_device_status).
+constexpr int kPR = 128;            // queries per tile (M)
 constexpr int kWidth = 256;
-constexpr int kPitchH = kWidth + 8; // BF16 elements per shared row (conflict-free fragments)
+constexpr int kOpRow = 4096;        // bytes between 8-row groups of an operand (K = 256)
+constexpr int kTmemPred = 512;      // columns: layer 2 at 0..255, layer 3 at 256..271
 
 struct RowInfo {
     long long base;                  // batch-vector offset of (player, hand)
@@ -178,23 +191,80 @@ struct RowInfo {
     float pos, tie, mu;
 };
 
-__host__ __device__ constexpr size_t predict_smem_bytes() {
-    return (size_t)(kWidth + kPR + 16) * kPitchH * 2 + kPR * sizeof(RowInfo);
-}
+// Shared memory: W2 [256 rows][K] (128 KB), the activations [128][K]
+// (64 KB), W3 [16][K] (8 KB), the row records, then the barrier and the
+// tensor-memory slot.
+constexpr size_t kOffW2 = 0, kOffH = kOffW2 + (size_t)kWidth / 8 * kOpRow, kOffW3 = kOffH + (size_t)kPR / 8 * kOpRow,
+                 kOffRows = kOffW3 + 2 * (size_t)kOpRow, kOffBar = kOffRows + kPR * sizeof(RowInfo);
+__host__ __device__ constexpr size_t predict_smem_bytes() { return kOffBar + 16 + 128; }
 
-__device__ __forceinline__ void mma_bf16(float *d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1) {
+__device__ __forceinline__ uint32_t op_off(int r, int k) {
+    return (uint32_t)((r >> 3) * kOpRow + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (8-row) byte offsets, the fixed version bits 46-48 = 0b001, no swizzle.
+__device__ __forceinline__ uint64_t op_desc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(kOpRow >> 4) << 32) |
+           (1ull << 46);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
 }
-
-__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
-
-__device__ __forceinline__ void st_pair(__nv_bfloat16 *p, float a, float b) {
-    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void pmbar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool pmbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait (2 s of %globaltimer); false when it gave up.
+__device__ __noinline__ bool pmbar_wait(uint32_t bar, uint32_t parity) {
+    if (pmbar_try(bar, parity)) return true;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (int i = 0; i < (1 << 26); ++i) {
+        if (pmbar_try(bar, parity)) return true;
+        if ((i & 63) == 63) {
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t - t0 > 2000000000ull) break;
+        }
+    }
+    return false;
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]), "=f"(r[8]),
+          "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(r[0]), "+f"(r[1]), "+f"(r[2]), "+f"(r[3]), "+f"(r[4]), "+f"(r[5]), "+f"(r[6]), "+f"(r[7]),
+                   "+f"(r[8]), "+f"(r[9]), "+f"(r[10]), "+f"(r[11]), "+f"(r[12]), "+f"(r[13]), "+f"(r[14]), "+f"(r[15])::"memory");
 }
 
 struct PredictArgs {
@@ -208,30 +278,52 @@ struct PredictArgs {
     int dout;
     long long nq;
     float *beh1, *beh2;
+    unsigned int *err;               // set when a wait gives up
 };
 
+__device__ unsigned int g_predict_err;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
 __global__ void __launch_bounds__(256, 1) predict_kernel(const PredictArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __nv_bfloat16 *W2t = reinterpret_cast<__nv_bfloat16 *>(smem_raw);        // [n][k]
-    __nv_bfloat16 *Hs = W2t + (size_t)kWidth * kPitchH;                       // [row][k]
-    __nv_bfloat16 *W3t = Hs + (size_t)kPR * kPitchH;                          // [n < 16][k]
-    RowInfo *rows = reinterpret_cast<RowInfo *>(W3t + (size_t)16 * kPitchH);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *W2s = smem_raw + kOffW2, *Hs = smem_raw + kOffH, *W3s = smem_raw + kOffW3;
+    RowInfo *rows = reinterpret_cast<RowInfo *>(smem_raw + kOffRows);
+    const uint32_t bar = smem_addr(smem_raw + kOffBar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_raw + kOffBar + 8);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int g = lane >> 2, t = lane & 3;
+    // W2 and W3 as B operands: row n of B is output column n, K contiguous
     for (int i = tid; i < kWidth * kWidth; i += blockDim.x) {
         const int k = i / kWidth, n = i % kWidth;
-        W2t[n * kPitchH + k] = a.W2[i];
+        *reinterpret_cast<__nv_bfloat16 *>(W2s + op_off(n, k)) = a.W2[i];
     }
     for (int i = tid; i < kWidth * 16; i += blockDim.x) {
         const int k = i / 16, n = i % 16;
-        W3t[n * kPitchH + k] = n < a.dout ? a.W3[k * a.dout + n] : __float2bfloat16_rn(0.f);
+        *reinterpret_cast<__nv_bfloat16 *>(W3s + op_off(n, k)) =
+            n < a.dout ? a.W3[k * a.dout + n] : __float2bfloat16_rn(0.f);
     }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                     "r"(kTmemPred));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) pmbar_init(bar);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;   // this warp's tensor-memory lanes
     // this thread's column of the hand part of layer 1
     const int j = tid;
     const float wpos = __bfloat162float(a.W1h[0 * kWidth + j]), wtie = __bfloat162float(a.W1h[1 * kWidth + j]),
                 wmu = __bfloat162float(a.W1h[2 * kWidth + j]), bias1 = a.b1[j];
     const __nv_bfloat16 *Wc = a.W1h + 4 * kWidth;
-    __syncthreads();
+    uint32_t phase = 0;
+    bool ok = true;
     const long long ntiles = (a.nq + kPR - 1) / kPR;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         if (tid < kPR) {
@@ -260,7 +352,7 @@ __global__ void __launch_bounds__(256, 1) predict_kernel(const PredictArgs a) {
             rows[tid] = ri;
         }
         __syncthreads();
-        // layer 1: column j of every row
+        // layer 1: column j of every row, written as BF16 in the A layout
         for (int r = 0; r < kPR; ++r) {
             const RowInfo &ri = rows[r];
             float z = 0.f;
@@ -270,88 +362,92 @@ __global__ void __launch_bounds__(256, 1) predict_kernel(const PredictArgs a) {
                 if (ri.cb >= 0) z += __bfloat162float(Wc[ri.cb * kWidth + j]);
                 z = fmaxf(z, 0.f);
             }
-            Hs[r * kPitchH + j] = __float2bfloat16_rn(z);
+            *reinterpret_cast<__nv_bfloat16 *>(Hs + op_off(r, j)) = __float2bfloat16_rn(z);
         }
+        // the activations (generic writes) before the tensor cores read them;
+        // the previous tile's tensor-memory loads before this tile's MMAs
+        fence_async_smem();
+        tc_fence_before();
         __syncthreads();
-        // layer 2: this warp's 16 rows x 256 columns
-        const int r0 = warp * 16;
-        float acc[32][4];
-#pragma unroll
-        for (int n = 0; n < 32; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+        tc_fence_after();
+        // layer 2: D[0..255] = H (128 x 256) x W2 (256 x 256)
+        if (tid == 0) {
+            const uint32_t ha = smem_addr(Hs), wa = smem_addr(W2s);
+            for (int s = 0; s < kWidth / 16; ++s)
+                mma_f16(tbase, op_desc(ha + 256u * s), op_desc(wa + 256u * s), mma_idesc(kPR, kWidth), s > 0);
+            mma_commit(bar);
+        }
+        if (ok) ok = pmbar_wait(bar, phase);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) break;
+        tc_fence_after();
+        // bias, ReLU, BF16, back into the A layout: warp w has rows 32 (w & 3)
+        // .. + 31 and columns 128 (w >> 2) .. + 127
+        {
+            const int r = 32 * (warp & 3) + lane, c0 = 128 * (warp >> 2);
 #pragma unroll 1
-        for (int k0 = 0; k0 < kWidth; k0 += 16) {
-            const uint32_t a0 = ld_pair(Hs + (r0 + g) * kPitchH + k0 + 2 * t);
-            const uint32_t a1 = ld_pair(Hs + (r0 + g + 8) * kPitchH + k0 + 2 * t);
-            const uint32_t a2 = ld_pair(Hs + (r0 + g) * kPitchH + k0 + 2 * t + 8);
-            const uint32_t a3 = ld_pair(Hs + (r0 + g + 8) * kPitchH + k0 + 2 * t + 8);
+            for (int cb = 0; cb < 8; ++cb) {
+                const int c = c0 + 16 * cb;
+                float v[16];
+                tc_ld16(tbase + tlane + (uint32_t)c, v);
+                uint32_t w[8];
 #pragma unroll
-            for (int n = 0; n < 32; ++n) {
-                const uint32_t b0 = ld_pair(W2t + (8 * n + g) * kPitchH + k0 + 2 * t);
-                const uint32_t b1 = ld_pair(W2t + (8 * n + g) * kPitchH + k0 + 2 * t + 8);
-                mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
+                for (int i = 0; i < 8; ++i)
+                    w[i] = pack_bf16(fmaxf(v[2 * i] + a.b2[c + 2 * i], 0.f), fmaxf(v[2 * i + 1] + a.b2[c + 2 * i + 1], 0.f));
+                *reinterpret_cast<uint4 *>(Hs + op_off(r, c)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4 *>(Hs + op_off(r, c + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
             }
         }
-        __syncwarp();
-#pragma unroll
-        for (int n = 0; n < 32; ++n) {
-            const int c = 8 * n + 2 * t;
-            const float bb0 = a.b2[c], bb1 = a.b2[c + 1];
-            st_pair(Hs + (r0 + g) * kPitchH + c, fmaxf(acc[n][0] + bb0, 0.f), fmaxf(acc[n][1] + bb1, 0.f));
-            st_pair(Hs + (r0 + g + 8) * kPitchH + c, fmaxf(acc[n][2] + bb0, 0.f), fmaxf(acc[n][3] + bb1, 0.f));
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // layer 3: D[256..271] = H2 (128 x 256) x W3 (256 x 16)
+        if (tid == 0) {
+            const uint32_t ha = smem_addr(Hs), wa = smem_addr(W3s);
+            for (int s = 0; s < kWidth / 16; ++s)
+                mma_f16(tbase + 256u, op_desc(ha + 256u * s), op_desc(wa + 256u * s), mma_idesc(kPR, 16), s > 0);
+            mma_commit(bar);
         }
-        __syncwarp();
-        // layer 3: 16 rows x 16 (padded) logits
-        float z3[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-#pragma unroll 4
-        for (int k0 = 0; k0 < kWidth; k0 += 16) {
-            const uint32_t a0 = ld_pair(Hs + (r0 + g) * kPitchH + k0 + 2 * t);
-            const uint32_t a1 = ld_pair(Hs + (r0 + g + 8) * kPitchH + k0 + 2 * t);
-            const uint32_t a2 = ld_pair(Hs + (r0 + g) * kPitchH + k0 + 2 * t + 8);
-            const uint32_t a3 = ld_pair(Hs + (r0 + g + 8) * kPitchH + k0 + 2 * t + 8);
-#pragma unroll
-            for (int n = 0; n < 2; ++n) {
-                const uint32_t b0 = ld_pair(W3t + (8 * n + g) * kPitchH + k0 + 2 * t);
-                const uint32_t b1 = ld_pair(W3t + (8 * n + g) * kPitchH + k0 + 2 * t + 8);
-                mma_bf16(z3[n], a0, a1, a2, a3, b0, b1);
-            }
-        }
-        // masked softmax of rows r0 + g and r0 + g + 8 across the 4 lanes of a row
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const RowInfo &ri = rows[r0 + g + 8 * half];
-            const int cols[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
-            float v[4];
-            v[0] = z3[0][2 * half];
-            v[1] = z3[0][2 * half + 1];
-            v[2] = z3[1][2 * half];
-            v[3] = z3[1][2 * half + 1];
-            float mx = -INFINITY;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                v[i] += cols[i] < a.dout ? a.b3[cols[i]] : 0.f;
-                if (cols[i] < ri.nact) mx = fmaxf(mx, v[i]);
-            }
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-            float e[4], s = 0.f;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                e[i] = cols[i] < ri.nact ? __expf(v[i] - mx) : 0.f;
-                s += e[i];
-            }
-            s += __shfl_xor_sync(0xffffffffu, s, 1);
-            s += __shfl_xor_sync(0xffffffffu, s, 2);
+        if (ok) ok = pmbar_wait(bar, phase);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) break;
+        tc_fence_after();
+        // masked softmax of row 32 w + lane over its first nact logits
+        if (warp < 4) {
+            const int r = 32 * warp + lane;
+            float z[16];
+            tc_ld16(tbase + tlane + 256u, z);
+            const RowInfo &ri = rows[r];
             if (ri.nact > 0) {
+                float mx = -INFINITY;
+#pragma unroll
+                for (int n = 0; n < 16; ++n) {
+                    z[n] += n < a.dout ? a.b3[n] : 0.f;
+                    if (n < ri.nact) mx = fmaxf(mx, z[n]);
+                }
+                float e[16], s = 0.f;
+#pragma unroll
+                for (int n = 0; n < 16; ++n) {
+                    e[n] = n < ri.nact ? __expf(z[n] - mx) : 0.f;
+                    s += e[n];
+                }
                 float *beh = ri.player == 0 ? a.beh1 : a.beh2;
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (cols[i] < ri.nact) beh[ri.base + (long long)(ri.s0 + cols[i]) * ri.hs] = e[i] / s;
+                for (int n = 0; n < 16; ++n)
+                    if (n < ri.nact) beh[ri.base + (long long)(ri.s0 + n) * ri.hs] = e[n] / s;
             }
         }
+        tc_fence_before();
         __syncthreads();
+        tc_fence_after();
     }
+    if (!ok && tid == 0) atomicExch(a.err, 1u);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemPred));
 }
-
 }  // namespace
 
 // Device tables of a batch's warm-start features (built on first use).
@@ -362,6 +458,14 @@ struct WarmTables {
 };
 
 namespace kps_abi {
+
+cudaError_t predict_take_error(bool *set) {
+    unsigned int v = 0, zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_predict_err, sizeof(v));
+    if (e == cudaSuccess && v) e = cudaMemcpyToSymbol(g_predict_err, &zero, sizeof(zero));
+    *set = v != 0;
+    return e;
+}
 
 void warm_free(kps_batch *b) {
     if (b->warm) {
@@ -591,13 +695,16 @@ kps_status kps_warm_predict(kps_batch *b, kps_mlp *m, float *beh1, float *beh2, 
         a.nq = t->nq;
         a.beh1 = beh1;
         a.beh2 = beh2;
+        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&a.err), g_predict_err);
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const long long ntiles = (t->nq + kPR - 1) / kPR;
         const int grid = (int)std::min<long long>(ntiles, sms);
-        predict_kernel<<<grid, 256, predict_smem_bytes(), s>>>(a);
-        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            predict_kernel<<<grid, 256, predict_smem_bytes(), s>>>(a);
+            e = cudaGetLastError();
+        }
     }
     // the temporaries are released after the work that reads them
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
