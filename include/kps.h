@@ -225,10 +225,12 @@ typedef struct kps_batch kps_batch;
 /* Multi-game kernels (kps_batch_shape.kernel):
  *   KPS_BATCH_TMEM    tensor-memory scan, 32-column tiles, 1-8 warps (every
  *                     storage type; FP64 runs its vector-register variant);
- *   KPS_BATCH_STAGED  FP32 only: 4 warps per CTA scan chunks of a game's
- *                     hand order in 16-hand boxes staged by cp.async, with
- *                     per-box hand records (games whose tie groups have at
- *                     most 4 hands and whose chunks fit 24 boxes). */
+ *   KPS_BATCH_STAGED  FP32, BF16 or FP16 storage (FP32 arithmetic): 4 warps
+ *                     per CTA scan chunks of a game's hand order in 16-hand
+ *                     boxes staged by cp.async, with per-box hand records
+ *                     (games whose tie groups have at most 4 hands and whose
+ *                     chunks fit 24 boxes; the others run on the
+ *                     tensor-memory kernel in a second launch). */
 #define KPS_BATCH_TMEM 0
 #define KPS_BATCH_STAGED 1
 
@@ -259,7 +261,7 @@ kps_status kps_batch_tune(kps_batch *batch, kps_dtype dt, void *stream, kps_batc
 kps_status kps_batch_shape_get(kps_batch *batch, kps_dtype dt, kps_batch_shape *shape);
 /* Sets the launch shape for `dt` (ms_per_pair ignored).  Errors: KPS_EINVAL
  * (out of range), KPS_ENOTSUP (warp count the games do not fit; the staged
- * kernel for another dtype than FP32, with other than 4 warps, more than 2
+ * kernel for FP64, with other than 4 warps, more than 2
  * CTAs per SM, or for games it does not take). */
 kps_status kps_batch_shape_set(kps_batch *batch, kps_dtype dt, const kps_batch_shape *shape);
 

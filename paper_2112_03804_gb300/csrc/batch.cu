@@ -264,7 +264,7 @@ kps_status batch_default_shape(kps_batch *b, kps_dtype dt, cudaStream_t stream, 
         while (s.nw > 1 && kps::vec_smem_bytes(storage, maxnc, s.nw) > (size_t)kps::max_dyn_smem()) --s.nw;
         s.nw = std::max(1, std::min(s.nw, (maxH + kps::kTile - 1) / kps::kTile));
         s.per_sm = std::max(1, kps::vec_multi_ctas_per_sm(storage, b->k, maxnc, s.nw));
-    } else if (dt == KPS_F32 && batch_staged_ready(b, stream)) {
+    } else if (dt != KPS_F64 && batch_staged_ready(b, stream)) {
         s.kernel = KPS_BATCH_STAGED;
         s.nw = 4;
         s.per_sm = std::min(kps::am_ctas_per_sm(b->am[0]), kps::am_ctas_per_sm(b->am[1]));
@@ -310,8 +310,7 @@ kps_status batch_matvec(kps_batch *b, int dir, const void *vin, void *vout, kps_
         cudaError_t e = cudaSuccess;
         if (s.schedule == 0) e = cudaMemsetAsync(b->ticket, 0, sizeof(int), stream);
         if (e != cudaSuccess) return cuda_fail(e, "clearing the work-item ticket");
-        e = kps::launch_async_multi(b->am[dir], static_cast<const float *>(vin), static_cast<float *>(vout), b->ticket,
-                                    s.schedule, s.grid, stream);
+        e = kps::launch_async_multi(b->am[dir], storage_of(dt), vin, vout, b->ticket, s.schedule, s.grid, stream);
         if (e != cudaSuccess) return cuda_fail(e, "launching the staged batched payoff scan");
         if (b->am_nrest > 0) {
             // the games the staged kernel leaves: tensor-memory kernel, static stride
@@ -322,9 +321,9 @@ kps_status batch_matvec(kps_batch *b, int dir, const void *vin, void *vout, kps_
             m.vin = vin;
             m.vout = vout;
             m.schedule = 1;
-            const int per = std::max(1, kps::tmem_multi_ctas_per_sm(kps::kStoreF32, b->k, m.nc, m.nw));
+            const int per = std::max(1, kps::tmem_multi_ctas_per_sm(storage_of(dt), b->k, m.nc, m.nw));
             const int grid = std::max(1, std::min(m.total_tiles, sm_count() * per));
-            e = kps::launch_tmem_multi(m, kps::kStoreF32, b->k, grid, stream);
+            e = kps::launch_tmem_multi(m, storage_of(dt), b->k, grid, stream);
             if (e != cudaSuccess) return cuda_fail(e, "launching the batched payoff scan of the remaining games");
         }
         return KPS_OK;
@@ -437,7 +436,7 @@ kps_status kps_batch_tune(kps_batch *b, kps_dtype dt, void *stream_ptr, kps_batc
                 cands.push_back(s);
             }
     }
-    if (dt == KPS_F32 && batch_staged_ready(b, stream)) {
+    if (dt != KPS_F64 && batch_staged_ready(b, stream)) {
         const int per = std::min(kps::am_ctas_per_sm(b->am[0]), kps::am_ctas_per_sm(b->am[1]));
         for (int sched = 0; sched < 2; ++sched)
             for (int mul = 1; mul <= per; ++mul) {
@@ -547,7 +546,7 @@ kps_status kps_batch_shape_set(kps_batch *b, kps_dtype dt, const kps_batch_shape
     if (shape->kernel != KPS_BATCH_TMEM && shape->kernel != KPS_BATCH_STAGED)
         return fail(KPS_EINVAL, "kernel must be KPS_BATCH_TMEM or KPS_BATCH_STAGED");
     if (shape->kernel == KPS_BATCH_STAGED) {
-        if (dt != KPS_F32) return fail(KPS_ENOTSUP, "the staged kernel takes FP32 vectors only");
+        if (dt == KPS_F64) return fail(KPS_ENOTSUP, "the staged kernel takes FP32, BF16 or FP16 vectors");
         if (shape->warps != 4) return fail(KPS_ENOTSUP, "the staged kernel runs 4 warps per CTA");
         if (!batch_staged_ready(b, nullptr)) return fail(KPS_ENOTSUP, "a game of the batch does not fit the staged kernel");
         if (shape->grid > kps::am_grid_cap(b->am[0])) return fail(KPS_ENOTSUP, "the staged kernel runs at most 2 CTAs per SM");

@@ -192,7 +192,8 @@ cudaError_t launch_tma_scan(TmaParams *p, const float *vin, float *vout, int bat
 // gives up (synchronises the device).
 cudaError_t tma_take_error(bool *set);
 
-// Staged multi-game path (FP32 storage, kernels_amulti.cu): one persistent
+// Staged multi-game path (FP32, BF16 or FP16 storage, kStore*; FP32
+// arithmetic; kernels_amulti.cu): one persistent
 // launch over (game, 32 output sequences) work items of a batch, one vector
 // per game; the warps of a CTA scan chunks of the game's hand order in
 // 16-hand boxes copied by cp.async.  One plan per direction.
@@ -216,7 +217,7 @@ int am_ctas_per_sm(const AmPlan *p);
 int am_grid_cap(const AmPlan *p);
 // One product over every game; ticket: a device counter cleared before the
 // launch when schedule == 0 (ticket), unused when 1 (static stride).
-cudaError_t launch_async_multi(AmPlan *p, const float *vin, float *vout, int *ticket, int schedule, int grid,
-                               cudaStream_t stream);
+cudaError_t launch_async_multi(AmPlan *p, int storage, const void *vin, void *vout, int *ticket, int schedule,
+                               int grid, cudaStream_t stream);
 
 }  // namespace kps

@@ -1,5 +1,6 @@
 // Kronecker-form payoff products of many games in one persistent launch
-// (sm_103a), FP32, one vector per game and player.
+// (sm_103a), one vector per game and player, FP32 / BF16 / FP16 storage with
+// FP32 arithmetic.
 //
 // Mathematics as in kernels_tma.cu (Prop. 1, Sec. 3):
 //   out / lambda_out = K_F(w) + S (2 Lo_ord(b) - TB(b) + TA(b)),
@@ -31,6 +32,8 @@
 #include "game.h"
 #include "scan_records.h"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -68,8 +71,8 @@ struct AmArgs {
     const AmGame *games;
     const int2 *items;             // (game, first output sequence)
     int nitems, nc, schedule;
-    const float *vin;
-    float *vout;
+    const void *vin;               // element type: the kernel's storage type
+    void *vout;
     float *scratch;                // [grid][4 warps][kMaxExtra][16][32]
     int *ticket;
 };
@@ -133,9 +136,65 @@ __device__ __forceinline__ TmaFinRec ldg_fin(const TmaFinRec *p) {
     return r;
 }
 
+// Storage types: a 16-byte chunk holds 4 FP32 or 8 BF16 / FP16 values.
+template <typename T> struct Store;
+template <> struct Store<float> {
+    static constexpr int kPer = 4;
+    __device__ static void load(const unsigned char *p, float *v) {
+        const float4 u = *reinterpret_cast<const float4 *>(p);
+        v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+    }
+    __device__ static uint4 pack(const float *v) {
+        return make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3]));
+    }
+};
+template <> struct Store<__nv_bfloat16> {
+    static constexpr int kPer = 8;
+    __device__ static void load(const unsigned char *p, float *v) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(p);
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            v[2 * i] = __uint_as_float(w[i] << 16);
+            v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    }
+    __device__ static uint4 pack(const float *v) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+            w[i] = *reinterpret_cast<uint32_t *>(&h);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+};
+template <> struct Store<__half> {
+    static constexpr int kPer = 8;
+    __device__ static void load(const unsigned char *p, float *v) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(p);
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[i]));
+            v[2 * i] = f.x;
+            v[2 * i + 1] = f.y;
+        }
+    }
+    __device__ static uint4 pack(const float *v) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+            w[i] = *reinterpret_cast<uint32_t *>(&h);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+};
+
 // One work item, one warp: scan of the warp's chunk, combination of the
 // four chunks (two CTA barriers), finishing pass.
-template <int K2>
+template <typename T, int K2>
 __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int sigma0, unsigned char *sm,
                                         uint32_t tmem, float *xs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -147,9 +206,10 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
     const float F = rf >= 0 ? G.fcoef[sigma] : 0.f;
     const float S = rs >= 0 ? G.scoef[sigma] : 0.f;
     const float S2 = 2.f * S;
-    const float *vin = P.vin + G.in_off;
-    const float *pa = vin + (size_t)(rf >= 0 ? rf : 0) * hs;
-    const float *pb = vin + (size_t)(rs >= 0 ? rs : 0) * hs;
+    constexpr int NQ = 16 / Store<T>::kPer;   // 16-byte chunks per 16-hand row segment
+    const T *vin = static_cast<const T *>(P.vin) + G.in_off;
+    const T *pa = vin + (size_t)(rf >= 0 ? rf : 0) * hs;
+    const T *pb = vin + (size_t)(rs >= 0 ? rs : 0) * hs;
     const uint32_t na = rf >= 0 ? 16u : 0u, nbytes_b = rs >= 0 ? 16u : 0u;
     unsigned char *ring = sm + am_ring_off(warp);
     const uint32_t ring_s = smem_u32(ring);
@@ -169,9 +229,9 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
             const int x = kTmaBox * (b0 + m);
             const uint32_t dst = ring_s + (uint32_t)(sl * kSlot) + 16u * (uint32_t)lane;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int h0 = x + 4 * q;
-                const bool in = h0 < hs;   // hs is a multiple of 8: a chunk of 4 is all in or all out
+            for (int q = 0; q < NQ; ++q) {
+                const int h0 = x + Store<T>::kPer * q;
+                const bool in = h0 < hs;   // hs is a multiple of 8: a chunk is all in or all out
                 cp16(dst + 512u * q, in ? pa + h0 : pa, in ? na : 0u);
                 cp16(dst + 2048u + 512u * q, in ? pb + h0 : pb, in ? nbytes_b : 0u);
             }
@@ -205,11 +265,9 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
         const unsigned char *slot = ring + sl * kSlot + 16 * lane;
         float yf[16], ys[16];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 u = *reinterpret_cast<const float4 *>(slot + 512 * q);
-            const float4 v = *reinterpret_cast<const float4 *>(slot + 2048 + 512 * q);
-            yf[4 * q] = u.x; yf[4 * q + 1] = u.y; yf[4 * q + 2] = u.z; yf[4 * q + 3] = u.w;
-            ys[4 * q] = v.x; ys[4 * q + 1] = v.y; ys[4 * q + 2] = v.z; ys[4 * q + 3] = v.w;
+        for (int q = 0; q < NQ; ++q) {
+            Store<T>::load(slot + 512 * q, yf + Store<T>::kPer * q);
+            Store<T>::load(slot + 2048 + 512 * q, ys + Store<T>::kPer * q);
         }
         const unsigned char *rsb = rring + sl * kScanBlock;
         const uint32_t tw0 = reinterpret_cast<const uint32_t *>(rsb + 256)[0];
@@ -322,19 +380,19 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
     }
     float Cw;
     {
-        float T = 0.f, gb = 0.f;
+        float tall = 0.f, gb = 0.f;
 #pragma unroll
         for (int k = 0; k < kTmaWarps; ++k) {
-            T += sums[(1 * kTmaWarps + k) * 32 + lane];
+            tall += sums[(1 * kTmaWarps + k) * 32 + lane];
             if (k < warp) gb += sums[(0 * kTmaWarps + k) * 32 + lane];
         }
-        Cw = T + S2 * gb;
+        Cw = tall + S2 * gb;
     }
     __syncthreads();
 
     // finishing: out = lambda_out (partial + C - Q[c1] - Q[c2])
     const unsigned char *qb = ring + 4 * lane;
-    float *orow = P.vout + G.out_off + (size_t)(act ? sigma : 0) * hs;
+    T *orow = static_cast<T *>(P.vout) + G.out_off + (size_t)(act ? sigma : 0) * hs;
     float cur[16], nxt[16];
     auto load_box = [&](int m, float *r) {
         if (m < 16) {
@@ -370,10 +428,9 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
         if (act) {
             const int x = kTmaBox * (b0 + m);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (x + 4 * q < hs)
-                    *reinterpret_cast<float4 *>(orow + x + 4 * q) =
-                        make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+            for (int q = 0; q < NQ; ++q)
+                if (x + Store<T>::kPer * q < hs)
+                    *reinterpret_cast<uint4 *>(orow + x + Store<T>::kPer * q) = Store<T>::pack(o + Store<T>::kPer * q);
         }
         if (m + 1 < nb) {
             tm_wait_ld16(nxt);
@@ -384,7 +441,7 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
     __syncwarp();
 }
 
-template <int K2>
+template <typename T, int K2>
 __global__ void __launch_bounds__(128, 2) async_multi_kernel(const __grid_constant__ AmArgs P) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int warp = threadIdx.x >> 5;
@@ -411,7 +468,7 @@ __global__ void __launch_bounds__(128, 2) async_multi_kernel(const __grid_consta
         }
         if (item >= P.nitems) break;
         const int2 it = P.items[item];
-        am_item<K2>(P, P.games[it.x], it.y, sm, tmem, xs);
+        am_item<T, K2>(P, P.games[it.x], it.y, sm, tmem, xs);
         // the next ticket is written only after every thread has read this one
         // (am_item ends its combination with a CTA barrier)
     }
@@ -571,8 +628,8 @@ int am_ctas_per_sm(const AmPlan *p) {
     return std::max(0, std::min(2, by_smem));
 }
 
-cudaError_t launch_async_multi(AmPlan *p, const float *vin, float *vout, int *ticket, int schedule, int grid,
-                               cudaStream_t stream) {
+cudaError_t launch_async_multi(AmPlan *p, int storage, const void *vin, void *vout, int *ticket, int schedule,
+                               int grid, cudaStream_t stream) {
     // the scratch area holds the chunk boxes past tensor memory of grid_cap CTAs
     if (grid <= 0 || grid > p->grid_cap) return cudaErrorInvalidValue;
     AmArgs a = p->a;
@@ -583,7 +640,15 @@ cudaError_t launch_async_multi(AmPlan *p, const float *vin, float *vout, int *ti
     a.schedule = schedule;
     if (a.nitems == 0) return cudaSuccess;
     const size_t smem = am_launch_smem(a.nc);
-    auto fn = p->k == 1 ? async_multi_kernel<1> : async_multi_kernel<2>;
+    void (*fn)(AmArgs);
+    switch (storage) {
+        case kStoreF32: fn = p->k == 1 ? async_multi_kernel<float, 1> : async_multi_kernel<float, 2>; break;
+        case kStoreBF16:
+            fn = p->k == 1 ? async_multi_kernel<__nv_bfloat16, 1> : async_multi_kernel<__nv_bfloat16, 2>;
+            break;
+        case kStoreF16: fn = p->k == 1 ? async_multi_kernel<__half, 1> : async_multi_kernel<__half, 2>; break;
+        default: return cudaErrorInvalidValue;
+    }
     cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, 32 * kTmaWarps, smem, stream>>>(a);

@@ -118,7 +118,7 @@ def test_every_warp_count_and_schedule(batch, schedule):
         _check(batch, kps.F32, False)
         _check(batch, kps.F32, True)
     assert tried >= 2
-    # the staged kernel takes 4 warps only, and FP32 only
+    # the staged kernel runs 4 warps only, and not FP64
     for w in (3, 5):
         with pytest.raises(kps.KpsError) as e:
             b.set_shape(kps.F32, w, sms, schedule, kps.BATCH_STAGED)
@@ -179,10 +179,10 @@ def test_misaligned_and_mixed_batches_rejected(batch):
 
 
 def test_staged_kernel_leaves_long_ties_to_tensor_memory_kernel():
-    """A game with a tie group of 5 hands is not taken by the staged FP32
-    kernel: the batch's default FP32 product runs the staged kernel for the
-    other games and the tensor-memory kernel for that one, and every game
-    matches the oracle."""
+    """A game with a tie group of 5 hands is not taken by the staged kernel:
+    the batch's default FP32 / BF16 / FP16 products run the staged kernel for
+    the other games and the tensor-memory kernel for that one, and every game
+    matches the oracle (half precision: on the rounded inputs)."""
     tied = synth.river_spec(seed=2)
     s = np.asarray(tied["strength"])
     order = np.lexsort((np.arange(len(s)), s))
@@ -199,5 +199,7 @@ def test_staged_kernel_leaves_long_ties_to_tensor_memory_kernel():
                      for i, og in enumerate(bt["oracles"])] for p in (0, 1)}
     bt["want"] = {0: [og.matvec_A(bt["vec"][1][i][None])[0] for i, og in enumerate(bt["oracles"])],
                   1: [og.matvec_AT(bt["vec"][0][i][None])[0] for i, og in enumerate(bt["oracles"])]}
-    _check(bt, kps.F32, False)
-    _check(bt, kps.F32, True)
+    for dt in (kps.F32, kps.BF16, kps.F16):
+        assert bt["b"].shape(dt)["kernel"] == kps.BATCH_STAGED
+        _check(bt, dt, False)
+        _check(bt, dt, True)
