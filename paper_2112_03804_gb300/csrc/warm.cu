@@ -197,6 +197,7 @@ struct RowInfo {
 constexpr size_t kOffW2 = 0, kOffH = kOffW2 + (size_t)kWidth / 8 * kOpRow, kOffW3 = kOffH + (size_t)kPR / 8 * kOpRow,
                  kOffRows = kOffW3 + 2 * (size_t)kOpRow, kOffBar = kOffRows + kPR * sizeof(RowInfo);
 __host__ __device__ constexpr size_t predict_smem_bytes() { return kOffBar + 16 + 128; }
+// (barrier at kOffBar, tensor-memory slot at +8, the tile's first game at +12)
 
 __device__ __forceinline__ uint32_t op_off(int r, int k) {
     return (uint32_t)((r >> 3) * kOpRow + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
@@ -325,13 +326,28 @@ __global__ void __launch_bounds__(256, 1) predict_kernel(const PredictArgs a) {
     uint32_t phase = 0;
     bool ok = true;
     const long long ntiles = (a.nq + kPR - 1) / kPR;
+    int *tile_game = reinterpret_cast<int *>(smem_raw + kOffBar + 12);
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        // the tile's queries are consecutive: one search for the game of its
+        // first query, then every row steps forward from it
+        if (tid == 0) *tile_game = decode(a.d, tile * kPR).game;
+        __syncthreads();
         if (tid < kPR) {
             const long long q = tile * kPR + tid;
             RowInfo ri;
             ri.nact = 0;
             if (q < a.nq) {
-                const Query Q = decode(a.d, q);
+                int gq = *tile_game;
+                while (a.d.qstart[gq + 1] <= q) ++gq;
+                const WarmGame &GQ = a.d.games[gq];
+                Query Q;
+                Q.game = gq;
+                int r = (int)(q - GQ.qstart);
+                const int n1 = GQ.nodes[0] * GQ.H;
+                Q.player = r < n1 ? 0 : 1;
+                if (Q.player) r -= n1;
+                Q.node = r / GQ.H;
+                Q.hand = r - Q.node * GQ.H;
                 const WarmGame &G = a.d.games[Q.game];
                 const int4 nd = a.d.node[G.node_off[Q.player] + Q.node];
                 const int2 cd = a.d.cards[G.hand_off + Q.hand];
@@ -352,17 +368,38 @@ __global__ void __launch_bounds__(256, 1) predict_kernel(const PredictArgs a) {
             rows[tid] = ri;
         }
         __syncthreads();
-        // layer 1: column j of every row, written as BF16 in the A layout
-        for (int r = 0; r < kPR; ++r) {
-            const RowInfo &ri = rows[r];
-            float z = 0.f;
-            if (ri.nact > 0) {
-                z = a.G1[(long long)ri.gp * kWidth + j] + a.N1[(long long)ri.node * kWidth + j] + ri.pos * wpos +
-                    ri.tie * wtie + ri.mu * wmu + __bfloat162float(Wc[ri.ca * kWidth + j]) + bias1;
-                if (ri.cb >= 0) z += __bfloat162float(Wc[ri.cb * kWidth + j]);
-                z = fmaxf(z, 0.f);
+        // layer 1: column j of every row, written as BF16 in the A layout.
+        // Eight rows at a time: their records and all their gathers are
+        // issued before any sum or store, so the loads overlap (the sum order
+        // is the definition's: game part, node part, hand features, cards).
+        for (int r0 = 0; r0 < kPR; r0 += 8) {
+            float g[8], nd[8], wa[8], wb[8], pos[8], tie[8], mu[8];
+            bool live[8], two[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const RowInfo &ri = rows[r0 + u];
+                live[u] = ri.nact > 0;
+                two[u] = ri.cb >= 0;
+                const int gp = live[u] ? ri.gp : 0, node = live[u] ? ri.node : 0;
+                const int ca = live[u] ? ri.ca : 0, cb = live[u] && two[u] ? ri.cb : 0;
+                g[u] = a.G1[(long long)gp * kWidth + j];
+                nd[u] = a.N1[(long long)node * kWidth + j];
+                wa[u] = __bfloat162float(Wc[ca * kWidth + j]);
+                wb[u] = __bfloat162float(Wc[cb * kWidth + j]);
+                pos[u] = ri.pos;
+                tie[u] = ri.tie;
+                mu[u] = ri.mu;
             }
-            *reinterpret_cast<__nv_bfloat16 *>(Hs + op_off(r, j)) = __float2bfloat16_rn(z);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                float z = 0.f;
+                if (live[u]) {
+                    z = g[u] + nd[u] + pos[u] * wpos + tie[u] * wtie + mu[u] * wmu + wa[u] + bias1;
+                    if (two[u]) z += wb[u];
+                    z = fmaxf(z, 0.f);
+                }
+                *reinterpret_cast<__nv_bfloat16 *>(Hs + op_off(r0 + u, j)) = __float2bfloat16_rn(z);
+            }
         }
         // the activations (generic writes) before the tensor cores read them;
         // the previous tile's tensor-memory loads before this tile's MMAs
