@@ -139,14 +139,80 @@ struct UpdateArgs {
     int nmax;                // largest sequence count (shared-memory rows)
 };
 
+// One node of the bottom-up walk with NA actions (exactly unrolled; NA = 0:
+// the node's own count na, up to kMaxActions, predicated): regrets updated
+// from the action values, the node's value added into its parent's slot.
+template <int NA, typename C, int BW>
+__device__ __forceinline__ void up_node(C *qv, C *rg, int s0, int na, int par, bool init, const float *beh0,
+                                        long long hs, C theta, int method, C dpos, C dneg) {
+    constexpr int M = NA > 0 ? NA : kMaxActions;
+    if (NA > 0) na = NA;
+    C r[M], b[M], q[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+        if (a < na) {
+            r[a] = rg[(s0 + a) * BW];
+            q[a] = qv[(s0 + a) * BW];
+        }
+    if (init) {
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+            if (a < na) b[a] = C(beh0[(long long)(s0 + a) * hs]);
+    } else {
+        C sum = C(0);
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+            if (a < na) sum += r[a] > C(0) ? r[a] : C(0);
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+            if (a < na) b[a] = sum > theta ? (r[a] > C(0) ? r[a] : C(0)) / sum : C(1) / C(na);
+    }
+    C v = C(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+        if (a < na) v += b[a] * q[a];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+        if (a < na) {
+            const C rn = r[a] + q[a] - v;
+            rg[(s0 + a) * BW] = method == 0 ? (rn > C(0) ? rn : C(0)) : rn * (rn > C(0) ? dpos : dneg);
+        }
+    if (par >= 0) qv[par * BW] += v;
+}
+
+// One node of the top-down walk: the next behavioural strategy by regret
+// matching and its sequence form from the parent's.
+template <int NA, typename C, int BW>
+__device__ __forceinline__ void down_node(C *qv, const C *rg, int s0, int na, int par, C theta) {
+    constexpr int M = NA > 0 ? NA : kMaxActions;
+    if (NA > 0) na = NA;
+    C r[M], b[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+        if (a < na) r[a] = rg[(s0 + a) * BW];
+    C sum = C(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+        if (a < na) sum += r[a] > C(0) ? r[a] : C(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+        if (a < na) b[a] = sum > theta ? (r[a] > C(0) ? r[a] : C(0)) / sum : C(1) / C(na);
+    const C xpar = par >= 0 ? qv[par * BW] : C(1);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+        if (a < na) qv[(s0 + a) * BW] = xpar * b[a];
+}
+
 // One half-iteration of one player (see the file comment).  Everything the
 // thread reads is loaded first, with independent loads, into shared memory
 // ([sequence][thread]: values, then regrets); the bottom-up and top-down
 // walks run in shared memory (child values are added into the parent's
 // value slot, which the walk reads after all children; the slots then take
 // the new sequence form), and regrets and strategy are written back last.
+// At least 10 resident 64-thread blocks per SM for 16- and 32-bit
+// accumulators (the kernel is latency bound); FP64 keeps its registers.
 template <typename S, typename C, int BW>
-__global__ void __launch_bounds__(BW) rm_update_kernel(const UpdateArgs<S, C> u) {
+__global__ void __launch_bounds__(BW, sizeof(C) == 8 ? 1 : 640 / BW) rm_update_kernel(const UpdateArgs<S, C> u) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Where w = locate<BW>(u.games, u.block_game);
     const SolverGame &G = u.games[w.game];
@@ -179,49 +245,33 @@ __global__ void __launch_bounds__(BW) rm_update_kernel(const UpdateArgs<S, C> u)
         rg[s * BW] = Rp[i];
         xsp[i] += wt * C(Cv<S>::ld(xp + i));
     }
-    // bottom-up: values and regrets
+    // bottom-up: values and regrets; top-down: next strategy (a node's
+    // action count picks an exactly unrolled step; the branch is uniform
+    // over the block, whose threads are hands of one game)
+    const float *beh0 = u.beh0 ? u.beh0 + base : nullptr;
     for (int k = nn - 1; k >= 0; --k) {
         const int4 nd = nodes[k];
         const int s0 = nd.x, na = nd.y, par = nd.z;
-        C r[kMaxActions], b[kMaxActions], q[kMaxActions];
-#pragma unroll
-        for (int a = 0; a < kMaxActions; ++a)
-            if (a < na) {
-                r[a] = rg[(s0 + a) * BW];
-                q[a] = qv[(s0 + a) * BW];
-            }
-        if (init) {
-#pragma unroll
-            for (int a = 0; a < kMaxActions; ++a)
-                if (a < na) b[a] = C(u.beh0[base + (long long)(s0 + a) * hs]);
-        } else {
-            regret_match<C>(r, na, b, theta);
+        switch (na) {
+            case 2: up_node<2, C, BW>(qv, rg, s0, na, par, init, beh0, hs, theta, u.method, dpos, dneg); break;
+            case 3: up_node<3, C, BW>(qv, rg, s0, na, par, init, beh0, hs, theta, u.method, dpos, dneg); break;
+            case 4: up_node<4, C, BW>(qv, rg, s0, na, par, init, beh0, hs, theta, u.method, dpos, dneg); break;
+            case 5: up_node<5, C, BW>(qv, rg, s0, na, par, init, beh0, hs, theta, u.method, dpos, dneg); break;
+            case 6: up_node<6, C, BW>(qv, rg, s0, na, par, init, beh0, hs, theta, u.method, dpos, dneg); break;
+            default: up_node<0, C, BW>(qv, rg, s0, na, par, init, beh0, hs, theta, u.method, dpos, dneg); break;
         }
-        C v = C(0);
-#pragma unroll
-        for (int a = 0; a < kMaxActions; ++a)
-            if (a < na) v += b[a] * q[a];
-#pragma unroll
-        for (int a = 0; a < kMaxActions; ++a)
-            if (a < na) {
-                const C rn = r[a] + q[a] - v;
-                rg[(s0 + a) * BW] = u.method == 0 ? (rn > C(0) ? rn : C(0)) : rn * (rn > C(0) ? dpos : dneg);
-            }
-        if (par >= 0) qv[par * BW] += v;
     }
-    // top-down: next behavioural strategy and its sequence form
     for (int k = 0; k < nn; ++k) {
         const int4 nd = nodes[k];
         const int s0 = nd.x, na = nd.y, par = nd.z;
-        C r[kMaxActions], b[kMaxActions];
-#pragma unroll
-        for (int a = 0; a < kMaxActions; ++a)
-            if (a < na) r[a] = rg[(s0 + a) * BW];
-        regret_match<C>(r, na, b, theta);
-        const C xpar = par >= 0 ? qv[par * BW] : C(1);
-#pragma unroll
-        for (int a = 0; a < kMaxActions; ++a)
-            if (a < na) qv[(s0 + a) * BW] = xpar * b[a];
+        switch (na) {
+            case 2: down_node<2, C, BW>(qv, rg, s0, na, par, theta); break;
+            case 3: down_node<3, C, BW>(qv, rg, s0, na, par, theta); break;
+            case 4: down_node<4, C, BW>(qv, rg, s0, na, par, theta); break;
+            case 5: down_node<5, C, BW>(qv, rg, s0, na, par, theta); break;
+            case 6: down_node<6, C, BW>(qv, rg, s0, na, par, theta); break;
+            default: down_node<0, C, BW>(qv, rg, s0, na, par, theta); break;
+        }
     }
     // regrets and strategy back
 #pragma unroll 4
