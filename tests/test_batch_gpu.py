@@ -126,6 +126,9 @@ def test_every_warp_count_and_schedule(batch, schedule):
     with pytest.raises(kps.KpsError) as e:
         b.set_shape(kps.F64, 4, sms, schedule, kps.BATCH_STAGED)
     assert e.value.status == kps.ENOTSUP
+    with pytest.raises(kps.KpsError) as e:                  # at most two CTAs per SM
+        b.set_shape(kps.F32, 4, 3 * sms, schedule, kps.BATCH_STAGED)
+    assert e.value.status == kps.ENOTSUP
     try:
         b.set_shape(kps.F32, 4, 3 if schedule else 2 * sms, schedule, kps.BATCH_STAGED)
     except kps.KpsError as e:

@@ -12,6 +12,8 @@ each block's own hand order (kps_turn_block).
 * Micro decks (two-card hands, three suits, one-card hands, uniform
   beliefs): every entry of A y and A^T x in FP64 (normwise 1e-12 per game)
   and FP32 (1e-5), on ragged vectors of Dirichlet strategies.
+* BF16 and FP16 storage (2^-8 / 2^-10 of each game's largest output)
+  against the oracle on the same rounded inputs.
 * Hands that hold the river card get exactly zero in that block.
 * The 52-card turn (1128 hands, 48 river cards per ending): sampled entries
   of both products, each computed one by one by the oracle, within the FP32
@@ -154,3 +156,26 @@ def test_full_turn_sampled_entries(full_turn):
             want = og.entries(v[None], [0], [s], [h], transpose=p_in == 0)[0]
             scale = float(np.max(np.abs(got[a:b])))
             assert abs(got[s, h] - want) <= 1e-5 * scale, (p_in, int(i), s, h)
+
+
+@pytest.mark.parametrize("dt,tol", [(kps.BF16, 2.0 ** -8), (kps.F16, 2.0 ** -10)], ids=["bf16", "f16"])
+def test_micro_turn_half_precision(dt, tol):
+    """BF16 / FP16 storage (the staged kernel's 16-bit path, FP32
+    arithmetic) against the oracle on the same rounded inputs."""
+    spec = synth.turn_spec(seed=3, ranks=5, suits=2, strength_top=6)
+    og, t = OracleTurn(spec), kps.Turn(spec)
+    lay = Layout(t)
+    tdt = {kps.BF16: torch.bfloat16, kps.F16: torch.float16}[dt]
+    for p_in, v in ((1, _strategies(og, 1, 5)), (0, _strategies(og, 0, 6))):
+        vin = torch.from_numpy(lay.to_library(v, p_in)).to("cuda", tdt)
+        rounded = lay.from_library(vin.double().cpu().numpy(), p_in)
+        out = torch.full((int(lay.off[1 - p_in][-1]),), float("nan"), dtype=tdt, device="cuda")
+        (t.matvec_A if p_in == 1 else t.matvec_AT)(vin, out, dt)
+        torch.cuda.synchronize()
+        got = lay.from_library(out.double().cpu().numpy(), 1 - p_in)
+        want = og.matvec(rounded[None], transpose=p_in == 0)[0]
+        p_out = 1 - p_in
+        for i in range(lay.games):
+            a, b = lay.start[p_out][i], lay.start[p_out][i + 1]
+            scale = np.max(np.abs(want[a:b]))
+            assert np.max(np.abs(got[a:b] - want[a:b])) <= tol * scale, (dt, p_in, i)
