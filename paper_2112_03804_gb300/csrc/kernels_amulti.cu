@@ -47,10 +47,11 @@ namespace kps {
 
 namespace {
 
+constexpr unsigned kFull = 0xffffffffu;
 constexpr int kNS = 3;                     // ring slots per warp
 constexpr int kSlot = 4096;                // bytes per slot: fold rows, then showdown rows
 constexpr int kRing = kNS * kSlot;         // per warp
-constexpr int kRecRing = kNS * kScanBlock; // per warp
+constexpr int kRecRing = 2 * kNS * kScanBlock; // per warp: two record blocks per slot (split items)
 constexpr int kTmemCols = 256;             // per CTA (two CTAs per SM)
 constexpr int kMaxExtra = 8;               // chunk boxes past tensor memory (scratch)
 
@@ -60,6 +61,8 @@ struct alignas(16) AmGame {
     int nbox, pad0, pad1, pad2;
     int bchunk[kTmaWarps + 1];
     int pad3[3];
+    int bchunk8[2 * kTmaWarps + 1];   // split items: each chunk cut in two at a tie-free box boundary
+    int pad4[3];
     long long in_off, out_off;     // element offsets of the game's input / output vectors
     const int *fcol, *scol;        // per output sequence: its fold / showdown input sequence or -1
     const float *fcoef, *scoef;    // and the payoffs
@@ -69,7 +72,7 @@ struct alignas(16) AmGame {
 
 struct AmArgs {
     const AmGame *games;
-    const int2 *items;             // (game, first output sequence)
+    const int4 *items;             // (game, first output sequence, split, 0)
     int nitems, nc, schedule;
     const void *vin;               // element type: the kernel's storage type
     void *vout;
@@ -193,14 +196,24 @@ template <> struct Store<__half> {
 };
 
 // One work item, one warp: scan of the warp's chunk, combination of the
-// four chunks (two CTA barriers), finishing pass.
+// four chunks (two CTA barriers), finishing pass.  A split item has at most
+// 16 output sequences: lanes 16-31 take the same sequences as lanes 0-15 over
+// the second half of the warp's chunk (eight sub-chunks in all), and the half
+// with fewer boxes runs zero-filled boxes to the other's count, so that the
+// warp's tensor-memory operations stay uniform.
 template <typename T, int K2>
-__device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int sigma0, unsigned char *sm,
+__device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int sigma0, int split, unsigned char *sm,
                                         uint32_t tmem, float *xs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nc = P.nc, hs = G.hs;
-    const int b0 = G.bchunk[warp], nb = G.bchunk[warp + 1] - b0;
-    const int sigma = sigma0 + lane;
+    const int half = split ? lane >> 4 : 0, col = split ? lane & 15 : lane;
+    const int sub = split ? 2 * warp + half : warp;   // this lane's (sub-)chunk
+    const int b0 = split ? G.bchunk8[sub] : G.bchunk[warp];
+    const int nbl = (split ? G.bchunk8[sub + 1] : G.bchunk[warp + 1]) - b0;   // this lane's boxes
+    const int b0h0 = __shfl_sync(kFull, b0, 0), b0h1 = __shfl_sync(kFull, b0, 16);
+    const int nbh0 = __shfl_sync(kFull, nbl, 0), nbh1 = __shfl_sync(kFull, nbl, 16);
+    const int nb = split ? max(nbh0, nbh1) : nbl;   // the warp's box count
+    const int sigma = sigma0 + col;
     const bool act = sigma < G.n_out;
     const int rf = act ? G.fcol[sigma] : -1, rs = act ? G.scol[sigma] : -1;
     const float F = rf >= 0 ? G.fcoef[sigma] : 0.f;
@@ -226,18 +239,27 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
     auto issue = [&](int m) {
         if (m < nb) {
             const int sl = m % kNS;
-            const int x = kTmaBox * (b0 + m);
+            const bool real = m < nbl;   // past its half's boxes a lane copies zeros
+            const int x = kTmaBox * (b0 + (real ? m : 0));
             const uint32_t dst = ring_s + (uint32_t)(sl * kSlot) + 16u * (uint32_t)lane;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const int h0 = x + Store<T>::kPer * q;
-                const bool in = h0 < hs;   // hs is a multiple of 8: a chunk is all in or all out
+                const bool in = real && h0 < hs;   // hs is a multiple of 8: a chunk is all in or all out
                 cp16(dst + 512u * q, in ? pa + h0 : pa, in ? na : 0u);
                 cp16(dst + 2048u + 512u * q, in ? pb + h0 : pb, in ? nbytes_b : 0u);
             }
-            if (lane < kScanBlock / 16)
-                cp16(rring_s + (uint32_t)(sl * kScanBlock) + 16u * (uint32_t)lane,
-                     G.rscan + (size_t)(b0 + m) * kScanBlock + 16 * lane, 16u);
+            // the record block of each half's box (zeros for a zero-filled box)
+            if (lane < kScanBlock / 16) {
+                const bool r0 = m < nbh0;
+                cp16(rring_s + (uint32_t)(2 * sl * kScanBlock) + 16u * (uint32_t)lane,
+                     G.rscan + (size_t)(b0h0 + (r0 ? m : 0)) * kScanBlock + 16 * lane, r0 ? 16u : 0u);
+                if (split) {
+                    const bool r1 = m < nbh1;
+                    cp16(rring_s + (uint32_t)((2 * sl + 1) * kScanBlock) + 16u * (uint32_t)lane,
+                         G.rscan + (size_t)(b0h1 + (r1 ? m : 0)) * kScanBlock + 16 * lane, r1 ? 16u : 0u);
+                }
+            }
         }
         cp_commit();
     };
@@ -269,7 +291,7 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
             Store<T>::load(slot + 512 * q, yf + Store<T>::kPer * q);
             Store<T>::load(slot + 2048 + 512 * q, ys + Store<T>::kPer * q);
         }
-        const unsigned char *rsb = rring + sl * kScanBlock;
+        const unsigned char *rsb = rring + (2 * sl + half) * kScanBlock;
         const uint32_t tw0 = reinterpret_cast<const uint32_t *>(rsb + 256)[0];
         const uint32_t tw1 = reinterpret_cast<const uint32_t *>(rsb + 256)[1];
         TmaScanRec rn = *reinterpret_cast<const TmaScanRec *>(rsb);
@@ -361,30 +383,60 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
     __syncthreads();
 
     // combination: Q_k[c] = Pall[c] + 2 S (mass of card c in chunks < k),
-    // [card][lane] floats at the start of warp k's ring
-    for (int q = warp; q < nc; q += kTmaWarps) {
-        float rr[kTmaWarps], pw[kTmaWarps];
+    // [card][lane] floats at the start of warp k's ring; a split item's
+    // sub-chunk k lives in warp k / 2, lanes 16 (k & 1) + column
+    if (!split) {
+        for (int q = warp; q < nc; q += kTmaWarps) {
+            float rr[kTmaWarps], pw[kTmaWarps];
 #pragma unroll
-        for (int k = 0; k < kTmaWarps; ++k) {
-            const float2 v = reinterpret_cast<const float2 *>(sm + am_state_off(k, nc))[q * 32 + lane];
-            rr[k] = v.x;
-            pw[k] = v.y;
+            for (int k = 0; k < kTmaWarps; ++k) {
+                const float2 v = reinterpret_cast<const float2 *>(sm + am_state_off(k, nc))[q * 32 + lane];
+                rr[k] = v.x;
+                pw[k] = v.y;
+            }
+            const float pall = (pw[0] + pw[1]) + (pw[2] + pw[3]);
+            float run = 0.f;
+#pragma unroll
+            for (int k = 0; k < kTmaWarps; ++k) {
+                reinterpret_cast<float *>(sm + am_ring_off(k))[q * 32 + lane] = pall + S2 * run;
+                run += rr[k];
+            }
         }
-        const float pall = (pw[0] + pw[1]) + (pw[2] + pw[3]);
-        float run = 0.f;
+    } else if (lane < 16) {
+        for (int q = warp; q < nc; q += kTmaWarps) {
+            float rr[2 * kTmaWarps], pw[2 * kTmaWarps];
 #pragma unroll
-        for (int k = 0; k < kTmaWarps; ++k) {
-            reinterpret_cast<float *>(sm + am_ring_off(k))[q * 32 + lane] = pall + S2 * run;
-            run += rr[k];
+            for (int k = 0; k < 2 * kTmaWarps; ++k) {
+                const float2 v =
+                    reinterpret_cast<const float2 *>(sm + am_state_off(k >> 1, nc))[q * 32 + lane + 16 * (k & 1)];
+                rr[k] = v.x;
+                pw[k] = v.y;
+            }
+            const float pall = ((pw[0] + pw[1]) + (pw[2] + pw[3])) + ((pw[4] + pw[5]) + (pw[6] + pw[7]));
+            float run = 0.f;
+#pragma unroll
+            for (int k = 0; k < 2 * kTmaWarps; ++k) {
+                reinterpret_cast<float *>(sm + am_ring_off(k >> 1))[q * 32 + lane + 16 * (k & 1)] = pall + S2 * run;
+                run += rr[k];
+            }
         }
     }
     float Cw;
     {
         float tall = 0.f, gb = 0.f;
+        if (!split) {
 #pragma unroll
-        for (int k = 0; k < kTmaWarps; ++k) {
-            tall += sums[(1 * kTmaWarps + k) * 32 + lane];
-            if (k < warp) gb += sums[(0 * kTmaWarps + k) * 32 + lane];
+            for (int k = 0; k < kTmaWarps; ++k) {
+                tall += sums[(1 * kTmaWarps + k) * 32 + lane];
+                if (k < warp) gb += sums[(0 * kTmaWarps + k) * 32 + lane];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 2 * kTmaWarps; ++k) {
+                const int at = (k >> 1) * 32 + col + 16 * (k & 1);
+                tall += sums[1 * kTmaWarps * 32 + at];
+                if (k < sub) gb += sums[at];
+            }
         }
         Cw = tall + S2 * gb;
     }
@@ -409,7 +461,8 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
     }
     for (int m = 0; m < nb; ++m) {
         if (m + 1 < nb) load_box(m + 1, nxt);
-        const TmaFinRec *fr = G.rfin + (size_t)kTmaBox / 2 * (b0 + m);
+        const bool real = m < nbl;   // a zero-filled box of the shorter half writes nothing
+        const TmaFinRec *fr = G.rfin + (size_t)kTmaBox / 2 * (b0 + (real ? m : 0));
         float o[16];
         TmaFinRec fnx = ldg_fin(fr);
 #pragma unroll
@@ -425,7 +478,7 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
             o[i] = r.lout1 * ((cur[i] + Cw) - q1);
             o[i + 1] = r.lout2 * ((cur[i + 1] + Cw) - q2);
         }
-        if (act) {
+        if (act && real) {
             const int x = kTmaBox * (b0 + m);
 #pragma unroll
             for (int q = 0; q < NQ; ++q)
@@ -467,8 +520,8 @@ __global__ void __launch_bounds__(128, 2) async_multi_kernel(const __grid_consta
             next += gridDim.x;
         }
         if (item >= P.nitems) break;
-        const int2 it = P.items[item];
-        am_item<T, K2>(P, P.games[it.x], it.y, sm, tmem, xs);
+        const int4 it = P.items[item];
+        am_item<T, K2>(P, P.games[it.x], it.y, it.z, sm, tmem, xs);
         // the next ticket is written only after every thread has read this one
         // (am_item ends its combination with a CTA barrier)
     }
@@ -538,7 +591,7 @@ AmPlan *am_create(const std::vector<AmGameDesc> &games, int grid_cap, cudaStream
         return nullptr;
     }
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    const size_t o_games = 0, o_items = al(sizeof(AmGame) * ng), o_rec = o_items + al(sizeof(int2) * (size_t)nitems);
+    const size_t o_games = 0, o_items = al(sizeof(AmGame) * ng), o_rec = o_items + al(sizeof(int4) * (size_t)nitems);
     const size_t total = o_rec + rbytes;
     AmPlan *p = new (std::nothrow) AmPlan();
     if (!p) {
@@ -558,7 +611,7 @@ AmPlan *am_create(const std::vector<AmGameDesc> &games, int grid_cap, cudaStream
     unsigned char *dev = static_cast<unsigned char *>(p->blob);
     std::vector<unsigned char> host(total, 0);
     std::vector<AmGame> g(ng);
-    std::vector<int2> items;
+    std::vector<int4> items;
     items.reserve((size_t)nitems);
     size_t ro = o_rec;
     for (int i = 0; i < ng; ++i) {
@@ -583,10 +636,32 @@ AmPlan *am_create(const std::vector<AmGameDesc> &games, int grid_cap, cudaStream
         x.rscan = dev + ro;
         x.rfin = reinterpret_cast<const TmaFinRec *>(dev + ro + (size_t)r.nbox * kScanBlock);
         ro += al(r.bytes.size());
-        for (int t = 0; t < (d.n_out + 31) / 32; ++t) items.push_back(make_int2(i, 32 * t));
+        // sub-chunks of split items: each chunk cut at the tie-free box
+        // boundary nearest its middle (an empty second half if there is none)
+        const HostGame &h = *d.h;
+        auto clean = [&](int bx) {
+            return bx <= 0 || bx >= r.nbox || 16 * bx >= r.H || h.group_lo[16 * bx] == 16 * bx;
+        };
+        bool split_ok = true;
+        for (int w = 0; w < kTmaWarps; ++w) {
+            const int lo = r.bchunk[w], hi = r.bchunk[w + 1], ideal = (lo + hi) / 2;
+            int mid = hi;
+            for (int dd = 0; dd <= hi - lo && mid == hi; ++dd) {
+                if (ideal - dd >= lo && clean(ideal - dd)) mid = ideal - dd;
+                else if (ideal + dd <= hi && clean(ideal + dd)) mid = ideal + dd;
+            }
+            x.bchunk8[2 * w] = lo;
+            x.bchunk8[2 * w + 1] = mid;
+            split_ok = split_ok && mid - lo <= 16 && hi - mid <= 16;
+        }
+        x.bchunk8[2 * kTmaWarps] = r.nbox;
+        // full items of 32 sequences; a tail of at most 16 as a split item
+        const int nfull = d.n_out / 32, tail = d.n_out - 32 * nfull;
+        for (int t = 0; t < nfull; ++t) items.push_back(make_int4(i, 32 * t, 0, 0));
+        if (tail > 0) items.push_back(make_int4(i, 32 * nfull, tail <= 16 && split_ok ? 1 : 0, 0));
     }
     std::memcpy(host.data() + o_games, g.data(), sizeof(AmGame) * ng);
-    if (!items.empty()) std::memcpy(host.data() + o_items, items.data(), sizeof(int2) * items.size());
+    if (!items.empty()) std::memcpy(host.data() + o_items, items.data(), sizeof(int4) * items.size());
     e = cudaMemcpyAsync(p->blob, host.data(), total, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
@@ -597,7 +672,7 @@ AmPlan *am_create(const std::vector<AmGameDesc> &games, int grid_cap, cudaStream
         return nullptr;
     }
     p->a.games = reinterpret_cast<const AmGame *>(dev + o_games);
-    p->a.items = reinterpret_cast<const int2 *>(dev + o_items);
+    p->a.items = reinterpret_cast<const int4 *>(dev + o_items);
     p->a.nitems = (int)nitems;
     p->a.nc = nc;
     p->k = k;
