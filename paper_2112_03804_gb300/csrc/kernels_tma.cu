@@ -229,6 +229,12 @@ __device__ __forceinline__ void tm_wait_ld16(float *r) {
                    "+f"(r[8]), "+f"(r[9]), "+f"(r[10]), "+f"(r[11]), "+f"(r[12]), "+f"(r[13]), "+f"(r[14]), "+f"(r[15])::"memory");
 }
 
+// Packed FP32x2 arithmetic (each component rounded to nearest, as the
+// scalar instruction would be).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 // Byte offset of lane `row`'s 16-byte chunk q (hands 4q..4q+3) in a
 // [32][16] fp32 box written by the 64-byte swizzle: chunk bits 4-5 are
 // XORed with address bits 7-8 (the row pair).
@@ -293,18 +299,22 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
     int nissued = min(NS, nb), nwaited = 0;   // boxes copied in / waited for (warp-uniform)
 
     // ---- scan (lane = column)
-    float G = 0.f;
-    float pp[16];                 // the previous box's partial results (stored one box late)
+    float G2 = 0.f;               // twice the b mass before the current hand
+    float2 pp[8];                 // the previous box's partial results (stored one box late)
     float bq1 = 0.f, bq2 = 0.f, bq3 = 0.f;   // b of the previous box's hands 15, 14, 13
+    const float2 F2 = make_float2(F, F), S2v = make_float2(S, S), nS2 = make_float2(-S, -S);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) pp[i] = 0.f;
-    auto store_box = [&](int m, const float *r) {
+    for (int k = 0; k < 8; ++k) pp[k] = make_float2(0.f, 0.f);
+    auto store_box = [&](int m, const float2 *r) {
         if (m < 16) {
-            tm_st16(c.tmem + (uint32_t)(16 * m), r);
+            tm_st16(c.tmem + (uint32_t)(16 * m), reinterpret_cast<const float *>(r));
         } else {
             float *xp = xpart + (m - 16) * (kTmaBox * 32);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) xp[i * 32 + lane] = r[i];
+            for (int k = 0; k < 8; ++k) {
+                xp[(2 * k) * 32 + lane] = r[k].x;
+                xp[(2 * k + 1) * 32 + lane] = r[k].y;
+            }
         }
     };
     for (int m = 0; m < nb; ++m) {
@@ -318,20 +328,23 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
         // may never have arrived: scan no further
         if (!c.ok) break;
         const unsigned char *slot = ring + sl * SLOT;
-        float yf[16], ys[16];
+        // the box's inputs as hand pairs (2i, 2i+1)
+        float2 yf[8], ys[8];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (HF) {
                 const float4 v = *reinterpret_cast<const float4 *>(slot + swz(lane, q));
-                yf[4 * q] = v.x; yf[4 * q + 1] = v.y; yf[4 * q + 2] = v.z; yf[4 * q + 3] = v.w;
+                yf[2 * q] = make_float2(v.x, v.y);
+                yf[2 * q + 1] = make_float2(v.z, v.w);
             } else {
-                yf[4 * q] = yf[4 * q + 1] = yf[4 * q + 2] = yf[4 * q + 3] = 0.f;
+                yf[2 * q] = yf[2 * q + 1] = make_float2(0.f, 0.f);
             }
             if (HS) {
                 const float4 v = *reinterpret_cast<const float4 *>(slot + (HF ? 2048 : 0) + swz(lane, q));
-                ys[4 * q] = v.x; ys[4 * q + 1] = v.y; ys[4 * q + 2] = v.z; ys[4 * q + 3] = v.w;
+                ys[2 * q] = make_float2(v.x, v.y);
+                ys[2 * q + 1] = make_float2(v.z, v.w);
             } else {
-                ys[4 * q] = ys[4 * q + 1] = ys[4 * q + 2] = ys[4 * q + 3] = 0.f;
+                ys[2 * q] = ys[2 * q + 1] = make_float2(0.f, 0.f);
             }
         }
         // the box's records: the next pair's are read before this pair's
@@ -340,82 +353,73 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
         const uint32_t tw0 = reinterpret_cast<const uint32_t *>(rs + 256)[0];
         const uint32_t tw1 = reinterpret_cast<const uint32_t *>(rs + 256)[1];
         TmaScanRec rn = *reinterpret_cast<const TmaScanRec *>(rs);
-        float p[16], bv[16];
+        // two hands per step; the arithmetic of the two hands (or of the two
+        // halves of a per-card float2) runs as packed FP32x2 instructions,
+        // each component rounded as the scalar operation would be
+        float2 p[8], bv[8];
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
+            const int k = i / 2;
             const TmaScanRec r = rn;
-            if (i + 2 < 16) rn = reinterpret_cast<const TmaScanRec *>(rs)[i / 2 + 1];
+            if (i + 2 < 16) rn = reinterpret_cast<const TmaScanRec *>(rs)[k + 1];
             unsigned char *A1 = row(r.oa1), *A2 = row(r.oa2), *B1 = row(r.ob1), *B2 = row(r.ob2);
-            float2 sa1, sa2, sb1 = make_float2(0.f, 0.f), sb2 = make_float2(0.f, 0.f);
+            const float2 lin = make_float2(r.lin1, r.lin2);
+            // the two hands' inputs: a (fold side), b (showdown side), w
+            const float2 bb = HS ? mul2(lin, ys[k]) : make_float2(0.f, 0.f);
+            bv[k] = bb;
+            float2 ww;
+            if (FS) ww = fma2(F2, mul2(lin, yf[k]), mul2(nS2, bb));   // F a - S b
+            else if (HF) ww = mul2(F2, mul2(lin, yf[k]));
+            else ww = make_float2(0.f, 0.f);   // a showdown-only column tracks b alone
+            float cs1, cs2;   // b mass of the hands' cards before them
             if (FS) {
-                sa1 = *reinterpret_cast<const float2 *>(A1);
-                sa2 = *reinterpret_cast<const float2 *>(A2);
+                // per-card rows {b mass, w total}
+                float2 sa1 = *reinterpret_cast<const float2 *>(A1);
+                float2 sa2 = *reinterpret_cast<const float2 *>(A2);
+                float2 sb1 = make_float2(0.f, 0.f), sb2 = make_float2(0.f, 0.f);
                 if (K2 == 2) {
                     sb1 = *reinterpret_cast<const float2 *>(B1);
                     sb2 = *reinterpret_cast<const float2 *>(B2);
                 }
+                const float2 h1 = make_float2(bb.x, ww.x), h2 = make_float2(bb.y, ww.y);
+                // the first hand's update, seen by the second hand's sums
+                // when they share a card (ma, mb are 0 or 1)
+                sa2 = fma2(make_float2(r.ma, r.ma), h1, sa2);
+                if (K2 == 2) sb2 = fma2(make_float2(r.mb, r.mb), h1, sb2);
+                cs1 = sa1.x + sb1.x;
+                cs2 = sa2.x + sb2.x;
+                *reinterpret_cast<float2 *>(A1) = add2(sa1, h1);
+                if (K2 == 2) *reinterpret_cast<float2 *>(B1) = add2(sb1, h1);
+                *reinterpret_cast<float2 *>(A2) = add2(sa2, h2);
+                if (K2 == 2) *reinterpret_cast<float2 *>(B2) = add2(sb2, h2);
             } else {
-                sa1.x = *reinterpret_cast<const float *>(A1);
-                sa2.x = *reinterpret_cast<const float *>(A2);
-                sa1.y = sa2.y = 0.f;
+                // one float per card: {first card, second card} of each hand
+                float2 s1 = make_float2(*reinterpret_cast<const float *>(A1), 0.f);
+                float2 s2 = make_float2(*reinterpret_cast<const float *>(A2), 0.f);
                 if (K2 == 2) {
-                    sb1.x = *reinterpret_cast<const float *>(B1);
-                    sb2.x = *reinterpret_cast<const float *>(B2);
+                    s1.y = *reinterpret_cast<const float *>(B1);
+                    s2.y = *reinterpret_cast<const float *>(B2);
                 }
-            }
-            // the two hands' inputs: a (fold side), b (showdown side), w
-            const float b1 = HS ? r.lin1 * ys[i] : 0.f, b2 = HS ? r.lin2 * ys[i + 1] : 0.f;
-            bv[i] = b1;
-            bv[i + 1] = b2;
-            float w1, w2;
-            if (FS) {
-                w1 = fmaf(F, r.lin1 * yf[i], -(S * b1));
-                w2 = fmaf(F, r.lin2 * yf[i + 1], -(S * b2));
-            } else if (HF) {
-                w1 = F * (r.lin1 * yf[i]);
-                w2 = F * (r.lin2 * yf[i + 1]);
-            } else {
-                w1 = w2 = 0.f;   // a showdown-only column tracks b alone
-            }
-            // the first hand's update, seen by the second hand's sums when
-            // they share a card (ma, mb are 0 or 1)
-            const float d1 = HS ? b1 : w1;
-            sa2.x = fmaf(r.ma, d1, sa2.x);
-            if (FS) sa2.y = fmaf(r.ma, w1, sa2.y);
-            if (K2 == 2) {
-                sb2.x = fmaf(r.mb, d1, sb2.x);
-                if (FS) sb2.y = fmaf(r.mb, w1, sb2.y);
+                const float d1 = HS ? bb.x : ww.x, d2 = HS ? bb.y : ww.y;
+                s2 = fma2(make_float2(r.ma, r.mb), make_float2(d1, d1), s2);
+                cs1 = s1.x + s1.y;
+                cs2 = s2.x + s2.y;
+                const float2 u1 = add2(s1, make_float2(d1, d1)), u2 = add2(s2, make_float2(d2, d2));
+                *reinterpret_cast<float *>(A1) = u1.x;
+                if (K2 == 2) *reinterpret_cast<float *>(B1) = u1.y;
+                *reinterpret_cast<float *>(A2) = u2.x;
+                if (K2 == 2) *reinterpret_cast<float *>(B2) = u2.y;
             }
             if (HS) {
-                // t = 2 Lo_ord - TB (b units); partial = w + S t, the w only
-                // for two-card hands (see K_F)
-                const float t1 = 2.f * (G - (sa1.x + sb1.x));
-                const float g1 = G + b1;
-                const float t2 = 2.f * (g1 - (sa2.x + sb2.x));
-                G = g1 + b2;
-                p[i] = fmaf(S, t1, K2 == 2 ? w1 : 0.f);
-                p[i + 1] = fmaf(S, t2, K2 == 2 ? w2 : 0.f);
-                if (!HF && K2 == 2) {
-                    // showdown only: w = -S b
-                    p[i] = fmaf(-S, b1, p[i]);
-                    p[i + 1] = fmaf(-S, b2, p[i + 1]);
-                }
+                // t = 2 Lo_ord - TB (b units), from the running 2G;
+                // partial = w + S t, the w only for two-card hands (see K_F)
+                const float gA = G2, gB = fmaf(2.f, bb.x, G2);
+                G2 = fmaf(2.f, bb.y, gB);
+                const float2 t = fma2(make_float2(-2.f, -2.f), make_float2(cs1, cs2), make_float2(gA, gB));
+                p[k] = fma2(S2v, t, K2 == 2 ? ww : make_float2(0.f, 0.f));
+                if (!HF && K2 == 2) p[k] = fma2(nS2, bb, p[k]);   // showdown only: w = -S b
             } else {
-                p[i] = K2 == 2 ? w1 : 0.f;
-                p[i + 1] = K2 == 2 ? w2 : 0.f;
-            }
-            // per-card updates (the second hand's store is the later one)
-            if (FS) {
-                *reinterpret_cast<float2 *>(A1) = make_float2(sa1.x + b1, sa1.y + w1);
-                if (K2 == 2) *reinterpret_cast<float2 *>(B1) = make_float2(sb1.x + b1, sb1.y + w1);
-                *reinterpret_cast<float2 *>(A2) = make_float2(sa2.x + b2, sa2.y + w2);
-                if (K2 == 2) *reinterpret_cast<float2 *>(B2) = make_float2(sb2.x + b2, sb2.y + w2);
-            } else {
-                const float d2 = HS ? b2 : w2;
-                *reinterpret_cast<float *>(A1) = sa1.x + d1;
-                if (K2 == 2) *reinterpret_cast<float *>(B1) = sb1.x + d1;
-                *reinterpret_cast<float *>(A2) = sa2.x + d2;
-                if (K2 == 2) *reinterpret_cast<float *>(B2) = sb2.x + d2;
+                p[k] = K2 == 2 ? ww : make_float2(0.f, 0.f);
             }
         }
         // tie corrections of the box (partial = w + S (2 Lo_ord - TB + TA)):
@@ -423,8 +427,12 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
         // partner's; partners before the box are the previous box's last
         // three hands (their partials are stored one box late)
         if (HS && (tw0 | tw1)) {
-            auto bat = [&](int j) { return j >= 0 ? bv[j] : (j == -1 ? bq1 : j == -2 ? bq2 : bq3); };
-            auto pat = [&](int j) -> float & { return j >= 0 ? p[j] : pp[16 + j]; };
+            auto hb = [&](int j) -> float { return (j & 1) ? bv[j >> 1].y : bv[j >> 1].x; };
+            auto bat = [&](int j) { return j >= 0 ? hb(j) : (j == -1 ? bq1 : j == -2 ? bq2 : bq3); };
+            auto pat = [&](int j) -> float & {
+                float2 &v = j >= 0 ? p[j >> 1] : pp[(16 + j) >> 1];
+                return (j & 1) ? v.y : v.x;
+            };
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const uint32_t tb = ((k < 4 ? tw0 : tw1) >> (8 * (k & 3))) & 0xfcu;
@@ -433,14 +441,14 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
 #pragma unroll
                     for (int d = 1; d <= 3; ++d)
                         if (tb & (1u << (1 + d))) {
-                            p[i] = fmaf(-S, bat(i - d), p[i]);
-                            pat(i - d) = fmaf(S, bv[i], pat(i - d));
+                            p[k].x = fmaf(-S, bat(i - d), p[k].x);
+                            pat(i - d) = fmaf(S, bv[k].x, pat(i - d));
                         }
 #pragma unroll
                     for (int d = 1; d <= 3; ++d)
                         if (tb & (1u << (4 + d))) {
-                            p[i + 1] = fmaf(-S, bat(i + 1 - d), p[i + 1]);
-                            pat(i + 1 - d) = fmaf(S, bv[i + 1], pat(i + 1 - d));
+                            p[k].y = fmaf(-S, bat(i + 1 - d), p[k].y);
+                            pat(i + 1 - d) = fmaf(S, bv[k].y, pat(i + 1 - d));
                         }
                 }
             }
@@ -456,10 +464,10 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
         }
         if (m > 0) store_box(m - 1, pp);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) pp[i] = p[i];
-        bq1 = bv[15];
-        bq2 = bv[14];
-        bq3 = bv[13];
+        for (int k = 0; k < 8; ++k) pp[k] = p[k];
+        bq1 = bv[7].y;
+        bq2 = bv[7].x;
+        bq3 = bv[6].y;
     }
     if (nb > 0) store_box(nb - 1, pp);
     tm_wait_st();
@@ -479,15 +487,15 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
                       : reinterpret_cast<const float *>(stb)[q * 32 + lane];
         if (K2 == 2) tot *= 0.5f;
     } else {
-        tot = -S * G;
+        tot = -S * (0.5f * G2);
     }
-    sums[(0 * kTmaWarps + warp) * 32 + lane] = G;
+    sums[(0 * kTmaWarps + warp) * 32 + lane] = 0.5f * G2;
     sums[(1 * kTmaWarps + warp) * 32 + lane] = tot;
     __syncthreads();
 
-    // ---- combination: Q_k[c] = Pall[c] + 2 S (mass of card c in chunks < k),
-    // [card][lane] floats at the start of warp k's ring (free now: every
-    // copy in has been consumed)
+    // ---- combination: -Q_k[c] with Q_k[c] = Pall[c] + 2 S (mass of card c
+    // in chunks < k), [card][lane] floats at the start of warp k's ring (free
+    // now: every copy in has been consumed)
     for (int q = warp; q < nc; q += kTmaWarps) {
         float rr[kTmaWarps], pw[kTmaWarps];
 #pragma unroll
@@ -507,7 +515,7 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
         float run = 0.f;
 #pragma unroll
         for (int k = 0; k < kTmaWarps; ++k) {
-            reinterpret_cast<float *>(c.sm + ring_off(k))[q * 32 + lane] = pall + S2 * run;
+            reinterpret_cast<float *>(c.sm + ring_off(k))[q * 32 + lane] = -(pall + S2 * run);
             run += rr[k];
         }
     }
@@ -527,7 +535,7 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
 }
 
 // Finishing pass (the same for every column kind): out = lambda_out
-// (partial + C - Q[c1] - Q[c2]), staged in swizzled boxes (the rest of the
+// ((partial + C) - (Q[c1] + Q[c2])), staged in swizzled boxes (the rest of the
 // ring, 2 KB each) and stored by TMA.
 template <int K2>
 __device__ __forceinline__ void tma_finish(const TmaArgs &P, const Ctx &c, float Cw) {
@@ -554,20 +562,20 @@ __device__ __forceinline__ void tma_finish(const TmaArgs &P, const Ctx &c, float
     for (int m = 0; m < nb; ++m) {
         if (m + 1 < nb) load_box(m + 1, nxt);
         const TmaFinRec *fr = P.rfin + (size_t)kTmaBox / 2 * (c.b0 + m);
-        float o[16];
+        float2 o[8];
         TmaFinRec fnx = ldg_fin(fr);
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
             const TmaFinRec r = fnx;
             if (i + 2 < 16) fnx = ldg_fin(fr + i / 2 + 1);
-            float q1 = *reinterpret_cast<const float *>(qb + r.oa1);
-            float q2 = *reinterpret_cast<const float *>(qb + r.oa2);
-            if (K2 == 2) {
-                q1 += *reinterpret_cast<const float *>(qb + r.ob1);
-                q2 += *reinterpret_cast<const float *>(qb + r.ob2);
-            }
-            o[i] = r.lout1 * ((cur[i] + Cw) - q1);
-            o[i + 1] = r.lout2 * ((cur[i + 1] + Cw) - q2);
+            // the table holds -Q: nq = -(Q[c1] + Q[c2]) for both hands
+            float2 nq = make_float2(*reinterpret_cast<const float *>(qb + r.oa1),
+                                    *reinterpret_cast<const float *>(qb + r.oa2));
+            if (K2 == 2)
+                nq = add2(nq, make_float2(*reinterpret_cast<const float *>(qb + r.ob1),
+                                          *reinterpret_cast<const float *>(qb + r.ob2)));
+            o[i / 2] = mul2(make_float2(r.lout1, r.lout2),
+                            add2(add2(make_float2(cur[i], cur[i + 1]), make_float2(Cw, Cw)), nq));
         }
         const int ob = m % nbuf;
         unsigned char *buf = ring + qbytes + ob * 2048;
@@ -577,7 +585,8 @@ __device__ __forceinline__ void tma_finish(const TmaArgs &P, const Ctx &c, float
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<float4 *>(buf + swz(lane, q)) = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+            *reinterpret_cast<float4 *>(buf + swz(lane, q)) =
+                make_float4(o[2 * q].x, o[2 * q].y, o[2 * q + 1].x, o[2 * q + 1].y);
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) {
