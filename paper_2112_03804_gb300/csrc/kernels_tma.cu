@@ -320,7 +320,10 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
     for (int m = 0; m < nb; ++m) {
         const int sl = m % NS;
         if (c.ok) {
-            const bool got = mbar_wait(bar0 + 8u * (uint32_t)sl, (uint32_t)((m / NS) & 1));
+            // the first try inline (the box is usually there), then the
+            // bounded loop
+            const uint32_t bar = bar0 + 8u * (uint32_t)sl, par = (uint32_t)((m / NS) & 1);
+            const bool got = mbar_try(bar, par) || mbar_wait(bar, par);
             c.ok = __all_sync(kFull, got);
             if (c.ok) nwaited = m + 1;
         }
