@@ -166,13 +166,14 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
                  "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
                  : "memory");
 }
-__device__ __forceinline__ TmaFinRec ldg_fin(const TmaFinRec *p) {
-    const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
-    const float4 y = __ldg(reinterpret_cast<const float4 *>(p) + 1);
-    TmaFinRec r;
-    r.oa1 = x.x; r.ob1 = x.y; r.oa2 = x.z; r.ob2 = x.w;
-    r.lout1 = y.x; r.lout2 = y.y; r.pad0 = y.z; r.pad1 = y.w;
-    return r;
+// 16-byte copy global -> shared by this thread (cp.async, L2 only)
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void tma_store3(const CUtensorMap *map, int x, int y, int z, uint32_t src) {
     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
@@ -539,15 +540,27 @@ __device__ __forceinline__ float tma_scan(const TmaArgs &P, Ctx &c) {
 
 // Finishing pass (the same for every column kind): out = lambda_out
 // ((partial + C) - (Q[c1] + Q[c2])), staged in swizzled boxes (the rest of the
-// ring, 2 KB each) and stored by TMA.
+// ring, 2 KB each) and stored by TMA.  A box's finishing records (256 bytes)
+// are copied one box ahead by cp.async into two buffers in the warp's record
+// ring (idle after the scan).  A warp whose scan gave up finishes nothing: a
+// copy into its ring may still be in flight.
 template <int K2>
 __device__ __forceinline__ void tma_finish(const TmaArgs &P, const Ctx &c, float Cw) {
+    if (!c.ok) return;
     const int lane = c.lane, nc = P.nc, nb = c.nb, z0 = 32 * c.bb;
     unsigned char *ring = c.sm + ring_off(c.warp);
     const float *xpart = reinterpret_cast<const float *>(c.sm + extra_off(c.warp, nc, P.extra));
     const unsigned char *qb = ring + 4 * lane;
     const int qbytes = (nc * 128 + 1023) & ~1023;
     const int nbuf = (kRingBytes - qbytes) / 2048;
+    unsigned char *frb = c.sm + rec_off(c.warp, nc, P.extra);
+    const uint32_t frb_s = smem_u32(frb);
+    auto fetch_fin = [&](int m) {
+        if (m < nb && lane < 16)
+            cp16(frb_s + (uint32_t)((m & 1) * 256 + 16 * lane),
+                 reinterpret_cast<const unsigned char *>(P.rfin + (size_t)kTmaBox / 2 * (c.b0 + m)) + 16 * lane);
+        cp_commit();
+    };
     float cur[16], nxt[16];
     auto load_box = [&](int m, float *r) {
         if (m < 16) {
@@ -558,19 +571,21 @@ __device__ __forceinline__ void tma_finish(const TmaArgs &P, const Ctx &c, float
             for (int i = 0; i < 16; ++i) r[i] = xp[i * 32 + lane];
         }
     };
+    fetch_fin(0);
     if (nb > 0) {
         load_box(0, cur);
         tm_wait_ld16(cur);
     }
     for (int m = 0; m < nb; ++m) {
         if (m + 1 < nb) load_box(m + 1, nxt);
-        const TmaFinRec *fr = P.rfin + (size_t)kTmaBox / 2 * (c.b0 + m);
+        fetch_fin(m + 1);
+        cp_wait<1>();   // this lane's copy of box m's records
+        __syncwarp();
+        const TmaFinRec *fr = reinterpret_cast<const TmaFinRec *>(frb + (m & 1) * 256);
         float2 o[8];
-        TmaFinRec fnx = ldg_fin(fr);
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
-            const TmaFinRec r = fnx;
-            if (i + 2 < 16) fnx = ldg_fin(fr + i / 2 + 1);
+            const TmaFinRec r = fr[i / 2];
             // the table holds -Q: nq = -(Q[c1] + Q[c2]) for both hands
             float2 nq = make_float2(*reinterpret_cast<const float *>(qb + r.oa1),
                                     *reinterpret_cast<const float *>(qb + r.oa2));
@@ -591,6 +606,8 @@ __device__ __forceinline__ void tma_finish(const TmaArgs &P, const Ctx &c, float
             *reinterpret_cast<float4 *>(buf + swz(lane, q)) =
                 make_float4(o[2 * q].x, o[2 * q].y, o[2 * q + 1].x, o[2 * q + 1].y);
         fence_proxy_async();
+        // every lane has read box m's records (their buffer is refilled
+        // with box m + 2 in the next iteration) and staged its outputs
         __syncwarp();
         if (lane == 0) {
             tma_store3(&P.tout, kTmaBox * (c.b0 + m), c.sigma, z0, smem_u32(buf));
@@ -602,6 +619,7 @@ __device__ __forceinline__ void tma_finish(const TmaArgs &P, const Ctx &c, float
             for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
         }
     }
+    cp_wait<0>();
     if (lane == 0) bulk_wait_read<0>();
     __syncwarp();
 }
