@@ -683,6 +683,21 @@ def measure_warmstart(train_games: int = 20480, per_game: int = 64, heldout: int
     return out
 
 
+def warmstart_summary(train_games: int = 2048, heldout: int = 128):
+    """A scaled-down learned warm start for the headline line: the network
+    trained on `train_games` solved endgames, then iterations and wall
+    seconds to 1e-3 of the pot on `heldout` other endgames, per arm (RM+ and
+    DCFR; cold FP32, cold BF16, warm FP32, warm BF16; inference included in
+    the warm arms)."""
+    r = measure_warmstart(train_games=train_games, heldout=heldout)
+    arms = {}
+    for k, v in r.items():
+        if k.startswith(("cold_", "warm_")):
+            arms[k] = [v["iterations"], round(v["seconds"], 4)]
+    return {"train_games": train_games, "heldout_games": heldout, "loss_first_last": r["loss_first_last"],
+            "arms_iterations_seconds": arms, "total_seconds": round(r["total_seconds"], 1)}
+
+
 def _e2e(g, y, x, oy, ox, stream, args, world):
     import torch
     from paper_2112_03804_gb300 import kps
@@ -778,7 +793,7 @@ def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec, ran, batche
         for key, fn in (("solver", measure_solver),
                         ("technique_b", measure_factors), ("libratus", measure_libratus),
                         ("libratus_solve", lambda: measure_libratus_solve(seeds=(2, 3))),
-                        ("turn", measure_turn)):
+                        ("turn", measure_turn), ("warmstart", warmstart_summary)):
             try:
                 line[key] = fn()
             except Exception as exc:   # reported, never silently dropped

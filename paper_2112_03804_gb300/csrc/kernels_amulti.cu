@@ -130,14 +130,6 @@ __device__ __forceinline__ void tm_wait_ld16(float *r) {
                  : "+f"(r[0]), "+f"(r[1]), "+f"(r[2]), "+f"(r[3]), "+f"(r[4]), "+f"(r[5]), "+f"(r[6]), "+f"(r[7]),
                    "+f"(r[8]), "+f"(r[9]), "+f"(r[10]), "+f"(r[11]), "+f"(r[12]), "+f"(r[13]), "+f"(r[14]), "+f"(r[15])::"memory");
 }
-__device__ __forceinline__ TmaFinRec ldg_fin(const TmaFinRec *p) {
-    const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
-    const float4 y = __ldg(reinterpret_cast<const float4 *>(p) + 1);
-    TmaFinRec r;
-    r.oa1 = x.x; r.ob1 = x.y; r.oa2 = x.z; r.ob2 = x.w;
-    r.lout1 = y.x; r.lout2 = y.y; r.pad0 = y.z; r.pad1 = y.w;
-    return r;
-}
 
 // Storage types: a 16-byte chunk holds 4 FP32 or 8 BF16 / FP16 values.
 template <typename T> struct Store;
@@ -455,6 +447,19 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
             for (int i = 0; i < 16; ++i) r[i] = xp[i * 32 + lane];
         }
     };
+    // each half's finishing records of box m (256 bytes) are copied one box
+    // ahead by its 16 lanes into two buffers in the record ring (idle after
+    // the scan): [m & 1][half]
+    const uint32_t frb_s = smem_u32(rring);
+    auto fetch_fin = [&](int m) {
+        if (m < nb && (split || lane < 16)) {
+            const int bm = b0 + (m < nbl ? m : 0);   // a zero-filled box reads its half's first records
+            cp16(frb_s + (uint32_t)((((m & 1) * 2 + half) * 256) + 16 * (lane & 15)),
+                 reinterpret_cast<const unsigned char *>(G.rfin + (size_t)kTmaBox / 2 * bm) + 16 * (lane & 15), 16u);
+        }
+        cp_commit();
+    };
+    fetch_fin(0);
     if (nb > 0) {
         load_box(0, cur);
         tm_wait_ld16(cur);
@@ -462,13 +467,15 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
     for (int m = 0; m < nb; ++m) {
         if (m + 1 < nb) load_box(m + 1, nxt);
         const bool real = m < nbl;   // a zero-filled box of the shorter half writes nothing
-        const TmaFinRec *fr = G.rfin + (size_t)kTmaBox / 2 * (b0 + (real ? m : 0));
+        __syncwarp();   // every lane has read box m - 1's records: refill their buffer
+        fetch_fin(m + 1);
+        cp_wait<1>();   // this lane's copy of box m's records
+        __syncwarp();
+        const TmaFinRec *fr = reinterpret_cast<const TmaFinRec *>(rring + ((m & 1) * 2 + half) * 256);
         float o[16];
-        TmaFinRec fnx = ldg_fin(fr);
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
-            const TmaFinRec r = fnx;
-            if (i + 2 < 16) fnx = ldg_fin(fr + i / 2 + 1);
+            const TmaFinRec r = fr[i / 2];
             float q1 = *reinterpret_cast<const float *>(qb + r.oa1);
             float q2 = *reinterpret_cast<const float *>(qb + r.oa2);
             if (K2 == 2) {
@@ -491,6 +498,7 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
             for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
         }
     }
+    cp_wait<0>();
     __syncwarp();
 }
 
