@@ -459,13 +459,10 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
         }
         cp_commit();
     };
-    fetch_fin(0);
-    if (nb > 0) {
-        load_box(0, cur);
-        tm_wait_ld16(cur);
-    }
-    for (int m = 0; m < nb; ++m) {
-        if (m + 1 < nb) load_box(m + 1, nxt);
+    // box m: its partials in pc, box m + 1's loaded into pn (the two arrays
+    // alternate, so no copy between boxes)
+    auto box = [&](int m, const float *pc, float *pn) {
+        if (m + 1 < nb) load_box(m + 1, pn);
         const bool real = m < nbl;   // a zero-filled box of the shorter half writes nothing
         __syncwarp();   // every lane has read box m - 1's records: refill their buffer
         fetch_fin(m + 1);
@@ -482,8 +479,8 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
                 q1 += *reinterpret_cast<const float *>(qb + r.ob1);
                 q2 += *reinterpret_cast<const float *>(qb + r.ob2);
             }
-            o[i] = r.lout1 * ((cur[i] + Cw) - q1);
-            o[i + 1] = r.lout2 * ((cur[i + 1] + Cw) - q2);
+            o[i] = r.lout1 * ((pc[i] + Cw) - q1);
+            o[i + 1] = r.lout2 * ((pc[i + 1] + Cw) - q2);
         }
         if (act && real) {
             const int x = kTmaBox * (b0 + m);
@@ -492,11 +489,16 @@ __device__ __forceinline__ void am_item(const AmArgs &P, const AmGame &G, int si
                 if (x + Store<T>::kPer * q < hs)
                     *reinterpret_cast<uint4 *>(orow + x + Store<T>::kPer * q) = Store<T>::pack(o + Store<T>::kPer * q);
         }
-        if (m + 1 < nb) {
-            tm_wait_ld16(nxt);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
-        }
+        if (m + 1 < nb) tm_wait_ld16(pn);
+    };
+    fetch_fin(0);
+    if (nb > 0) {
+        load_box(0, cur);
+        tm_wait_ld16(cur);
+    }
+    for (int m = 0; m < nb; m += 2) {
+        box(m, cur, nxt);
+        if (m + 1 < nb) box(m + 1, nxt, cur);
     }
     cp_wait<0>();
     __syncwarp();

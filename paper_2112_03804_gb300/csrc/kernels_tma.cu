@@ -571,13 +571,10 @@ __device__ __forceinline__ void tma_finish(const TmaArgs &P, const Ctx &c, float
             for (int i = 0; i < 16; ++i) r[i] = xp[i * 32 + lane];
         }
     };
-    fetch_fin(0);
-    if (nb > 0) {
-        load_box(0, cur);
-        tm_wait_ld16(cur);
-    }
-    for (int m = 0; m < nb; ++m) {
-        if (m + 1 < nb) load_box(m + 1, nxt);
+    // box m of the chunk: its partials in pc, box m + 1's loaded into pn
+    // (the two arrays alternate, so no copy between boxes)
+    auto box = [&](int m, const float *pc, float *pn) {
+        if (m + 1 < nb) load_box(m + 1, pn);
         fetch_fin(m + 1);
         cp_wait<1>();   // this lane's copy of box m's records
         __syncwarp();
@@ -593,7 +590,7 @@ __device__ __forceinline__ void tma_finish(const TmaArgs &P, const Ctx &c, float
                 nq = add2(nq, make_float2(*reinterpret_cast<const float *>(qb + r.ob1),
                                           *reinterpret_cast<const float *>(qb + r.ob2)));
             o[i / 2] = mul2(make_float2(r.lout1, r.lout2),
-                            add2(add2(make_float2(cur[i], cur[i + 1]), make_float2(Cw, Cw)), nq));
+                            add2(add2(make_float2(pc[i], pc[i + 1]), make_float2(Cw, Cw)), nq));
         }
         const int ob = m % nbuf;
         unsigned char *buf = ring + qbytes + ob * 2048;
@@ -607,17 +604,22 @@ __device__ __forceinline__ void tma_finish(const TmaArgs &P, const Ctx &c, float
                 make_float4(o[2 * q].x, o[2 * q].y, o[2 * q + 1].x, o[2 * q + 1].y);
         fence_proxy_async();
         // every lane has read box m's records (their buffer is refilled
-        // with box m + 2 in the next iteration) and staged its outputs
+        // with box m + 2 in the next box) and staged its outputs
         __syncwarp();
         if (lane == 0) {
             tma_store3(&P.tout, kTmaBox * (c.b0 + m), c.sigma, z0, smem_u32(buf));
             bulk_commit();
         }
-        if (m + 1 < nb) {
-            tm_wait_ld16(nxt);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
-        }
+        if (m + 1 < nb) tm_wait_ld16(pn);
+    };
+    fetch_fin(0);
+    if (nb > 0) {
+        load_box(0, cur);
+        tm_wait_ld16(cur);
+    }
+    for (int m = 0; m < nb; m += 2) {
+        box(m, cur, nxt);
+        if (m + 1 < nb) box(m + 1, nxt, cur);
     }
     cp_wait<0>();
     if (lane == 0) bulk_wait_read<0>();
