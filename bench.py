@@ -49,6 +49,9 @@ def _args():
                     help="matvec: the headline line; batch / solver / warmstart / factors / libratus: print "
                          "only that measurement")
     ap.add_argument("--games", type=int, default=4096, help="games of the batched workload")
+    ap.add_argument("--batch-shape", default=None,
+                    help="kernel,warps,grid,schedule: the batched launch shape instead of the autotuner's "
+                         "(profiling runs)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the batched and solver measurements in the headline line")
     return ap.parse_args()
@@ -305,7 +308,7 @@ BATCH_WORKLOAD = ("uneven river endgames in one persistent launch: boards of 3-5
 
 
 def measure_batch(ngames: int, steps: int, warmup: int, rank: int = 0, world: int = 1, dist=None,
-                  solve_iters: int = 0):
+                  solve_iters: int = 0, fixed_shape=None):
     """Batched products over uneven games (one A and one A^T launch per
     step, captured in a CUDA graph), launch shape from the autotuner.  With
     `world` ranks the job is ngames * world games, split into contiguous
@@ -336,7 +339,12 @@ def measure_batch(ngames: int, steps: int, warmup: int, rank: int = 0, world: in
             flat[off[p][j]:off[p][j + 1]] = w.reshape(-1)
         vec[p] = torch.from_numpy(flat).cuda()
     out = {p: torch.empty(int(off[p][-1]), device="cuda") for p in (0, 1)}
-    shape = b.tune(kps.F32, stream)
+    if fixed_shape:
+        kern, warps, grid, sched = (int(v) for v in fixed_shape.split(","))
+        b.set_shape(kps.F32, warps, grid, sched, kern)
+        shape = dict(b.shape(kps.F32), ms_per_pair=None)
+    else:
+        shape = b.tune(kps.F32, stream)
     # one step = A y and A^T x for every game, captured once as a graph
     b.matvec_A(vec[1], out[0], stream=stream)
     b.matvec_AT(vec[0], out[1], stream=stream)
@@ -813,7 +821,7 @@ def main():
         if world > 1:
             import torch.distributed as dist
             dist.init_process_group("nccl")
-        res = measure_batch(args.games, args.steps, args.warmup, rank, world, dist)
+        res = measure_batch(args.games, args.steps, args.warmup, rank, world, dist, fixed_shape=args.batch_shape)
         if rank == 0:
             print(json.dumps(res), flush=True)
         if dist:
