@@ -700,7 +700,7 @@ def warmstart_summary(train_games: int = 2048, heldout: int = 128):
     r = measure_warmstart(train_games=train_games, heldout=heldout)
     arms = {}
     for k, v in r.items():
-        if k.startswith(("cold_", "warm_")):
+        if k.startswith(("cold_", "warm_")) and isinstance(v, dict) and "iterations" in v:
             arms[k] = [v["iterations"], round(v["seconds"], 4)]
     return {"train_games": train_games, "heldout_games": heldout, "loss_first_last": r["loss_first_last"],
             "arms_iterations_seconds": arms, "total_seconds": round(r["total_seconds"], 1)}
