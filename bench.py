@@ -797,11 +797,13 @@ def _report(args, world, ms, la, lt, H, n1, n2, inf, clk, e2e, spec, ran, batche
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_seconds)
     if not args.no_secondary:
-        line["batched"] = batched
+        # the batched and warm-start figures go last, where a tail of the
+        # output keeps them
         for key, fn in (("solver", measure_solver),
                         ("technique_b", measure_factors), ("libratus", measure_libratus),
                         ("libratus_solve", lambda: measure_libratus_solve(seeds=(2, 3))),
-                        ("turn", measure_turn), ("warmstart", warmstart_summary)):
+                        ("turn", measure_turn), ("batched", lambda: batched),
+                        ("warmstart", warmstart_summary)):
             try:
                 line[key] = fn()
             except Exception as exc:   # reported, never silently dropped
