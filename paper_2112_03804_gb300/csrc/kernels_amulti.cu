@@ -24,8 +24,9 @@
 // stay in tensor memory (lane = column, a column per hand); later boxes go
 // to a per-CTA scratch area in global memory (L2-resident).  The four
 // chunks are combined in shared memory exactly as in the single-game
-// kernel, and each lane writes its finished row segments with 16-byte
-// stores.  CTAs are persistent: they take work items from an atomic ticket
+// kernel; the finishing pass reads each box's finishing records from the
+// record ring (copied one box ahead with cp.async, 256 bytes per half-warp),
+// and each lane writes its finished row segments with 16-byte stores.  CTAs are persistent: they take work items from an atomic ticket
 // or a static stride.  No spin-waits (cp.async groups complete in
 // hardware), no atomics on results: bit-reproducible.
 #include "kernels.h"

@@ -29,22 +29,26 @@
 // swizzled slot of the warp's ring (an mbarrier per slot); lanes read their
 // row four hands at a time (conflict free under the swizzle).  Per-card sums
 // live in shared memory [card][lane] (float2: mass of b for Lo, total of w
-// for K_F), addressed by per-hand byte offsets from the parameter block.
-// Two hands per step: all four per-card loads are issued together; when the
-// second hand holds a card of the first, its loaded sums get the first
-// hand's update in registers.  Partial results stay on chip: the first 16
-// boxes of a chunk in tensor memory (lane = column, a column per hand, one
-// tcgen05.st per box), later boxes in shared memory.  After a barrier the
-// four chunks' per-card sums are combined in place into
-// Q[c] = Pall[c] + 2 S R_before[c], and each warp finishes its boxes:
-// out = lambda_out (partial + C - Q[c1] - Q[c2]) with
-// C = Tot + 2 S G_before, written into a swizzled box and stored with one
-// cp.async.bulk.tensor per box.  No atomics: results are bit-reproducible.
+// for K_F), addressed by per-hand byte offsets from the box's hand records
+// (copied by cp.async.bulk with the box into a record ring).  Two hands per
+// step: all four per-card loads are issued together; when the second hand
+// holds a card of the first, its loaded sums get the first hand's update in
+// registers; the two hands' arithmetic (and the two halves of a float2 sum)
+// runs as packed FP32x2 instructions.  Partial results stay on chip: the
+// first 16 boxes of a chunk in tensor memory (lane = column, a column per
+// hand, one tcgen05.st per box), later boxes in shared memory.  After a
+// barrier the four chunks' per-card sums are combined into
+// -Q[c] = -(Pall[c] + 2 S R_before[c]) at the start of each warp's ring, and
+// each warp finishes its boxes: out = lambda_out ((partial + C) - (Q[c1] +
+// Q[c2])) with C = Tot + 2 S G_before, the finishing records read from the
+// record ring (copied one box ahead by cp.async), written into a swizzled
+// box and stored with one cp.async.bulk.tensor per box.  No atomics:
+// results are bit-reproducible.
 //
 // Waits are bounded: a wait that gives up sets *err; the warp scans no
-// further box, the CTA runs to its end without waiting again (its results
-// are not valid), waits (bounded) for its copies still in flight and frees
-// its tensor memory.
+// further box and finishes nothing, the CTA runs to its end without waiting
+// again (its results are not valid), waits (bounded) for its copies still in
+// flight and frees its tensor memory.
 #include "kernels.h"
 #include "game.h"
 #include "scan_records.h"
