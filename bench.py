@@ -45,7 +45,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--workload", default="matvec", choices=["matvec", "batch", "solver", "warmstart", "factors", "libratus", "libratus_solve",
-                                                   "turn"],
+                                                   "turn", "predict"],
                     help="matvec: the headline line; batch / solver / warmstart / factors / libratus: print "
                          "only that measurement")
     ap.add_argument("--games", type=int, default=4096, help="games of the batched workload")
@@ -702,6 +702,32 @@ def measure_warmstart(train_games: int = 20480, per_game: int = 64, heldout: int
     return out
 
 
+def measure_predict(ngames: int = 512, steps: int = 5, warmup: int = 3):
+    """The fused warm-start predictor (`kps_warm_predict`) over every
+    (game, player, node, hand) query of `ngames` river endgames (the
+    1081-hand generator, seeds 0..ngames-1) with a freshly initialised
+    network; CUDA events around each call (which includes its game- and
+    node-part products and a sync)."""
+    import torch
+    from paper_2112_03804_gb300 import kps, synth, warmstart as W
+    b = kps.Batch([kps.Game(synth.river_spec(seed=i)) for i in range(ngames)])
+    mlp = kps.MLP(seed=1)
+    for _ in range(max(warmup, 1)):
+        W.predict(mlp, b)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        W.predict(mlp, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    nq = kps.warm_num_queries(b)
+    return {"workload": f"warm-start predictor over {ngames} river endgames (1081 hands, 43+43 sequences)",
+            "queries": nq, "ms_per_call": statistics.median(ms), "queries_per_s": nq / (statistics.median(ms) / 1e3)}
+
+
 def warmstart_summary(train_games: int = 2048, heldout: int = 128):
     """A scaled-down learned warm start for the headline line: the network
     trained on `train_games` solved endgames, then iterations and wall
@@ -839,6 +865,10 @@ def main():
             print(json.dumps(res), flush=True)
         if dist:
             dist.destroy_process_group()
+    elif args.workload == "predict":
+        import torch
+        torch.cuda.set_device(_dist()[2])
+        print(json.dumps(measure_predict(args.games, args.steps, args.warmup)), flush=True)
     elif args.workload == "warmstart":
         import torch
         torch.cuda.set_device(_dist()[2])
