@@ -39,3 +39,19 @@ def test_warmstart_summary_keeps_only_solver_arms(monkeypatch):
     assert s["train_games"] == 16 and s["heldout_games"] == 4
     assert s["arms_iterations_seconds"] == {"cold_f32": [300, 0.25], "warm_bf16": [200, 0.25],
                                             "cold_dcfr_f32": [300, 0.25]}
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    out = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                          "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                          "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
